@@ -1,0 +1,130 @@
+/*
+ * sadi.h -- C ABI of the S-ADI library (splitting ADI scheme for the 2D
+ * fractional Laplacian wave equation, arXiv 2312.06206), GB300 / sm_103a.
+ *
+ * Problem (Sec. 1, eq. "wave equation"): on Omega = (a, b)^2,
+ *     u_tt = -kappa (-Delta)^{alpha/2} u + g(u),  u = 0 outside Omega,
+ *     u(x, y, 0) = phi1,  u_t(x, y, 0) = phi2,
+ * discretised on N x N interior points with h = (b - a)/(N + 1) (Sec. 2) and
+ * advanced by the S-ADI scheme in its factored increment form (Sec. 3, eq.
+ * "ADI scheme equivalent"):
+ *     (1 + tau^2 kappa/2 delta_x)(1 + tau^2 kappa/2 delta_y) uhat^n = B^n,
+ * with both ADI factors solved by the Gohberg-Semencul formula (Proposition 1,
+ * Algorithm 1) and L_h u^n applied by a zero-padded 2D FFT convolution (Sec. 3).
+ *
+ * Conventions shared by every entry point:
+ *  - Grid functions are N x N row-major arrays of double, element [j*N + i] is
+ *    the value at (x_{i+1}, y_{j+1}): i is the x index (contiguous), j the y
+ *    index.  Host arrays are read or written synchronously and are owned by
+ *    the caller; the library never keeps a host pointer.
+ *  - The context owns all of its device memory and frees it in sadi_destroy.
+ *  - Every call returns a status and never aborts or exits; on failure the
+ *    context keeps a message readable with sadi_last_error.  After a CUDA
+ *    error (SADI_ECUDA) the context refuses further steps with SADI_ESTATE.
+ *  - All device work of a context is issued on its stream (sadi_set_stream);
+ *    calls on one context must not run concurrently from several host threads.
+ */
+#ifndef SADI_H
+#define SADI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sadi_ctx sadi_ctx;
+
+typedef enum {
+  SADI_OK = 0,
+  SADI_EINVAL = 1,        /* invalid argument (message names it)                */
+  SADI_ENOMEM = 2,        /* device or host allocation failed                   */
+  SADI_ECUDA = 3,         /* a CUDA call failed; the context is now unusable    */
+  SADI_ENOTSPD = 4,       /* generator solve broke down (H not SPD numerically) */
+  SADI_ESTATE = 5,        /* call out of order (e.g. step before set_initial)   */
+  SADI_ETIMEOUT = 6,      /* a bounded device wait ran out                      */
+  SADI_ENONFINITE = 7,    /* non-finite value detected in the state             */
+  SADI_EUNSUPPORTED = 8   /* valid request this build does not implement       */
+} sadi_status;
+
+/* Nonlinearity g(u) of Sec. 1 (Sec. 6 uses -sin u and -u^3). */
+typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2 } sadi_g;
+
+/* Arithmetic of the per-step path.  Setup (weights, generator, spectra) is
+ * always FP64.  SADI_PREC_FP64: FFTs, sweeps and state in double.
+ * SADI_PREC_FP32: FFTs and sweeps in float; the state u^n, u^{n-1} in float. */
+typedef enum { SADI_PREC_FP64 = 0, SADI_PREC_FP32 = 1 } sadi_prec;
+
+/* Create a context for N interior points per direction, fractional order
+ * alpha in (1, 2] (2 = the classical wave equation limit; the paper states
+ * (1, 2)), kappa > 0, time step tau > 0 and Omega = (domain[0], domain[1])^2.
+ * Runs the FP64 setup on the current CUDA device: the 1D Riesz weights a_i
+ * (Sec. 2, eq. "single coefficient discrete Riesz"), the 2D weights a_ij
+ * (Sec. 2, eq. "center discretization"; trapezoid rule + Richardson), the
+ * symbol of the block-circulant embedding of L_h (Sec. 3), and the
+ * Gohberg-Semencul generator c = H^-1 e_1 with its spectra (Proposition 1,
+ * eq. "eigenvalue of CS").  Defaults: g = SADI_G_ZERO, precision FP64, a
+ * stream owned by the context.  N must be in [1, 4096] (FP64 path) or
+ * [1, 8192] (FP32 path).  On success *out receives the context; on failure
+ * *out is NULL and the status says why (no context is left behind). */
+sadi_status sadi_create(int N, double alpha, double kappa, double tau,
+                        const double domain[2], sadi_ctx **out);
+
+/* Choose g and the step precision.  Must be called before sadi_set_initial
+ * (SADI_ESTATE otherwise). */
+sadi_status sadi_set_options(sadi_ctx *ctx, int g, int prec);
+
+/* Issue all further device work on cuda_stream (a cudaStream_t, e.g. a torch
+ * stream's handle); NULL selects the context's own stream.  The caller keeps
+ * ownership of the stream and must keep it alive while the context uses it. */
+sadi_status sadi_set_stream(sadi_ctx *ctx, void *cuda_stream);
+
+/* Copy the initial data phi1 = u(., 0) and phi2 = u_t(., 0) (host, N*N doubles
+ * each, layout above) to the device and reset the step counter n to 0.  phi2
+ * may be NULL (meaning 0).  Synchronous with respect to the host buffers. */
+sadi_status sadi_set_initial(sadi_ctx *ctx, const double *phi1, const double *phi2);
+
+/* Advance nsteps >= 0 time steps (asynchronous on the context's stream).  The
+ * first step after sadi_set_initial uses the n = 0 formula of Sec. 3
+ * (u^1 - u^0 with B^0 = tau phi2 - tau^2/2 kappa L_h u^0 + tau^2/2 g(u^0)),
+ * every later step the n >= 1 formula (u^{n+1} - 2u^n + u^{n-1} with
+ * B^n = -tau^2 kappa L_h u^n + tau^2 g(u^n)). */
+sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
+
+/* Copy u^n to the host (N*N doubles) after the stream's pending work; *n_out
+ * (may be NULL) receives n.  Synchronous. */
+sadi_status sadi_get(sadi_ctx *ctx, double *u_out, long long *n_out);
+
+/* Copy u^n device-to-device into dst (N*N contiguous elements of dtype 0 =
+ * double or 1 = float, device memory owned by the caller), on the context's
+ * stream (asynchronous). */
+sadi_status sadi_get_device(sadi_ctx *ctx, void *dst, int dtype);
+
+/* Setup tables for parity tests, FP64, copied to the host (synchronous):
+ *   which = 0: a_i, 0 <= i < N                         (count N)
+ *   which = 1: a_ij, 0 <= i, j < N, row-major          (count N*N)
+ *   which = 2: generator c' = H'^-1 e_1 of the bordered Toeplitz matrix
+ *              H' = I + s T(a_0 .. a_{N'-1}), N' = the FFT length (count N')
+ *   which = 3: symbol Lambda(k1, k2) of the block-circulant embedding of
+ *              size 2N' x 2N' (unscaled), 0 <= k1, k2 <= N'  (count (N'+1)^2)
+ * count must equal the stated size.  N' is returned by sadi_get_info. */
+sadi_status sadi_get_setup(sadi_ctx *ctx, int which, double *out, size_t count);
+
+/* Sizes chosen at create: fft_len = N' (power of two >= N, >= 8) and the
+ * border rank r = N' - N of the Gohberg-Semencul solve.  Either pointer may
+ * be NULL. */
+sadi_status sadi_get_info(const sadi_ctx *ctx, int *fft_len, int *border_rank);
+
+/* Last error message of ctx ("" if none).  ctx may be NULL: then the message
+ * of the last failed sadi_create on this thread is returned. */
+const char *sadi_last_error(const sadi_ctx *ctx);
+
+/* Free the context and all its device memory (waits for its stream). NULL is
+ * a no-op. */
+void sadi_destroy(sadi_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SADI_H */

@@ -1,0 +1,377 @@
+// sadi_api.cu -- the C ABI declared in include/sadi.h: context lifetime,
+// argument validation, FP64 setup orchestration and the step loop.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+
+#include "../../include/sadi.h"
+#include "fft.cuh"
+#include "sadi_internal.h"
+
+using namespace sadi;
+
+struct sadi_ctx {
+  Geom g{};
+  double alpha = 0, kappa = 0, tau = 0, a = 0, b = 0, h = 0, s = 0;
+  int gkind = SADI_G_ZERO;
+  int prec = SADI_PREC_FP64;
+  int device = 0;
+  cudaStream_t own_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  // FP64 setup products
+  double* a1 = nullptr;      // Np
+  double* a2d = nullptr;     // N x N
+  double* cgen = nullptr;    // Np
+  double* lnat = nullptr;    // (Np+1)^2
+  double2* tw64 = nullptr;   // P
+  float2* tw32 = nullptr;    // P
+  double* lpb64 = nullptr;   // (Np+1) 2 Np
+  float* lpb32 = nullptr;
+  double2* lamc64 = nullptr;
+  double2* lams64 = nullptr;
+  float2* lamc32 = nullptr;
+  float2* lams32 = nullptr;
+  double* G64 = nullptr;     // N x r
+  float* G32 = nullptr;
+  // state (element type per prec)
+  void* ubuf[2] = {nullptr, nullptr};
+  void* phi2 = nullptr;
+  void* S = nullptr;         // N x Np complex
+  void* W = nullptr;         // N x N
+  double* stage = nullptr;   // N x N doubles (host <-> device staging)
+  int cur = 0;
+  long long n = 0;
+  bool initialized = false;
+  bool broken = false;
+  std::string err;
+};
+
+static thread_local std::string g_create_err;
+
+namespace {
+
+sadi_status fail(sadi_ctx* c, sadi_status st, const std::string& msg) {
+  if (c) c->err = msg;
+  return st;
+}
+
+sadi_status cuda_fail(sadi_ctx* c, cudaError_t e, const char* what) {
+  std::string m = std::string(what) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+  if (c) {
+    c->err = m;
+    c->broken = true;
+  }
+  return SADI_ECUDA;
+}
+
+#define CK(call, what)                                   \
+  do {                                                   \
+    cudaError_t e__ = (call);                            \
+    if (e__ != cudaSuccess) return cuda_fail(c, e__, what); \
+  } while (0)
+
+template <typename T>
+T* dalloc(size_t n, cudaError_t* e) {
+  void* p = nullptr;
+  *e = cudaMalloc(&p, n * sizeof(T) > 0 ? n * sizeof(T) : 16);
+  return static_cast<T*>(p);
+}
+
+void free_all(sadi_ctx* c) {
+  void* ptrs[] = {c->a1,     c->a2d,    c->cgen,   c->lnat,   c->tw64,   c->tw32, c->lpb64,
+                  c->lpb32,  c->lamc64, c->lams64, c->lamc32, c->lams32, c->G64,  c->G32,
+                  c->ubuf[0], c->ubuf[1], c->phi2, c->S,      c->W,      c->stage};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  if (c->own_stream) cudaStreamDestroy(c->own_stream);
+}
+
+int log2i(int v) {
+  int l = 0;
+  while ((1 << l) < v) ++l;
+  return l;
+}
+
+size_t esize(int prec) { return prec == SADI_PREC_FP32 ? sizeof(float) : sizeof(double); }
+
+sadi_status alloc_state(sadi_ctx* c) {
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  const size_t es = esize(c->prec);
+  cudaError_t e;
+  for (int k = 0; k < 2; ++k) {
+    if (c->ubuf[k]) cudaFree(c->ubuf[k]);
+    c->ubuf[k] = nullptr;
+    CK(cudaMalloc(&c->ubuf[k], nn * es), "cudaMalloc(state)");
+  }
+  if (c->phi2) cudaFree(c->phi2);
+  if (c->S) cudaFree(c->S);
+  if (c->W) cudaFree(c->W);
+  c->phi2 = c->S = c->W = nullptr;
+  CK(cudaMalloc(&c->phi2, nn * es), "cudaMalloc(phi2)");
+  CK(cudaMalloc(&c->S, (size_t)c->g.N * c->g.Np * 2 * es), "cudaMalloc(spectrum)");
+  CK(cudaMalloc(&c->W, nn * es), "cudaMalloc(sweep)");
+  (void)e;
+  return SADI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sadi_status sadi_create(int N, double alpha, double kappa, double tau, const double domain[2], sadi_ctx** out) {
+  if (!out) {
+    g_create_err = "sadi_create: out is NULL";
+    return SADI_EINVAL;
+  }
+  *out = nullptr;
+  if (!domain) { g_create_err = "sadi_create: domain is NULL"; return SADI_EINVAL; }
+  if (N < 1 || N > 8192) { g_create_err = "sadi_create: N must be in [1, 8192]"; return SADI_EINVAL; }
+  if (!std::isfinite(alpha) || !(alpha > 1.0) || alpha > 2.0) {
+    g_create_err = "sadi_create: alpha must be in (1, 2]";
+    return SADI_EINVAL;
+  }
+  if (!std::isfinite(kappa) || !(kappa > 0.0)) { g_create_err = "sadi_create: kappa must be > 0"; return SADI_EINVAL; }
+  if (!std::isfinite(tau) || !(tau > 0.0)) { g_create_err = "sadi_create: tau must be > 0"; return SADI_EINVAL; }
+  if (!std::isfinite(domain[0]) || !std::isfinite(domain[1]) || !(domain[0] < domain[1])) {
+    g_create_err = "sadi_create: domain must satisfy a < b (finite)";
+    return SADI_EINVAL;
+  }
+  sadi_ctx* c = new (std::nothrow) sadi_ctx();
+  if (!c) { g_create_err = "sadi_create: host allocation failed"; return SADI_ENOMEM; }
+  auto bail = [&](sadi_status st) {
+    g_create_err = c->err;
+    free_all(c);
+    delete c;
+    return st;
+  };
+  c->alpha = alpha;
+  c->kappa = kappa;
+  c->tau = tau;
+  c->a = domain[0];
+  c->b = domain[1];
+  c->h = (c->b - c->a) / (N + 1);
+  c->s = kappa * tau * tau / (2.0 * std::pow(c->h, alpha));
+  Geom& g = c->g;
+  g.N = N;
+  g.logNp = log2i(N < 8 ? 8 : N);
+  g.Np = 1 << g.logNp;
+  g.P = 2 * g.Np;
+  g.logP = g.logNp + 1;
+  g.r = g.Np - N;
+  cudaError_t e = cudaGetDevice(&c->device);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaGetDevice"));
+  e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+  if (e != cudaSuccess) return bail(cuda_fail(c, e, "cudaStreamCreate"));
+  c->stream = c->own_stream;
+  const int Np = g.Np, P = g.P;
+  const size_t nn = (size_t)N * N;
+  const size_t nlpb = (size_t)(Np + 1) * 2 * Np;
+  struct A { void** p; size_t bytes; } allocs[] = {
+      {(void**)&c->a1, sizeof(double) * Np},
+      {(void**)&c->a2d, sizeof(double) * nn},
+      {(void**)&c->cgen, sizeof(double) * Np},
+      {(void**)&c->lnat, sizeof(double) * (size_t)(Np + 1) * (Np + 1)},
+      {(void**)&c->tw64, sizeof(double2) * P},
+      {(void**)&c->tw32, sizeof(float2) * P},
+      {(void**)&c->lpb64, sizeof(double) * nlpb},
+      {(void**)&c->lpb32, sizeof(float) * nlpb},
+      {(void**)&c->lamc64, sizeof(double2) * Np},
+      {(void**)&c->lams64, sizeof(double2) * Np},
+      {(void**)&c->lamc32, sizeof(float2) * Np},
+      {(void**)&c->lams32, sizeof(float2) * Np},
+      {(void**)&c->G64, sizeof(double) * ((size_t)N * g.r + 1)},
+      {(void**)&c->G32, sizeof(float) * ((size_t)N * g.r + 1)},
+      {(void**)&c->stage, sizeof(double) * nn},
+  };
+  for (auto& al : allocs) {
+    e = cudaMalloc(al.p, al.bytes);
+    if (e != cudaSuccess) {
+      c->err = std::string("sadi_create: cudaMalloc failed: ") + cudaGetErrorString(e);
+      return bail(SADI_ENOMEM);
+    }
+  }
+  cudaStream_t st = c->stream;
+  if ((e = launch_twiddles(c->tw64, c->tw32, P, st))) return bail(cuda_fail(c, e, "twiddles"));
+  if ((e = launch_riesz1d(c->a1, Np, alpha, st))) return bail(cuda_fail(c, e, "riesz weights"));
+  const int M = (8 * Np > 1024) ? 8 * Np : 1024;
+  if ((e = run_weights2d(c->a2d, g, alpha, M, c->tw64, st))) return bail(cuda_fail(c, e, "2D weights"));
+  const double scale = -kappa * tau * tau * std::pow(c->h, -alpha) / ((double)P * (double)Np);
+  if ((e = run_lambda(c->a2d, g, c->tw64, scale, c->lnat, c->lpb64, c->lpb32, st)))
+    return bail(cuda_fail(c, e, "symbol"));
+  int gstat = 1;
+  if ((e = run_generator(c->a1, g, c->s, c->tw64, c->cgen, c->lamc64, c->lams64, c->lamc32, c->lams32, c->G64,
+                         c->G32, &gstat, st)))
+    return bail(cuda_fail(c, e, "generator"));
+  if (gstat != 0) {
+    c->err = "sadi_create: Durbin recursion broke down (H not numerically SPD)";
+    return bail(SADI_ENOTSPD);
+  }
+  if ((e = step_setup_attributes<float>())) return bail(cuda_fail(c, e, "kernel attributes"));
+  if ((e = step_setup_attributes<double>())) return bail(cuda_fail(c, e, "kernel attributes"));
+  sadi_status sst = alloc_state(c);
+  if (sst != SADI_OK) return bail(sst);
+  if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "setup"));
+  *out = c;
+  return SADI_OK;
+}
+
+sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (c->initialized) return fail(c, SADI_ESTATE, "sadi_set_options must precede sadi_set_initial");
+  if (g < SADI_G_ZERO || g > SADI_G_NEG_SIN) return fail(c, SADI_EINVAL, "g must be 0, 1 or 2");
+  if (prec != SADI_PREC_FP64 && prec != SADI_PREC_FP32) return fail(c, SADI_EINVAL, "prec must be 0 or 1");
+  if (prec == SADI_PREC_FP64 && c->g.N > 4096)
+    return fail(c, SADI_EUNSUPPORTED, "the FP64 step path supports N <= 4096");
+  c->gkind = g;
+  if (prec != c->prec) {
+    c->prec = prec;
+    return alloc_state(c);
+  }
+  return SADI_OK;
+}
+
+sadi_status sadi_set_stream(sadi_ctx* c, void* stream) {
+  if (!c) return SADI_EINVAL;
+  c->stream = stream ? static_cast<cudaStream_t>(stream) : c->own_stream;
+  return SADI_OK;
+}
+
+sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!phi1) return fail(c, SADI_EINVAL, "phi1 is NULL");
+  if (c->prec == SADI_PREC_FP64 && c->g.N > 4096)
+    return fail(c, SADI_EUNSUPPORTED, "the FP64 step path supports N <= 4096; select SADI_PREC_FP32");
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  cudaStream_t st = c->stream;
+  c->cur = 0;
+  CK(cudaMemcpyAsync(c->stage, phi1, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy phi1");
+  if (c->prec == SADI_PREC_FP64) {
+    CK(cudaMemcpyAsync(c->ubuf[0], c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "phi1");
+  } else {
+    CK(launch_convert_d2f(c->stage, static_cast<float*>(c->ubuf[0]), nn, st), "phi1 convert");
+  }
+  if (phi2) {
+    CK(cudaMemcpyAsync(c->stage, phi2, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy phi2");
+    if (c->prec == SADI_PREC_FP64)
+      CK(cudaMemcpyAsync(c->phi2, c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "phi2");
+    else
+      CK(launch_convert_d2f(c->stage, static_cast<float*>(c->phi2), nn, st), "phi2 convert");
+  } else {
+    CK(cudaMemsetAsync(c->phi2, 0, nn * esize(c->prec), st), "phi2 zero");
+  }
+  CK(cudaStreamSynchronize(st), "set_initial");
+  c->n = 0;
+  c->initialized = true;
+  return SADI_OK;
+}
+
+sadi_status sadi_step(sadi_ctx* c, int nsteps) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_step before sadi_set_initial");
+  if (nsteps < 0) return fail(c, SADI_EINVAL, "nsteps must be >= 0");
+  for (int it = 0; it < nsteps; ++it) {
+    RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0};
+    void* ucur = c->ubuf[c->cur];
+    void* uoth = c->ubuf[1 - c->cur];
+    cudaError_t e;
+    if (c->prec == SADI_PREC_FP64) {
+      StepTables<double> tb{c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
+      e = launch_step<double>(c->g, tb, rp, static_cast<const double*>(ucur), static_cast<const double*>(uoth),
+                              static_cast<double*>(uoth), static_cast<const double*>(c->phi2), c->S,
+                              static_cast<double*>(c->W), c->stream);
+    } else {
+      StepTables<float> tb{c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+      e = launch_step<float>(c->g, tb, rp, static_cast<const float*>(ucur), static_cast<const float*>(uoth),
+                             static_cast<float*>(uoth), static_cast<const float*>(c->phi2), c->S,
+                             static_cast<float*>(c->W), c->stream);
+    }
+    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+    c->cur = 1 - c->cur;
+    c->n += 1;
+  }
+  return SADI_OK;
+}
+
+sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_get before sadi_set_initial");
+  if (!u_out) return fail(c, SADI_EINVAL, "u_out is NULL");
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  cudaStream_t st = c->stream;
+  if (c->prec == SADI_PREC_FP64) {
+    CK(cudaMemcpyAsync(u_out, c->ubuf[c->cur], nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
+  } else {
+    CK(launch_convert_f2d(static_cast<const float*>(c->ubuf[c->cur]), c->stage, nn, st), "u convert");
+    CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
+  }
+  CK(cudaStreamSynchronize(st), "sadi_get");
+  if (n_out) *n_out = c->n;
+  return SADI_OK;
+}
+
+sadi_status sadi_get_device(sadi_ctx* c, void* dst, int dtype) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_get_device before sadi_set_initial");
+  if (!dst) return fail(c, SADI_EINVAL, "dst is NULL");
+  if (dtype != 0 && dtype != 1) return fail(c, SADI_EINVAL, "dtype must be 0 (double) or 1 (float)");
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  cudaStream_t st = c->stream;
+  const void* src = c->ubuf[c->cur];
+  if (c->prec == SADI_PREC_FP64) {
+    if (dtype == 0) CK(cudaMemcpyAsync(dst, src, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
+    else CK(launch_convert_d2f(static_cast<const double*>(src), static_cast<float*>(dst), nn, st), "convert");
+  } else {
+    if (dtype == 1) CK(cudaMemcpyAsync(dst, src, nn * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy");
+    else CK(launch_convert_f2d(static_cast<const float*>(src), static_cast<double*>(dst), nn, st), "convert");
+  }
+  return SADI_OK;
+}
+
+sadi_status sadi_get_setup(sadi_ctx* c, int which, double* out, size_t count) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!out) return fail(c, SADI_EINVAL, "out is NULL");
+  const double* src = nullptr;
+  size_t n = 0;
+  const size_t N = c->g.N, Np = c->g.Np;
+  switch (which) {
+    case 0: src = c->a1; n = N; break;
+    case 1: src = c->a2d; n = N * N; break;
+    case 2: src = c->cgen; n = Np; break;
+    case 3: src = c->lnat; n = (Np + 1) * (Np + 1); break;
+    default: return fail(c, SADI_EINVAL, "which must be 0..3");
+  }
+  if (count != n) return fail(c, SADI_EINVAL, "count does not match the table size");
+  CK(cudaMemcpyAsync(out, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy setup table");
+  CK(cudaStreamSynchronize(c->stream), "sadi_get_setup");
+  return SADI_OK;
+}
+
+sadi_status sadi_get_info(const sadi_ctx* c, int* fft_len, int* border_rank) {
+  if (!c) return SADI_EINVAL;
+  if (fft_len) *fft_len = c->g.Np;
+  if (border_rank) *border_rank = c->g.r;
+  return SADI_OK;
+}
+
+const char* sadi_last_error(const sadi_ctx* c) {
+  if (!c) return g_create_err.c_str();
+  return c->err.c_str();
+}
+
+void sadi_destroy(sadi_ctx* c) {
+  if (!c) return;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  free_all(c);
+  delete c;
+}
+
+}  // extern "C"

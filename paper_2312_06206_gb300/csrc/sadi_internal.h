@@ -1,0 +1,65 @@
+// sadi_internal.h -- launch wrappers shared by the translation units of the
+// S-ADI library.  Not part of the public C ABI (include/sadi.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+namespace sadi {
+
+// Sizes of one instance.  N interior points per direction; the FFT length
+// Np = N' is the smallest power of two >= max(N, 8); the 2D convolution works
+// on the 2Np x 2Np block-circulant embedding (P = 2Np >= 2N - 1); the
+// Gohberg-Semencul solves work on the bordered Np x Np Toeplitz matrix with
+// border rank r = Np - N.
+struct Geom {
+  int N, Np, logNp, P, logP, r;
+};
+
+// Scalars of the right-hand side B^n (Sec. 3): tau, tau^2, g kind, n == 0.
+struct RhsParams {
+  double tau, tau2;
+  int g;
+  int first;
+};
+
+// ---- setup (FP64), setup_kernels.cu ----------------------------------------
+cudaError_t launch_twiddles(double2* tw64, float2* tw32, int P, cudaStream_t st);
+cudaError_t launch_riesz1d(double* a, int n, double alpha, cudaStream_t st);
+// 2D weights a_ij (0 <= i, j < N) by the trapezoid rule on grids M and 2M +
+// one Richardson step.  Scratch is allocated and freed inside.
+cudaError_t run_weights2d(double* a2d, const Geom& g, double alpha, int M, const double2* tw64,
+                          cudaStream_t st);
+// Symbol of the block-circulant embedding: lnat[(Np+1) x (Np+1)] (unscaled,
+// natural order), and the bit-reversed conv tables lpb (scaled) in FP64/FP32.
+cudaError_t run_lambda(const double* a2d, const Geom& g, const double2* tw64, double scale, double* lnat,
+                       double* lpb64, float* lpb32, cudaStream_t st);
+// Gohberg-Semencul generator of H' = I + s T(a_0..a_{Np-1}): c' (Np), spectra
+// lam_c, lam_s (bit-reversed, scaled) and border correction G (N x r).
+// *status_host receives 0 on success, 1 if the Durbin recursion broke down.
+cudaError_t run_generator(const double* a1, const Geom& g, double s, const double2* tw64, double* cgen,
+                          double2* lamc64, double2* lams64, float2* lamc32, float2* lams32, double* G64,
+                          float* G32, int* status_host, cudaStream_t st);
+cudaError_t launch_convert_d2f(const double* src, float* dst, size_t n, cudaStream_t st);
+cudaError_t launch_convert_f2d(const float* src, double* dst, size_t n, cudaStream_t st);
+
+// ---- per-step kernels, step_kernels.cu --------------------------------------
+template <typename T>
+struct StepTables {
+  const void* tw;      // cx<T>[P]
+  const T* lpb;        // [(Np+1) * 2 * Np]
+  const void* lam_s;   // cx<T>[Np]
+  const void* lam_c;   // cx<T>[Np]
+  const T* G;          // [N * r]
+};
+
+template <typename T>
+cudaError_t step_setup_attributes();
+
+// One S-ADI step: u_next (may alias u_prev) from u_cur, u_prev.
+// S: N x Np complex scratch, W: N x N scratch.
+template <typename T>
+cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const RhsParams& rp, const T* u_cur,
+                        const T* u_prev, T* u_next, const T* phi2, void* S, T* W, cudaStream_t st);
+
+}  // namespace sadi

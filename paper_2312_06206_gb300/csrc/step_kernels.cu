@@ -1,0 +1,384 @@
+// step_kernels.cu -- the per-time-step hot path of the S-ADI scheme
+// (arXiv 2312.06206, Sec. 3, eq. "ADI scheme equivalent"):
+//
+//   B^n  = -tau^2 kappa L_h u^n + tau^2 g(u^n)            (n >= 1)
+//        = tau phi2 + 1/2 (-tau^2 kappa L_h u^0 + tau^2 g(u^0))   (n = 0)
+//   W    = B H^-1      (x sweep: H w = b on every grid row)
+//   uhat = H^-1 W      (y sweep: on every grid column)
+//   u^{n+1} = 2u^n - u^{n-1} + uhat   (n >= 1),   u^1 = u^0 + uhat   (n = 0)
+//
+// L_h u^n is the block-Toeplitz-Toeplitz-block product of Sec. 3, applied by
+// the 2Np x 2Np block-circulant embedding and 2D FFTs.  Each H^-1 v is the
+// Gohberg-Semencul formula (Proposition 1) evaluated by Algorithm 1 on the
+// bordered Toeplitz matrix H' (size Np = power of two) followed by a rank-r
+// correction (r = Np - N) that recovers H^-1 exactly.
+//
+// Four kernels per step, all FFTs of the single length Np in shared memory:
+//   k_rows_r2c   rows of u^n -> half spectrum along x (real FFT of length 2Np)
+//   k_cols_conv  per x frequency: FFT along y, x symbol, inverse FFT along y
+//   k_rows_solve inverse real FFT along x + B^n epilogue + x sweep (Algorithm 1)
+//   k_cols_solve y sweep (Algorithm 1) + leapfrog epilogue
+#include <cuda_runtime.h>
+
+#include "fft.cuh"
+#include "sadi_internal.h"
+
+namespace sadi {
+
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kMaxPairs = 16;
+
+template <typename T>
+__device__ __forceinline__ T g_of(int kind, T u) {
+  if (kind == 1) return -u * u * u;
+  if (kind == 2) return -sin(u);
+  return T(0);
+}
+
+template <typename T>
+__device__ __forceinline__ T real_view(const cx<T>* v, int k) {
+  const T* f = reinterpret_cast<const T*>(v + padi(k >> 1));
+  return f[k & 1];
+}
+
+// ---------------------------------------------------------------------------
+// Gohberg-Semencul core, Algorithm 1 on the bordered matrix H':
+// input  buf[v] = Q v1 with v1 = (v' + i J v') (natural order),
+// output buf[v] = vhat (natural order); H'^-1 v' = Re vhat + J Im vhat.
+// lam_s, lam_c carry 1/Np and 1/(2 p1 Np); Q = diag(exp(-i pi k / Np)).
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ void gs_core(cx<T>* buf, int nvec, int vs, const Geom& g, const cx<T>* __restrict__ tw,
+                        const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c) {
+  const int Np = g.Np, logNp = g.logNp;
+  fft_dif<T>(buf, logNp, nvec, vs, tw, g.logP);
+  for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
+    const int v = t >> logNp, p = t & (Np - 1);
+    cx<T>* e = buf + v * vs + padi(p);
+    *e = cmul(*e, __ldg(&lam_s[p]));
+  }
+  __syncthreads();
+  fft_dit<T>(buf, logNp, nvec, vs, tw, g.logP);
+  for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
+    const int v = t >> logNp, k = t & (Np - 1);
+    cx<T>* e = buf + v * vs + padi(k);
+    *e = cmulc(*e, __ldg(&tw[k]));       // Q^H
+  }
+  __syncthreads();
+  fft_dif<T>(buf, logNp, nvec, vs, tw, g.logP);
+  for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
+    const int v = t >> logNp, p = t & (Np - 1);
+    cx<T>* e = buf + v * vs + padi(p);
+    *e = cmul(*e, __ldg(&lam_c[p]));
+  }
+  __syncthreads();
+  fft_dit<T>(buf, logNp, nvec, vs, tw, g.logP);
+}
+
+// (H^-1 v)[k] for k < N from vhat: Re vhat[k] + Im vhat[Np-1-k] plus the
+// border correction sum_q G[k, q] ybot[q], ybot[q] = (H'^-1 v')[N + q].
+template <typename T>
+__device__ __forceinline__ T gs_out(const cx<T>* vh, int k, const Geom& g, const T* __restrict__ G) {
+  T y = vh[padi(k)].x + vh[padi(g.Np - 1 - k)].y;
+  for (int q = 0; q < g.r; ++q) {
+    const int kb = g.N + q;
+    const T yb = vh[padi(kb)].x + vh[padi(g.Np - 1 - kb)].y;
+    y += __ldg(&G[(size_t)k * g.r + q]) * yb;
+  }
+  return y;
+}
+
+// ---------------------------------------------------------------------------
+// k_rows_r2c: rows j of u -> S[j][slot], the DFT of the row zero-padded to
+// length P = 2Np, via a complex FFT of length Np of z[n] = x[2n] + i x[2n+1].
+// Slot s >= 1 holds X[brev(s)]; slot 0 holds X[0] + i X[Np] (both real).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ tw, int NR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int N = g.N, Np = g.Np, logNp = g.logNp;
+  const int vs = vec_stride(Np);
+  const int row0 = blockIdx.x * NR;
+  const int nrows = min(NR, N - row0);
+  for (int t = threadIdx.x; t < (NR << logNp); t += blockDim.x) {
+    const int v = t >> logNp, n = t & (Np - 1);
+    T a = T(0), b = T(0);
+    if (v < nrows) {
+      const T* row = u + (size_t)(row0 + v) * N;
+      if (2 * n < N) a = row[2 * n];
+      if (2 * n + 1 < N) b = row[2 * n + 1];
+    }
+    buf[v * vs + padi(n)] = mkc(a, b);
+  }
+  __syncthreads();
+  fft_dif<T>(buf, logNp, NR, vs, tw, g.logP);
+  const T half = T(0.5);
+  for (int t = threadIdx.x; t < (nrows << logNp); t += blockDim.x) {
+    const int v = t >> logNp, s = t & (Np - 1);
+    const int k = brev(s, logNp);
+    const int sp = brev((Np - k) & (Np - 1), logNp);
+    const cx<T> Z = buf[v * vs + padi(s)];
+    const cx<T> Zc = cconj(buf[v * vs + padi(sp)]);
+    const cx<T> E = cscale(cadd(Z, Zc), half);
+    const cx<T> O = cscale(cmul_mi(csub(Z, Zc)), half);   // (Z - Zc) / (2i)
+    cx<T> X;
+    if (s == 0) X = mkc(E.x + O.x, E.x - O.x);
+    else X = cadd(E, cmul(__ldg(&tw[k]), O));
+    S[(size_t)(row0 + v) * Np + s] = X;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_cols_conv: for each slot (x frequency k1) the column over j is convolved
+// along y with the symbol: FFT of length P (N nonzero inputs) split into its
+// even and odd frequency halves (two FFTs of length Np), multiply by the
+// symbol, inverse, keep rows j < N.  Slot 0 holds two real columns (k1 = 0
+// and k1 = Np) packed as re + i im; their different symbols are applied with
+// the partner formula (L0 + LN)/2 Y[k] + (L0 - LN)/2 conj(Y[-k]).
+// In place on S.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ tw, const T* __restrict__ lpb, int CT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int N = g.N, Np = g.Np, logNp = g.logNp;
+  const int vs = vec_stride(Np);
+  const int s0 = blockIdx.x * CT;
+  for (int t = threadIdx.x; t < CT * Np; t += blockDim.x) {
+    const int c = t % CT, j = t / CT;
+    cx<T> val = mkc(T(0), T(0));
+    if (j < N) val = S[(size_t)j * Np + s0 + c];
+    buf[(2 * c) * vs + padi(j)] = val;
+    buf[(2 * c + 1) * vs + padi(j)] = cmul(val, __ldg(&tw[j]));
+  }
+  __syncthreads();
+  fft_dif<T>(buf, logNp, 2 * CT, vs, tw, g.logP);
+  for (int t = threadIdx.x; t < ((2 * CT) << logNp); t += blockDim.x) {
+    const int vec = t >> logNp, p = t & (Np - 1);
+    const int slot = s0 + (vec >> 1), h = vec & 1;
+    if (slot == 0) continue;
+    cx<T>* e = buf + vec * vs + padi(p);
+    *e = cscale(*e, __ldg(&lpb[((size_t)slot * 2 + h) * Np + p]));
+  }
+  if (s0 == 0) {
+    // slot 0: pairs (p, partner) in each half, handled by one thread each.
+    for (int t = threadIdx.x; t < 2 * Np; t += blockDim.x) {
+      const int h = t >> logNp, p = t & (Np - 1);
+      const int pp = (h == 0) ? brev((Np - brev(p, logNp)) & (Np - 1), logNp) : (Np - 1 - p);
+      if (pp < p) continue;
+      cx<T>* e = buf + h * vs;
+      const cx<T> Y = e[padi(p)], Yp = e[padi(pp)];
+      const T A = __ldg(&lpb[(size_t)h * Np + p]);
+      const T B = __ldg(&lpb[((size_t)Np * 2 + h) * Np + p]);
+      e[padi(p)] = cadd(cscale(Y, A), cscale(cconj(Yp), B));
+      if (pp != p) {
+        const T Ap = __ldg(&lpb[(size_t)h * Np + pp]);
+        const T Bp = __ldg(&lpb[((size_t)Np * 2 + h) * Np + pp]);
+        e[padi(pp)] = cadd(cscale(Yp, Ap), cscale(cconj(Y), Bp));
+      }
+    }
+  }
+  __syncthreads();
+  fft_dit<T>(buf, logNp, 2 * CT, vs, tw, g.logP);
+  for (int t = threadIdx.x; t < CT * N; t += blockDim.x) {
+    const int c = t % CT, j = t / CT;
+    const cx<T> ye = buf[(2 * c) * vs + padi(j)];
+    const cx<T> yo = buf[(2 * c + 1) * vs + padi(j)];
+    S[(size_t)j * Np + s0 + c] = cadd(ye, cmulc(yo, __ldg(&tw[j])));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_rows_solve: per row j: inverse real FFT of the convolved half spectrum
+// (gives -kappa tau^2 L_h u^n, the scale being folded into the symbol),
+// B^n epilogue with g(u^n) (and phi2 when n = 0), then the x sweep W_j = H^-1 B_j.
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ phi2, T* __restrict__ W,
+             Geom g, RhsParams rp, const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s,
+             const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int N = g.N, Np = g.Np, logNp = g.logNp;
+  const int vs = vec_stride(Np);
+  const int row0 = blockIdx.x * NR;
+  const int nrows = min(NR, N - row0);
+  for (int t = threadIdx.x; t < (NR << logNp); t += blockDim.x) {
+    const int v = t >> logNp, s = t & (Np - 1);
+    cx<T> val = mkc(T(0), T(0));
+    if (v < nrows) val = S[(size_t)(row0 + v) * Np + s];
+    buf[v * vs + padi(s)] = val;
+  }
+  __syncthreads();
+  // half spectrum X[k] (slots) -> Z[k] = E + iO, the spectrum of
+  // z[n] = x[2n] + i x[2n+1]; each thread owns a partner pair of slots.
+  const T half = T(0.5);
+  for (int t = threadIdx.x; t < (NR << logNp); t += blockDim.x) {
+    const int v = t >> logNp, s = t & (Np - 1);
+    const int k = brev(s, logNp);
+    const int kp = (Np - k) & (Np - 1);
+    const int sp = brev(kp, logNp);
+    if (sp < s) continue;
+    cx<T>* e = buf + v * vs;
+    const cx<T> X = e[padi(s)];
+    if (s == 0) {
+      e[padi(0)] = mkc((X.x + X.y) * half, (X.x - X.y) * half);
+      continue;
+    }
+    const cx<T> Xp = e[padi(sp)];
+    {
+      const cx<T> E = cscale(cadd(X, cconj(Xp)), half);
+      const cx<T> O = cscale(cmulc(csub(X, cconj(Xp)), __ldg(&tw[k])), half);
+      e[padi(s)] = cadd(E, cmul_pi(O));
+    }
+    if (sp != s) {
+      const cx<T> E = cscale(cadd(Xp, cconj(X)), half);
+      const cx<T> O = cscale(cmulc(csub(Xp, cconj(X)), __ldg(&tw[kp])), half);
+      e[padi(sp)] = cadd(E, cmul_pi(O));
+    }
+  }
+  __syncthreads();
+  fft_dit<T>(buf, logNp, NR, vs, tw, g.logP);
+  // B^n and v1 = Q (v' + i J v'), staged through registers (in place).
+  const int halfNp = Np >> 1;
+  const int npairs = NR * halfNp;
+  T ra[kMaxPairs], rb[kMaxPairs];
+#pragma unroll
+  for (int it = 0; it < kMaxPairs; ++it) {
+    const int t = threadIdx.x + it * blockDim.x;
+    ra[it] = T(0);
+    rb[it] = T(0);
+    if (t < npairs) {
+      const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
+      if (v < nrows) {
+        const int row = row0 + v;
+        const cx<T>* e = buf + v * vs;
+        if (k < N) {
+          const T conv = real_view<T>(e, k);
+          const T uu = u[(size_t)row * N + k];
+          const T gg = T(rp.tau2) * g_of<T>(rp.g, uu);
+          ra[it] = rp.first ? T(rp.tau) * phi2[(size_t)row * N + k] + half * (conv + gg) : conv + gg;
+        }
+        if (k2 < N) {
+          const T conv = real_view<T>(e, k2);
+          const T uu = u[(size_t)row * N + k2];
+          const T gg = T(rp.tau2) * g_of<T>(rp.g, uu);
+          rb[it] = rp.first ? T(rp.tau) * phi2[(size_t)row * N + k2] + half * (conv + gg) : conv + gg;
+        }
+      }
+    }
+  }
+  __syncthreads();
+#pragma unroll
+  for (int it = 0; it < kMaxPairs; ++it) {
+    const int t = threadIdx.x + it * blockDim.x;
+    if (t < npairs) {
+      const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
+      cx<T>* e = buf + v * vs;
+      e[padi(k)] = cmul(mkc(ra[it], rb[it]), __ldg(&tw[k]));
+      e[padi(k2)] = cmul(mkc(rb[it], ra[it]), __ldg(&tw[k2]));
+    }
+  }
+  __syncthreads();
+  gs_core<T>(buf, NR, vs, g, tw, lam_s, lam_c);
+  for (int t = threadIdx.x; t < nrows * N; t += blockDim.x) {
+    const int v = t / N, k = t % N;
+    W[(size_t)(row0 + v) * N + k] = gs_out<T>(buf + v * vs, k, g, G);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_cols_solve: per column i: y sweep uhat = H^-1 W_{:,i}, then the leapfrog
+// u^{n+1} = 2u^n - u^{n-1} + uhat (n >= 1) or u^1 = u^0 + uhat (n = 0).
+// u_next may alias u_prev (each element is read before it is written, by the
+// same thread).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_cols_solve(const T* __restrict__ W, const T* __restrict__ u_cur, const T* u_prev, T* u_next, Geom g, int first,
+             const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c,
+             const T* __restrict__ G, int CT) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int N = g.N, Np = g.Np, logNp = g.logNp;
+  const int vs = vec_stride(Np);
+  const int i0 = blockIdx.x * CT;
+  for (int t = threadIdx.x; t < CT * Np; t += blockDim.x) {
+    const int c = t % CT, k = t / CT;
+    const int i = i0 + c, k2 = Np - 1 - k;
+    T a = T(0), b = T(0);
+    if (i < N) {
+      if (k < N) a = W[(size_t)k * N + i];
+      if (k2 < N) b = W[(size_t)k2 * N + i];
+    }
+    buf[c * vs + padi(k)] = cmul(mkc(a, b), __ldg(&tw[k]));
+  }
+  __syncthreads();
+  gs_core<T>(buf, CT, vs, g, tw, lam_s, lam_c);
+  for (int t = threadIdx.x; t < CT * N; t += blockDim.x) {
+    const int c = t % CT, j = t / CT;
+    const int i = i0 + c;
+    if (i >= N) continue;
+    const T uh = gs_out<T>(buf + c * vs, j, g, G);
+    const size_t idx = (size_t)j * N + i;
+    const T uc = u_cur[idx];
+    u_next[idx] = first ? uc + uh : (T(2) * uc - u_prev[idx]) + uh;
+  }
+}
+
+template <typename T>
+struct Cfg {
+  // rows per block of the row kernels, slots/columns per block of the column kernels
+  static int rows(int Np) { int r = (int)(4096 * sizeof(float) / sizeof(T)) / Np; return r < 1 ? 1 : r; }
+  static int conv_cols(int Np) { int c = (int)(2048 * sizeof(float) / sizeof(T)) / Np; return c < 1 ? 1 : (c > 8 ? 8 : c); }
+  static int solve_cols(int Np) { int c = (int)(8192 * sizeof(float) / sizeof(T)) / Np; return c < 1 ? 1 : (c > 16 ? 16 : c); }
+};
+
+}  // namespace
+
+template <typename T>
+cudaError_t step_setup_attributes() {
+  const int mx = 227 * 1024;
+  cudaError_t e;
+  if ((e = cudaFuncSetAttribute(k_rows_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if ((e = cudaFuncSetAttribute(k_cols_conv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if ((e = cudaFuncSetAttribute(k_cols_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const RhsParams& rp, const T* u_cur,
+                        const T* u_prev, T* u_next, const T* phi2, void* Sv, T* W, cudaStream_t st) {
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
+  const cx<T>* ls = reinterpret_cast<const cx<T>*>(tb.lam_s);
+  const cx<T>* lc = reinterpret_cast<const cx<T>*>(tb.lam_c);
+  cx<T>* S = reinterpret_cast<cx<T>*>(Sv);
+  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  const int NR = Cfg<T>::rows(g.Np);
+  const int CTc = Cfg<T>::conv_cols(g.Np);
+  const int CTs = Cfg<T>::solve_cols(g.Np);
+  if (NR * (g.Np / 2) > kMaxPairs * kThreads) return cudaErrorInvalidConfiguration;
+  const int rblocks = (g.N + NR - 1) / NR;
+  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, tw, NR);
+  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, tw, tb.lpb, CTc);
+  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, tw, ls, lc, tb.G, NR);
+  k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, g, rp.first, tw,
+                                                                          ls, lc, tb.G, CTs);
+  return cudaGetLastError();
+}
+
+template cudaError_t step_setup_attributes<float>();
+template cudaError_t step_setup_attributes<double>();
+template cudaError_t launch_step<float>(const Geom&, const StepTables<float>&, const RhsParams&, const float*,
+                                        const float*, float*, const float*, void*, float*, cudaStream_t);
+template cudaError_t launch_step<double>(const Geom&, const StepTables<double>&, const RhsParams&, const double*,
+                                         const double*, double*, const double*, void*, double*, cudaStream_t);
+
+}  // namespace sadi

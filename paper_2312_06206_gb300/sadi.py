@@ -1,0 +1,160 @@
+"""Thin ctypes binding of the S-ADI C ABI (include/sadi.h).
+
+Argument marshalling only: every numerical step runs inside libsadi.so.  The
+library is loaded from this package directory; if it is missing the import of
+this module fails loudly (there is no fallback).
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsadi.so")
+
+SADI_OK, SADI_EINVAL, SADI_ENOMEM, SADI_ECUDA, SADI_ENOTSPD, SADI_ESTATE, SADI_ETIMEOUT, \
+    SADI_ENONFINITE, SADI_EUNSUPPORTED = range(9)
+STATUS_NAMES = {0: "SADI_OK", 1: "SADI_EINVAL", 2: "SADI_ENOMEM", 3: "SADI_ECUDA", 4: "SADI_ENOTSPD",
+                5: "SADI_ESTATE", 6: "SADI_ETIMEOUT", 7: "SADI_ENONFINITE", 8: "SADI_EUNSUPPORTED"}
+SADI_G_ZERO, SADI_G_NEG_CUBE, SADI_G_NEG_SIN = 0, 1, 2
+SADI_PREC_FP64, SADI_PREC_FP32 = 0, 1
+
+# every symbol include/sadi.h declares, with its ctypes signature
+_SIGS = {
+    "sadi_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                              C.POINTER(C.c_void_p)]),
+    "sadi_set_options": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "sadi_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sadi_set_initial": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
+    "sadi_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "sadi_get": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
+    "sadi_get_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
+    "sadi_get_setup": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
+    "sadi_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sadi_last_error": (C.c_char_p, [C.c_void_p]),
+    "sadi_destroy": (None, [C.c_void_p]),
+}
+
+
+class SadiError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+def load_library(path: str = LIB_PATH) -> C.CDLL:
+    if not os.path.exists(path):
+        raise RuntimeError(f"libsadi.so not found at {path}: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = C.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    return lib
+
+
+_lib = None
+
+
+def lib() -> C.CDLL:
+    global _lib
+    if _lib is None:
+        _lib = load_library()
+    return _lib
+
+
+def _check(st: int, ctx=None):
+    if st != SADI_OK:
+        msg = lib().sadi_last_error(ctx)
+        raise SadiError(st, msg.decode() if msg else "")
+
+
+def _f64(a, N):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    if a.shape != (N, N):
+        raise ValueError(f"expected shape {(N, N)}, got {a.shape}")
+    return a
+
+
+class Sadi:
+    """One S-ADI instance (wraps a sadi_ctx*)."""
+
+    def __init__(self, N: int, alpha: float, kappa: float, tau: float, domain=(-1.0, 1.0)):
+        self.N = int(N)
+        dom = (C.c_double * 2)(float(domain[0]), float(domain[1]))
+        out = C.c_void_p()
+        st = lib().sadi_create(self.N, float(alpha), float(kappa), float(tau), dom, C.byref(out))
+        _check(st, None)
+        self.ctx = out.value
+
+    # -- C ABI calls, same names -------------------------------------------
+    def sadi_set_options(self, g: int = SADI_G_ZERO, prec: int = SADI_PREC_FP64):
+        _check(lib().sadi_set_options(self.ctx, int(g), int(prec)), self.ctx)
+
+    def sadi_set_stream(self, stream_handle: int | None):
+        _check(lib().sadi_set_stream(self.ctx, C.c_void_p(stream_handle or 0)), self.ctx)
+
+    def sadi_set_initial(self, phi1, phi2=None):
+        p1 = _f64(phi1, self.N)
+        p2 = None if phi2 is None else _f64(phi2, self.N)
+        _check(lib().sadi_set_initial(self.ctx, p1.ctypes.data,
+                                      None if p2 is None else p2.ctypes.data), self.ctx)
+
+    def sadi_step(self, nsteps: int = 1):
+        _check(lib().sadi_step(self.ctx, int(nsteps)), self.ctx)
+
+    def sadi_get(self):
+        u = np.empty((self.N, self.N), dtype=np.float64)
+        n = C.c_longlong()
+        _check(lib().sadi_get(self.ctx, u.ctypes.data, C.byref(n)), self.ctx)
+        return u, int(n.value)
+
+    def sadi_get_device(self, dst_ptr: int, dtype: int):
+        _check(lib().sadi_get_device(self.ctx, C.c_void_p(dst_ptr), int(dtype)), self.ctx)
+
+    def sadi_get_setup(self, which: int):
+        Np, _ = self.sadi_get_info()
+        n = {0: self.N, 1: self.N * self.N, 2: Np, 3: (Np + 1) ** 2}[which]
+        out = np.empty(n, dtype=np.float64)
+        _check(lib().sadi_get_setup(self.ctx, int(which), out.ctypes.data, n), self.ctx)
+        if which == 1:
+            return out.reshape(self.N, self.N)
+        if which == 3:
+            return out.reshape(Np + 1, Np + 1)
+        return out
+
+    def sadi_get_info(self):
+        a, b = C.c_int(), C.c_int()
+        _check(lib().sadi_get_info(self.ctx, C.byref(a), C.byref(b)), self.ctx)
+        return a.value, b.value
+
+    def sadi_last_error(self) -> str:
+        return lib().sadi_last_error(self.ctx).decode()
+
+    def sadi_destroy(self):
+        if getattr(self, "ctx", None):
+            lib().sadi_destroy(self.ctx)
+            self.ctx = None
+
+    # -- conveniences ------------------------------------------------------
+    set_options = sadi_set_options
+    set_stream = sadi_set_stream
+    set_initial = sadi_set_initial
+    step = sadi_step
+    get = sadi_get
+    close = sadi_destroy
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.sadi_destroy()
+
+    def __del__(self):
+        try:
+            self.sadi_destroy()
+        except Exception:
+            pass

@@ -1,0 +1,145 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 CPU oracle.
+
+Tolerances: FP64 path <= 1e-10 relative L2 (element-wise 1e-10 of the max for
+setup tables); FP32 path <= 1e-5 relative L2.  Inputs are seeded and
+synthetic (workloads.py)."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import sadi as O
+from oracle import weights as OW
+from paper_2312_06206_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_06206_gb300 import build
+    build.build()
+    from paper_2312_06206_gb300 import sadi
+    return sadi
+
+
+def _run_gpu(S, N, alpha, kappa, tau, g, phi1, phi2, steps, prec, dom=(-1.0, 1.0)):
+    with S.Sadi(N, alpha, kappa, tau, dom) as s:
+        s.set_options(g, prec)
+        s.set_initial(phi1, phi2)
+        s.step(steps)
+        u, n = s.get()
+    assert n == steps
+    return u
+
+
+# ------------------------------------------------------------- setup -------
+
+@pytest.mark.parametrize("N,alpha", [(1, 1.5), (7, 1.3), (63, 1.5), (100, 1.8), (255, 1.2)])
+def test_setup_tables_match_oracle(S, N, alpha):
+    tau, kappa = 0.01, 1.0
+    with S.Sadi(N, alpha, kappa, tau) as s:
+        Np, r = s.sadi_get_info()
+        a1 = s.sadi_get_setup(0)
+        a2 = s.sadi_get_setup(1)
+        c = s.sadi_get_setup(2)
+        lam = s.sadi_get_setup(3)
+    assert Np >= max(N, 8) and Np & (Np - 1) == 0 and r == Np - N
+    ref1 = OW.riesz_1d(alpha, N)
+    assert np.abs(a1 - ref1).max() <= 1e-13 * np.abs(ref1).max()
+    ref2 = OW.lap2d_trap(alpha, N, OW.trap_grid_size(N))
+    assert np.abs(a2 - ref2).max() <= 1e-13 * np.abs(ref2).max()
+    # generator of the bordered matrix H' = I + s T(a_0..a_{Np-1})
+    h = 2.0 / (N + 1)
+    s_ = kappa * tau ** 2 / (2 * h ** alpha)
+    Hp = np.eye(Np) + s_ * scipy.linalg.toeplitz(OW.riesz_1d(alpha, Np))
+    cref = np.linalg.solve(Hp, np.eye(Np)[:, 0])
+    assert np.abs(c - cref).max() <= 1e-13 * np.abs(cref).max()
+    # symbol of the 2Np x 2Np block-circulant embedding
+    P = 2 * Np
+    dist = np.minimum(np.arange(P), P - np.arange(P))
+    ok = dist <= N - 1
+    dc = np.minimum(dist, N - 1)
+    K = np.where(ok[:, None] & ok[None, :], ref2[dc[:, None], dc[None, :]], 0.0)
+    Lref = np.fft.fft2(K).real[:Np + 1, :Np + 1]
+    assert np.abs(lam - Lref).max() <= 1e-12 * np.abs(Lref).max()
+
+
+# -------------------------------------------------------------- steps -------
+
+def test_config_small_fp64_full_run(S):
+    # N=63, alpha=1.5, kappa=1, tau=1/64, 64 steps, g=-u^3, phi1=exp(-20 r^2)
+    w = WL.small_fp64(63)
+    P = O.Problem(w.N, w.alpha, w.kappa, w.tau, w.a, w.b, w.g)
+    ref = O.run(P, w.phi1, w.phi2, w.steps, tier="direct")
+    u = _run_gpu(S, w.N, w.alpha, w.kappa, w.tau, w.g, w.phi1, w.phi2, w.steps, S.SADI_PREC_FP64)
+    assert O.rel_l2(u, ref) <= 1e-10
+
+
+@pytest.mark.parametrize("N,alpha,g", [(1, 1.5, 1), (2, 1.3, 2), (3, 1.9, 1), (5, 1.5, 0), (7, 1.1, 2),
+                                       (8, 1.6, 1), (9, 1.4, 2), (16, 1.5, 1), (31, 1.7, 2), (33, 1.2, 1),
+                                       (64, 1.5, 2), (100, 1.8, 1), (2, 2.0, 0), (15, 2.0, 1)])
+def test_fp64_step_parity_ragged_sizes(S, N, alpha, g):
+    kappa, tau = 0.9, 0.05
+    phi1 = WL.random_field(N, 11 + N)
+    phi2 = 0.5 * WL.random_field(N, 97 + N)
+    steps = 3
+    P = O.Problem(N, alpha, kappa, tau, -1.0, 1.0, g)
+    ref = O.run(P, phi1, phi2, steps, tier="direct")
+    u = _run_gpu(S, N, alpha, kappa, tau, g, phi1, phi2, steps, S.SADI_PREC_FP64)
+    assert O.rel_l2(u, ref) <= 1e-10, O.rel_l2(u, ref)
+    # element-wise as well
+    assert np.abs(u - ref).max() <= 1e-10 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("N,alpha,g", [(63, 1.5, 1), (100, 1.3, 2), (255, 1.8, 2)])
+def test_fp32_step_parity(S, N, alpha, g):
+    kappa, tau = 1.0, 0.02
+    phi1 = WL.gaussian_bumps(N, 8, 5 + N)
+    phi2 = 0.2 * WL.gaussian(N, 10.0)
+    steps = 10
+    P = O.Problem(N, alpha, kappa, tau, -1.0, 1.0, g)
+    ref = O.run(P, phi1, phi2, steps, tier="fft")
+    u = _run_gpu(S, N, alpha, kappa, tau, g, phi1, phi2, steps, S.SADI_PREC_FP32)
+    assert O.rel_l2(u, ref) <= 1e-5, O.rel_l2(u, ref)
+
+
+def test_full_size_1023_fp64_and_fp32(S):
+    # N=1023, alpha=1.5, kappa=1, tau=1e-3, g=-sin u, 8 seeded bumps: a few
+    # steps against the oracle (FFT tier, itself pinned to the direct tier)
+    w = WL.bumps_1023(1.5, steps=4)
+    P = O.Problem(w.N, w.alpha, w.kappa, w.tau, w.a, w.b, w.g)
+    ref = O.run(P, w.phi1, w.phi2, w.steps, tier="fft")
+    u64 = _run_gpu(S, w.N, w.alpha, w.kappa, w.tau, w.g, w.phi1, w.phi2, w.steps, S.SADI_PREC_FP64)
+    assert O.rel_l2(u64, ref) <= 1e-10, O.rel_l2(u64, ref)
+    u32 = _run_gpu(S, w.N, w.alpha, w.kappa, w.tau, w.g, w.phi1, w.phi2, w.steps, S.SADI_PREC_FP32)
+    assert O.rel_l2(u32, ref) <= 1e-5, O.rel_l2(u32, ref)
+
+
+def test_rerun_is_bitwise_identical_and_symmetric(S):
+    N = 63
+    phi1 = WL.gaussian(N, 12.0)            # symmetric under x <-> y
+    us = [_run_gpu(S, N, 1.6, 1.0, 0.03, 2, phi1, None, 8, S.SADI_PREC_FP64) for _ in range(2)]
+    assert np.array_equal(us[0], us[1])
+    assert np.abs(us[0] - us[0].T).max() <= 1e-13 * np.abs(us[0]).max()
+
+
+def test_state_errors(S):
+    with S.Sadi(15, 1.5, 1.0, 0.1) as s:
+        with pytest.raises(S.SadiError) as ei:
+            s.step(1)
+        assert ei.value.status == S.SADI_ESTATE
+        with pytest.raises(S.SadiError) as ei:
+            s.set_options(7, 0)
+        assert ei.value.status == S.SADI_EINVAL
+        s.set_initial(np.zeros((15, 15)))
+        with pytest.raises(S.SadiError) as ei:
+            s.set_options(0, 1)
+        assert ei.value.status == S.SADI_ESTATE
+        with pytest.raises(S.SadiError):
+            s.step(-1)
+        s.step(0)
+        u, n = s.get()
+        assert n == 0 and not u.any()
