@@ -1,0 +1,405 @@
+#!/usr/bin/env python3
+"""Benchmark of the S-ADI per-time-step hot path on GB300.
+
+Workload (one bench "step" = one S-ADI time step of every instance):
+  N = 1023 interior points per direction on Omega = (-1, 1)^2, kappa = 1,
+  tau = 1e-3, g(u) = -sin u, three instances alpha in {1.2, 1.5, 1.8},
+  phi1 = 8 seeded Gaussian bumps (centres U(-0.6, 0.6)^2, widths U(0.05, 0.2),
+  amplitudes U(-1, 1)), phi2 = 0.  Synthetic, seeded.
+Metric: grid-point updates per second, N^2 * steps * instances / time, for the
+chosen form (FP32 FFTs and sweeps, FP64 setup), with the plain FP64 GS-FFT
+path on the same GPU and the relative L2 difference between the two stated.
+
+Timing: W untimed warm-up steps, then K timed steps; each step is bracketed
+by CUDA events on the launching stream and an L2 flush (a 256 MiB write) runs
+between timed steps, outside the events (the working set, ~30 MB per
+instance, is smaller than L2).  Multi-GPU: every rank advances its own copy
+of the three instances (independent problems, no collective); value = all
+ranks' updates / the slowest rank's time.
+
+--impl reference times the FP64 CPU oracle (the reference arm for this
+paper-only workload) on the host cores: each step is one S-ADI step of one
+instance (cycling through the three alpha), rank 0 only.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+N_DEFAULT = 1023
+ALPHAS = (1.2, 1.5, 1.8)
+KAPPA, TAU = 1.0, 1e-3
+METRIC = "grid-point updates/s (N^2*steps/s)"
+UNIT = "pt/s"
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload(N):
+    from paper_2312_06206_gb300 import workloads as WL
+    phi1 = WL.gaussian_bumps(N, 8, WL.SEED_BASE + 2)
+    return phi1
+
+
+def _config(N, extra=None):
+    cfg = {"workload": f"sadi-step N={N} alpha={{1.2,1.5,1.8}} kappa=1 tau=1e-3 g=-sin(u) "
+                       f"phi1=8 gaussian bumps phi2=0",
+           "N": N, "instances": len(ALPHAS), "alphas": list(ALPHAS), "kappa": KAPPA, "tau": TAU,
+           "g": "-sin(u)", "domain": [-1.0, 1.0]}
+    if extra:
+        cfg.update(extra)
+    return cfg
+
+
+# --------------------------------------------------------------- clocks ------
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        out = {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
+        if self.proc is None:
+            return out
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return out
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = set()
+        for r in rows:
+            for k, nm in enumerate(names):
+                if r[5 + k].lower().startswith("active"):
+                    reasons.add(nm)
+        out.update({"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                    "reasons": sorted(reasons), "samples": len(rows)})
+        return out
+
+
+# --------------------------------------------------------- cpu baseline ------
+
+def cpu_baseline(N, phi1, nsteps=3, alpha=1.5):
+    """The FP64 oracle (FFT tier) as it stands, on the host cores: nsteps
+    S-ADI steps (n >= 1 formula) of one instance; the problem set-up and the
+    n = 0 start step are not timed."""
+    from oracle import sadi as O
+    P = O.Problem(N, alpha, KAPPA, TAU, -1.0, 1.0, O.G_NEG_SIN)
+    import numpy as np
+    u0 = np.array(phi1)
+    u1 = O.step(P, None, u0, True, np.zeros_like(u0), tier="fft")
+    t0 = time.perf_counter()
+    up, uc = u0, u1
+    for _ in range(nsteps):
+        up, uc = uc, O.step(P, up, uc, False, tier="fft")
+    dt = time.perf_counter() - t0
+    return {"value": N * N * nsteps / dt, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"{nsteps} S-ADI steps (n>=1) of one instance (alpha={alpha}) of the N={N} workload; "
+                      "oracle FFT tier (numpy FFT convolution + LAPACK Cholesky sweeps, FP64), "
+                      "default BLAS threading", "seconds": dt}, (u0, u1, uc)
+
+
+# --------------------------------------------------------- reference arm -----
+
+def run_reference(a):
+    ws, rank, _ = _dist()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import sadi as O
+    N = a.N
+    phi1 = _workload(N)
+    probs = [O.Problem(N, al, KAPPA, TAU, -1.0, 1.0, O.G_NEG_SIN) for al in ALPHAS]
+    states = []
+    for P in probs:
+        u0 = phi1.copy()
+        u1 = O.step(P, None, u0, True, np.zeros_like(u0), tier="fft")
+        states.append([u0, u1])
+
+    def one(k):
+        i = k % len(probs)
+        up, uc = states[i]
+        states[i] = [uc, O.step(probs[i], up, uc, False, tier="fft")]
+    for k in range(a.warmup):
+        one(k)
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        one(a.warmup + k)
+    dt = time.perf_counter() - t0
+    val = N * N * a.steps / dt
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": _config(N, {"reference": "FP64 CPU oracle (FFT tier); one step = one S-ADI step of one "
+                                               "instance, cycling alpha"}),
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{a.steps} single-instance S-ADI steps at N={N}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+# ------------------------------------------------------------- our arm -------
+
+def algorithmic(N, Np, es):
+    """Per-launch algorithmic work of each kernel (one instance), for the
+    roofline: (bytes, flops).  FFT flops are the nominal 5 L log2 L of a
+    complex FFT of length L."""
+    cs = 2 * es
+    fft = 5.0 * Np * math.log2(Np)
+    return {
+        "k_rows_r2c": (N * N * es + N * Np * cs, N * fft),
+        "k_cols_conv": (2 * N * Np * cs + 2 * Np * Np * es, Np * 4 * fft),
+        "k_rows_solve": (N * Np * cs + 2 * N * N * es, N * 5 * fft),
+        "k_cols_solve": (4 * N * N * es, N * 4 * fft),
+    }
+
+
+def main():
+    a = _args()
+    if a.impl == "reference":
+        return run_reference(a)
+    ws, rank, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2312_06206_gb300 import build
+    build.build()
+    from paper_2312_06206_gb300 import sadi as S
+    N = a.N
+    phi1 = _workload(N)
+    # a dedicated stream (the legacy default stream has handle 0, which the
+    # library reads as "use the context's own stream")
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    def make(prec):
+        ctxs = []
+        for al in ALPHAS:
+            s = S.Sadi(N, al, KAPPA, TAU, (-1.0, 1.0))
+            s.set_options(S.SADI_G_NEG_SIN, prec)
+            s.set_stream(stream.cuda_stream)
+            s.set_initial(phi1, None)
+            ctxs.append(s)
+        return ctxs
+
+    def timed(ctxs, K, W, profile=False):
+        for _ in range(W):
+            for s in ctxs:
+                s.step(1)
+        if profile:
+            for s in ctxs:
+                s.sadi_profile(True)
+        barrier()
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        for k in range(K):
+            flush.zero_()
+            evs[k][0].record(stream)
+            for s in ctxs:
+                s.step(1)
+            evs[k][1].record(stream)
+        barrier()
+        ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+        phases = None
+        if profile:
+            tot = [0.0] * 4
+            nst = 0
+            for s in ctxs:
+                p, n = s.sadi_get_phase_times()
+                s.sadi_profile(False)
+                tot = [x + y for x, y in zip(tot, p)]
+                nst += n
+            phases = ([t / nst for t in tot], nst)
+        return ms, phases
+
+    # plain FP64 GS-FFT path
+    sampler = ClockSampler(local)
+    sampler.start()
+    c64 = make(S.SADI_PREC_FP64)
+    K64 = max(1, min(a.steps, 20))
+    ms64, _ = timed(c64, K64, a.warmup)
+    # chosen form: FP32 FFTs and sweeps
+    c32 = make(S.SADI_PREC_FP32)
+    ms32, _ = timed(c32, a.steps, a.warmup)
+    clocks = sampler.stop()
+    # accuracy of the chosen form against the plain FP64 path after the same
+    # number of steps from the same data
+    extra = a.warmup + a.steps - (a.warmup + K64)
+    for _ in range(max(0, extra)):
+        for s in c64:
+            s.step(1)
+    rels = []
+    for s64, s32 in zip(c64, c32):
+        u64, n64 = s64.get()
+        u32, n32 = s32.get()
+        assert n64 == n32
+        rels.append(float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)))
+    nsteps_cmp = n32
+    # per-kernel timing (separate profiled pass) for the roofline
+    Kp = max(5, min(a.steps, 20))
+    _, (phase_ms, _) = timed(c32, Kp, 0, profile=True)
+    names = ["k_rows_r2c", "k_cols_conv", "k_rows_solve", "k_cols_solve"]
+    Np = c32[0].sadi_get_info()[0]
+    alg = algorithmic(N, Np, 4)
+    dom = max(range(4), key=lambda k: phase_ms[k])
+    dname = names[dom]
+    dur_s = phase_ms[dom] / 1e3
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6750.0))
+    b_alg, f_alg = alg[dname]
+    ach_tf = f_alg / dur_s / 1e12
+    ach_gbs = b_alg / dur_s / 1e9
+    roofline = {"kernel": dname, "bound": "alu", "achieved": ach_tf, "peak": fp32_peak_tflops,
+                "unit": "TFLOP/s", "frac": ach_tf / fp32_peak_tflops, "traffic": None,
+                "avg_launch_us": phase_ms[dom] * 1e3,
+                "peak_note": f"FP32 FMA peak of measured-max clock: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz",
+                "hbm_view": {"achieved_gbs": ach_gbs, "peak_gbs": hbm_peak, "frac": ach_gbs / hbm_peak},
+                "kernel_us": {n: phase_ms[k] * 1e3 for k, n in enumerate(names)},
+                "kernel_share": {n: phase_ms[k] / sum(phase_ms) for k, n in enumerate(names)}}
+    # e2e through the public API with host buffers: set_initial from pinned
+    # host arrays, then every step sadi_step(1) + sadi_get into pinned host.
+    pin_in = torch.from_numpy(phi1).pin_memory()
+    pin_out = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in ALPHAS]
+    Ke = max(3, min(a.steps, 20))
+    import ctypes
+    lib = S.lib()
+    nll = ctypes.c_longlong()
+    barrier()
+    t0 = time.perf_counter()
+    for s in c32:
+        st = lib.sadi_set_initial(s.ctx, ctypes.c_void_p(pin_in.data_ptr()), None)
+        assert st == 0, s.sadi_last_error()
+    for k in range(Ke):
+        for i, s in enumerate(c32):
+            assert lib.sadi_step(s.ctx, 1) == 0
+            assert lib.sadi_get(s.ctx, ctypes.c_void_p(pin_out[i].data_ptr()), ctypes.byref(nll)) == 0
+    dt_e2e = time.perf_counter() - t0
+    barrier()
+    h2d = len(ALPHAS) * N * N * 8 / Ke
+    d2h = len(ALPHAS) * N * N * 8
+    # aggregate over ranks (max time)
+    t32 = torch.tensor([ms32, ms64, dt_e2e], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t32, op=torch.distributed.ReduceOp.MAX)
+    ms32m, ms64m, e2em = [float(x) for x in t32.tolist()]
+    pts = N * N * len(ALPHAS)
+    value = ws * pts * a.steps / (ms32m / 1e3)
+    value64 = ws * pts * K64 / (ms64m / 1e3)
+    e2e_val = ws * pts * Ke / e2em
+    if rank == 0:
+        cpu = None
+        rel_oracle = None
+        if ws == 1 and not a.no_cpu_baseline:
+            cpu, (u0, u1, uK) = cpu_baseline(N, phi1)
+            # FP64 GPU path vs the oracle after the same 1 + 3 steps (alpha=1.5)
+            with S.Sadi(N, 1.5, KAPPA, TAU, (-1.0, 1.0)) as s:
+                s.set_options(S.SADI_G_NEG_SIN, S.SADI_PREC_FP64)
+                s.set_initial(phi1, None)
+                s.step(4)
+                ug, _ = s.get()
+                rel_oracle = float(np.linalg.norm(ug - uK) / np.linalg.norm(uK))
+            with S.Sadi(N, 1.5, KAPPA, TAU, (-1.0, 1.0)) as s:
+                s.set_options(S.SADI_G_NEG_SIN, S.SADI_PREC_FP32)
+                s.set_initial(phi1, None)
+                s.step(4)
+                ug32, _ = s.get()
+                rel_oracle32 = float(np.linalg.norm(ug32 - uK) / np.linalg.norm(uK))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms32m / a.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": _config(N, {"form": "FP32 FFT/sweeps, FP64 setup", "parallelism": f"replicas x{ws}",
+                                  "l2": "flushed between timed steps (256 MiB write outside the step events)"}),
+            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64m / K64, "steps": K64},
+            "speedup_vs_fp64": value / value64,
+            "rel_l2_fp32_vs_fp64": max(rels), "rel_l2_steps": nsteps_cmp,
+            "rel_l2_vs_oracle_4steps": None if rel_oracle is None else
+            {"fp64": rel_oracle, "fp32": rel_oracle32, "alpha": 1.5},
+            "roofline": roofline,
+            "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "how": "C ABI with pinned host buffers: sadi_set_initial once, then per step sadi_step(1) + "
+                           "sadi_get of u^{n+1} for each instance; wall clock"},
+            "gpu_launches": 4 * len(ALPHAS) * a.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for s in c64 + c32:
+        s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

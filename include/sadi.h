@@ -115,6 +115,32 @@ sadi_status sadi_get_setup(sadi_ctx *ctx, int which, double *out, size_t count);
  * be NULL. */
 sadi_status sadi_get_info(const sadi_ctx *ctx, int *fft_len, int *border_rank);
 
+/* Work decomposition of the four step kernels for the precision currently
+ * selected: grid rows per block of the row kernels, spectrum slots per block
+ * of the column convolution (a divisor of N'), grid columns per block of the
+ * y sweep.  All zero restores the defaults.  Invalid combinations (shared
+ * memory above 227 KB per block, or more rows than the row kernel stages)
+ * return SADI_EINVAL and leave the setting unchanged.  Results do not depend
+ * on the tiles (bitwise). Call after sadi_set_options. */
+sadi_status sadi_set_tiles(sadi_ctx *ctx, int rows, int conv_cols, int solve_cols);
+
+/* Current tiles of the selected precision: tiles[0..2] = rows, conv_cols,
+ * solve_cols. */
+sadi_status sadi_get_tiles(const sadi_ctx *ctx, int tiles[3]);
+
+/* Per-kernel timing (a tracing aid).  enable != 0: every later step records
+ * CUDA events on the context's stream around each of its four kernels
+ * (0 row FFT, 1 column convolution, 2 row inverse FFT + RHS + x sweep,
+ * 3 y sweep + leapfrog); enable = 0 stops recording.  Recording adds event
+ * records between the kernels, so time throughput with it disabled. */
+sadi_status sadi_profile(sadi_ctx *ctx, int enable);
+
+/* Wait for the context's stream, then return in ms[4] the milliseconds
+ * accumulated per kernel since the last call (or since sadi_profile), and
+ * in *nsteps (may be NULL) the number of steps they cover; resets the
+ * accumulators. */
+sadi_status sadi_get_phase_times(sadi_ctx *ctx, double ms[4], long long *nsteps);
+
 /* Last error message of ctx ("" if none).  ctx may be NULL: then the message
  * of the last failed sadi_create on this thread is returned. */
 const char *sadi_last_error(const sadi_ctx *ctx);

@@ -11,20 +11,29 @@
 // spectra lambda_c, lambda_s of Algorithm 1) is stored in the same bit-reversed
 // order, no reordering pass is ever needed.
 //
-// Stages: radix 8 (three radix-2 levels fused in registers), plus one radix-2
-// or radix-4 stage for log2 L not divisible by 3 (outermost span in DIF,
-// innermost-last in DIT).  The radix-2 cascade inside a butterfly leaves
-// register p holding the DFT output brev_R(p), so storing register p to slot p
-// makes the whole DIF produce exactly the bit-reversal permutation.
+// Stages (the "plan"): radix 8 (three radix-2 levels fused in registers),
+// plus one radix-2 or radix-4 stage when log2 L is not a multiple of 3; in the
+// DIF order the odd stage comes first (span L), then radix-8 stages down to
+// span 8; DIT runs the same stages in reverse.  The radix-2 cascade inside a
+// butterfly leaves register p holding DFT output brev_R(p), so storing
+// register p to slot p makes the whole DIF produce the bit-reversal
+// permutation.
+//
+// Fusion: the last DIF stage (span 8) and the first DIT stage (span 8) act on
+// the same 8 consecutive elements, and so do the last DIT stage and the first
+// DIF stage (span L); a pointwise multiply between a forward and an inverse
+// transform (or between an inverse and a forward one) is therefore done in
+// registers by one thread with no shared-memory round trip (fused8 / fusedL).
+//
+// Twiddles: per-stage tables, laid out [(q-1) * (S/R) + j] for register q of
+// butterfly j of the stage with span S, so that the threads of a warp read
+// consecutive addresses.  A separate table tw[k] = exp(-2 pi i k / P), P = 2L,
+// provides the exp(-i pi k / L) twist of Algorithm 1 and the packing factors.
 //
 // Shared-memory layout: element i of a vector lives at i + (i >> 3) (one pad
-// slot per 8 elements), which spreads the stride-8 accesses of the last DIF /
-// first DIT stage over all banks.  A buffer of nvec vectors uses
-// nvec * vec_stride(L) elements.
-//
-// Twiddles come from one table tw[k] = exp(-2 pi i k / P), 0 <= k < P, with
-// P = 2L (the same table provides the exp(-i pi k / L) twist of Algorithm 1
-// and the exp(-2 pi i k / 2L) factors of the real/complex packing).
+// slot per 8 elements), which spreads the stride-8 accesses of the span-8
+// stages over all banks.  A buffer of nvec vectors uses nvec * vec_stride(L)
+// elements.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -56,11 +65,78 @@ template <typename V> __device__ __forceinline__ V cmul_mi(V a) { return mkc(a.y
 // multiply by +i
 template <typename V> __device__ __forceinline__ V cmul_pi(V a) { return mkc(-a.y, a.x); }
 
+// multiply by a real or a complex factor
+__device__ __forceinline__ float2 cmulany(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__device__ __forceinline__ double2 cmulany(double2 a, double s) { return make_double2(a.x * s, a.y * s); }
+__device__ __forceinline__ float2 cmulany(float2 a, float2 b) { return cmul(a, b); }
+__device__ __forceinline__ double2 cmulany(double2 a, double2 b) { return cmul(a, b); }
+
 __host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 3); }
 __host__ __device__ __forceinline__ int vec_stride(int L) { return L + (L >> 3) + 2; }
 
 __device__ __forceinline__ int brev(int p, int logL) {
   return (int)(__brev((unsigned)p) >> (32 - logL));
+}
+
+// Stage plan of a length-2^logL transform in DIF order.
+struct FftPlan {
+  int n;          // number of stages
+  int logS[8];    // log2 span
+  int logR[8];    // log2 radix (1, 2 or 3)
+  int off[8];     // offset of the stage's twiddle sub-table
+  int total;      // twiddle entries
+};
+
+__host__ __device__ inline FftPlan fft_plan(int logL) {
+  FftPlan p;
+  p.n = 0;
+  int logS = logL, off = 0;
+  const int rem = logL % 3;
+  if (rem) {
+    p.logS[0] = logL;
+    p.logR[0] = rem;
+    p.off[0] = 0;
+    off += ((1 << rem) - 1) << (logL - rem);
+    p.n = 1;
+    logS -= rem;
+  }
+  while (logS >= 3) {
+    p.logS[p.n] = logS;
+    p.logR[p.n] = 3;
+    p.off[p.n] = off;
+    off += 7 << (logS - 3);
+    p.n++;
+    logS -= 3;
+  }
+  p.total = off;
+  return p;
+}
+
+// Stage s of the plan, computed arithmetically (no local arrays):
+// the odd stage (if any) first, then radix-8 stages k = 0, 1, ... with span
+// 2^(logL - rem - 3k) and twiddle offset base + 2^(logL-rem) - 2^(logL-rem-3k).
+struct Stage {
+  int logS, logR, off;
+};
+__host__ __device__ __forceinline__ int plan_stages(int logL) {
+  const int rem = logL % 3;
+  return (rem ? 1 : 0) + (logL - rem) / 3;
+}
+__host__ __device__ __forceinline__ Stage plan_stage(int logL, int s) {
+  const int rem = logL % 3;
+  Stage st;
+  if (rem && s == 0) {
+    st.logS = logL;
+    st.logR = rem;
+    st.off = 0;
+    return st;
+  }
+  const int k = s - (rem ? 1 : 0);
+  const int base = rem ? (((1 << rem) - 1) << (logL - rem)) : 0;
+  st.logS = logL - rem - 3 * k;
+  st.logR = 3;
+  st.off = base + (1 << (logL - rem)) - (1 << (logL - rem - 3 * k));
+  return st;
 }
 
 template <typename T> __device__ __forceinline__ T rsqrt2();
@@ -147,30 +223,25 @@ __device__ __forceinline__ void bfly8(cx<T>* x) {
   }
 }
 
-__device__ __forceinline__ int brev_small(int p, int logR) {
-  // bit reversal of p in logR bits (logR <= 3)
-  return logR == 1 ? p : logR == 2 ? (((p & 1) << 1) | (p >> 1))
-                                   : (((p & 1) << 2) | (p & 2) | (p >> 2));
-}
-
-template <typename T, int R>
-__device__ __forceinline__ void bfly(cx<T>* x, bool fwd) {
+template <typename T, int R, bool FWD>
+__device__ __forceinline__ void bfly(cx<T>* x) {
   if (R == 2) bfly2<T>(x);
-  else if (R == 4) { if (fwd) bfly4<T, true>(x); else bfly4<T, false>(x); }
-  else { if (fwd) bfly8<T, true>(x); else bfly8<T, false>(x); }
+  else if (R == 4) bfly4<T, FWD>(x);
+  else bfly8<T, FWD>(x);
 }
 
+// ---------------------------------------------------------------------------
 // One radix-R stage over nvec vectors of length L (span S, stride m = S/R).
-// tw: table of exp(-2 pi i k / P); twshift = log2(P / S).
+// stw: this stage's twiddle sub-table.
+// ---------------------------------------------------------------------------
 template <typename T, int R, bool FWD>
 __device__ __forceinline__ void fft_stage(cx<T>* __restrict__ buf, int logL, int logS, int nvec, int vstride,
-                                          const cx<T>* __restrict__ tw, int logP) {
+                                          const cx<T>* __restrict__ stw) {
   constexpr int logR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
   const int logm = logS - logR;
   const int m = 1 << logm;
   const int lognb = logL - logR;           // butterflies per vector = L / R
   const int total = nvec << lognb;
-  const int twshift = logP - logS;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int v = t >> lognb;
     const int u = t & ((1 << lognb) - 1);
@@ -182,47 +253,123 @@ __device__ __forceinline__ void fft_stage(cx<T>* __restrict__ buf, int logL, int
     for (int q = 0; q < R; ++q) x[q] = p[padi(base + (q << logm))];
     if (!FWD && j != 0) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], __ldg(&tw[(j * brev_small(q, logR)) << twshift]));
+      for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], __ldg(&stw[((q - 1) << logm) + j]));
     }
-    if (FWD) bfly<T, R>(x, true); else bfly<T, R>(x, false);
+    bfly<T, R, FWD>(x);
     if (FWD && j != 0) {
 #pragma unroll
-      for (int q = 1; q < R; ++q) x[q] = cmul(x[q], __ldg(&tw[(j * brev_small(q, logR)) << twshift]));
+      for (int q = 1; q < R; ++q) x[q] = cmul(x[q], __ldg(&stw[((q - 1) << logm) + j]));
     }
 #pragma unroll
     for (int q = 0; q < R; ++q) p[padi(base + (q << logm))] = x[q];
   }
 }
 
-// Forward DIF FFT (natural -> bit-reversed) of nvec vectors; ends with a
-// __syncthreads().  Must be called by every thread of the block, with the
-// input already visible (caller synchronised).
-template <typename T>
-__device__ void fft_dif(cx<T>* buf, int logL, int nvec, int vstride, const cx<T>* tw, int logP) {
-  int logS = logL;
-  const int rem = logL % 3;
-  if (rem == 1) { fft_stage<T, 2, true>(buf, logL, logS, nvec, vstride, tw, logP); logS -= 1; __syncthreads(); }
-  else if (rem == 2) { fft_stage<T, 4, true>(buf, logL, logS, nvec, vstride, tw, logP); logS -= 2; __syncthreads(); }
-  while (logS >= 3) {
-    fft_stage<T, 8, true>(buf, logL, logS, nvec, vstride, tw, logP);
-    logS -= 3;
-    __syncthreads();
-  }
+template <typename T, bool FWD>
+__device__ __forceinline__ void run_stage(int logL, int s, cx<T>* buf, int nvec, int vs, const cx<T>* stw) {
+  const Stage st = plan_stage(logL, s);
+  if (st.logR == 3) fft_stage<T, 8, FWD>(buf, logL, st.logS, nvec, vs, stw + st.off);
+  else if (st.logR == 2) fft_stage<T, 4, FWD>(buf, logL, st.logS, nvec, vs, stw + st.off);
+  else fft_stage<T, 2, FWD>(buf, logL, st.logS, nvec, vs, stw + st.off);
+  __syncthreads();
 }
 
-// Inverse DIT FFT (bit-reversed -> natural), unnormalised; ends with a
-// __syncthreads().
+// Forward DIF FFT stages [s0, s1) of the plan; every stage ends with a
+// __syncthreads().  Must be called by every thread of the block.
 template <typename T>
-__device__ void fft_dit(cx<T>* buf, int logL, int nvec, int vstride, const cx<T>* tw, int logP) {
-  const int rem = logL % 3;
-  int logS = 3;
-  while (logS <= logL - rem) {
-    fft_stage<T, 8, false>(buf, logL, logS, nvec, vstride, tw, logP);
-    logS += 3;
-    __syncthreads();
+__device__ void dif_stages(cx<T>* buf, int logL, int nvec, int vs, const cx<T>* stw, int s0, int s1) {
+  for (int s = s0; s < s1; ++s) run_stage<T, true>(logL, s, buf, nvec, vs, stw);
+}
+// Inverse DIT FFT stages, DIF-order indices s1-1 down to s0.
+template <typename T>
+__device__ void dit_stages(cx<T>* buf, int logL, int nvec, int vs, const cx<T>* stw, int s0, int s1) {
+  for (int s = s1 - 1; s >= s0; --s) run_stage<T, false>(logL, s, buf, nvec, vs, stw);
+}
+
+template <typename T>
+__device__ void fft_dif(cx<T>* buf, int logL, int nvec, int vs, const cx<T>* stw) {
+  dif_stages<T>(buf, logL, nvec, vs, stw, 0, plan_stages(logL));
+}
+template <typename T>
+__device__ void fft_dit(cx<T>* buf, int logL, int nvec, int vs, const cx<T>* stw) {
+  dit_stages<T>(buf, logL, nvec, vs, stw, 0, plan_stages(logL));
+}
+
+// ---------------------------------------------------------------------------
+// fused8: last DIF stage (span 8) -> multiply by mult[v * mstride + p] ->
+// first DIT stage (span 8), in registers (span-8 stages have no twiddles).
+// Requires a plan with >= 2 stages (L >= 16).  Ends with __syncthreads().
+// ---------------------------------------------------------------------------
+template <typename T, typename M>
+__device__ void fused8(cx<T>* __restrict__ buf, int logL, int nvec, int vs, const M* __restrict__ mult,
+                       int mstride) {
+  const int lognb = logL - 3;
+  const int total = nvec << lognb;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int v = t >> lognb;
+    const int base = (t & ((1 << lognb) - 1)) << 3;
+    cx<T>* p = buf + v * vs + padi(base);     // 8 consecutive elements share one pad group
+    const M* mm = mult + (size_t)v * mstride + base;
+    cx<T> x[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = p[q];
+    bfly8<T, true>(x);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) x[q] = cmulany(x[q], __ldg(&mm[q]));
+    bfly8<T, false>(x);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) p[q] = x[q];
   }
-  if (rem == 1) { fft_stage<T, 2, false>(buf, logL, logL, nvec, vstride, tw, logP); __syncthreads(); }
-  else if (rem == 2) { fft_stage<T, 4, false>(buf, logL, logL, nvec, vstride, tw, logP); __syncthreads(); }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// fusedL: last DIT stage (span L) -> multiply natural position k by
+// conj(tw[k]) -> first DIF stage (span L), in registers.  Requires >= 2 stages.
+// Ends with __syncthreads().
+// ---------------------------------------------------------------------------
+template <typename T, int R>
+__device__ void fusedL_impl(cx<T>* __restrict__ buf, int logL, int nvec, int vs, const cx<T>* __restrict__ stw,
+                            const cx<T>* __restrict__ tw) {
+  constexpr int logR = (R == 2) ? 1 : (R == 4) ? 2 : 3;
+  const int logm = logL - logR;
+  const int m = 1 << logm;
+  const int total = nvec << logm;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int v = t >> logm;
+    const int j = t & (m - 1);
+    cx<T>* p = buf + v * vs;
+    cx<T> x[R];
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = p[padi(j + (q << logm))];
+    cx<T> w[R];
+    w[0] = mkc(T(1), T(0));
+#pragma unroll
+    for (int q = 1; q < R; ++q) w[q] = __ldg(&stw[((q - 1) << logm) + j]);
+    if (j != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], w[q]);
+    }
+    bfly<T, R, false>(x);
+#pragma unroll
+    for (int q = 0; q < R; ++q) x[q] = cmulc(x[q], __ldg(&tw[j + (q << logm)]));
+    bfly<T, R, true>(x);
+    if (j != 0) {
+#pragma unroll
+      for (int q = 1; q < R; ++q) x[q] = cmul(x[q], w[q]);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) p[padi(j + (q << logm))] = x[q];
+  }
+  __syncthreads();
+}
+
+template <typename T>
+__device__ void fusedL(cx<T>* buf, int logL, int nvec, int vs, const cx<T>* stw, const cx<T>* tw) {
+  const int lr = plan_stage(logL, 0).logR;
+  if (lr == 3) fusedL_impl<T, 8>(buf, logL, nvec, vs, stw, tw);
+  else if (lr == 2) fusedL_impl<T, 4>(buf, logL, nvec, vs, stw, tw);
+  else fusedL_impl<T, 2>(buf, logL, nvec, vs, stw, tw);
 }
 
 }  // namespace sadi

@@ -5,7 +5,9 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <array>
 #include <string>
+#include <vector>
 
 #include "../../include/sadi.h"
 #include "fft.cuh"
@@ -28,6 +30,9 @@ struct sadi_ctx {
   double* lnat = nullptr;    // (Np+1)^2
   double2* tw64 = nullptr;   // P
   float2* tw32 = nullptr;    // P
+  double2* stw64 = nullptr;  // per-stage FFT twiddles
+  float2* stw32 = nullptr;
+  Tiles tiles64{}, tiles32{};
   double* lpb64 = nullptr;   // (Np+1) 2 Np
   float* lpb32 = nullptr;
   double2* lamc64 = nullptr;
@@ -47,6 +52,12 @@ struct sadi_ctx {
   bool initialized = false;
   bool broken = false;
   std::string err;
+  // per-kernel timing (sadi_profile)
+  bool profiling = false;
+  std::vector<std::array<cudaEvent_t, 5>> ev_pool;   // recorded, not yet folded
+  std::vector<std::array<cudaEvent_t, 5>> ev_free;
+  double phase_ms[4] = {0, 0, 0, 0};
+  long long phase_steps = 0;
 };
 
 static thread_local std::string g_create_err;
@@ -81,12 +92,36 @@ T* dalloc(size_t n, cudaError_t* e) {
 }
 
 void free_all(sadi_ctx* c) {
-  void* ptrs[] = {c->a1,     c->a2d,    c->cgen,   c->lnat,   c->tw64,   c->tw32, c->lpb64,
+  void* ptrs[] = {c->stw64, c->stw32, c->a1,     c->a2d,    c->cgen,   c->lnat,   c->tw64,   c->tw32, c->lpb64,
                   c->lpb32,  c->lamc64, c->lams64, c->lamc32, c->lams32, c->G64,  c->G32,
                   c->ubuf[0], c->ubuf[1], c->phi2, c->S,      c->W,      c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  for (auto& a : c->ev_pool)
+    for (auto e : a) cudaEventDestroy(e);
+  for (auto& a : c->ev_free)
+    for (auto e : a) cudaEventDestroy(e);
+  c->ev_pool.clear();
+  c->ev_free.clear();
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
+}
+
+// Fold recorded per-kernel events into the accumulators (waits for them).
+cudaError_t fold_events(sadi_ctx* c) {
+  for (auto& a : c->ev_pool) {
+    cudaError_t e = cudaEventSynchronize(a[4]);
+    if (e != cudaSuccess) return e;
+    for (int k = 0; k < 4; ++k) {
+      float ms = 0.f;
+      e = cudaEventElapsedTime(&ms, a[k], a[k + 1]);
+      if (e != cudaSuccess) return e;
+      c->phase_ms[k] += ms;
+    }
+    c->phase_steps += 1;
+    c->ev_free.push_back(a);
+  }
+  c->ev_pool.clear();
+  return cudaSuccess;
 }
 
 int log2i(int v) {
@@ -176,6 +211,8 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
       {(void**)&c->lnat, sizeof(double) * (size_t)(Np + 1) * (Np + 1)},
       {(void**)&c->tw64, sizeof(double2) * P},
       {(void**)&c->tw32, sizeof(float2) * P},
+      {(void**)&c->stw64, sizeof(double2) * fft_plan(g.logNp).total},
+      {(void**)&c->stw32, sizeof(float2) * fft_plan(g.logNp).total},
       {(void**)&c->lpb64, sizeof(double) * nlpb},
       {(void**)&c->lpb32, sizeof(float) * nlpb},
       {(void**)&c->lamc64, sizeof(double2) * Np},
@@ -195,14 +232,15 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
   }
   cudaStream_t st = c->stream;
   if ((e = launch_twiddles(c->tw64, c->tw32, P, st))) return bail(cuda_fail(c, e, "twiddles"));
+  if ((e = launch_stage_twiddles(c->stw64, c->stw32, g.logNp, st))) return bail(cuda_fail(c, e, "stage twiddles"));
   if ((e = launch_riesz1d(c->a1, Np, alpha, st))) return bail(cuda_fail(c, e, "riesz weights"));
   const int M = (8 * Np > 1024) ? 8 * Np : 1024;
-  if ((e = run_weights2d(c->a2d, g, alpha, M, c->tw64, st))) return bail(cuda_fail(c, e, "2D weights"));
+  if ((e = run_weights2d(c->a2d, g, alpha, M, c->stw64, st))) return bail(cuda_fail(c, e, "2D weights"));
   const double scale = -kappa * tau * tau * std::pow(c->h, -alpha) / ((double)P * (double)Np);
-  if ((e = run_lambda(c->a2d, g, c->tw64, scale, c->lnat, c->lpb64, c->lpb32, st)))
+  if ((e = run_lambda(c->a2d, g, c->stw64, c->tw64, scale, c->lnat, c->lpb64, c->lpb32, st)))
     return bail(cuda_fail(c, e, "symbol"));
   int gstat = 1;
-  if ((e = run_generator(c->a1, g, c->s, c->tw64, c->cgen, c->lamc64, c->lams64, c->lamc32, c->lams32, c->G64,
+  if ((e = run_generator(c->a1, g, c->s, c->stw64, c->tw64, c->cgen, c->lamc64, c->lams64, c->lamc32, c->lams32, c->G64,
                          c->G32, &gstat, st)))
     return bail(cuda_fail(c, e, "generator"));
   if (gstat != 0) {
@@ -211,6 +249,8 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
   }
   if ((e = step_setup_attributes<float>())) return bail(cuda_fail(c, e, "kernel attributes"));
   if ((e = step_setup_attributes<double>())) return bail(cuda_fail(c, e, "kernel attributes"));
+  c->tiles64 = default_tiles<double>(Np);
+  c->tiles32 = default_tiles<float>(Np);
   sadi_status sst = alloc_state(c);
   if (sst != SADI_OK) return bail(sst);
   if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "setup"));
@@ -277,19 +317,31 @@ sadi_status sadi_step(sadi_ctx* c, int nsteps) {
   if (nsteps < 0) return fail(c, SADI_EINVAL, "nsteps must be >= 0");
   for (int it = 0; it < nsteps; ++it) {
     RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0};
+    cudaEvent_t* ev = nullptr;
+    if (c->profiling) {
+      if (c->ev_pool.size() >= 512) CK(fold_events(c), "profile events");
+      if (c->ev_free.empty()) {
+        std::array<cudaEvent_t, 5> a{};
+        for (auto& e : a) CK(cudaEventCreate(&e), "cudaEventCreate");
+        c->ev_free.push_back(a);
+      }
+      c->ev_pool.push_back(c->ev_free.back());
+      c->ev_free.pop_back();
+      ev = c->ev_pool.back().data();
+    }
     void* ucur = c->ubuf[c->cur];
     void* uoth = c->ubuf[1 - c->cur];
     cudaError_t e;
     if (c->prec == SADI_PREC_FP64) {
-      StepTables<double> tb{c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
-      e = launch_step<double>(c->g, tb, rp, static_cast<const double*>(ucur), static_cast<const double*>(uoth),
+      StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
+      e = launch_step<double>(c->g, tb, c->tiles64, rp, static_cast<const double*>(ucur), static_cast<const double*>(uoth),
                               static_cast<double*>(uoth), static_cast<const double*>(c->phi2), c->S,
-                              static_cast<double*>(c->W), c->stream);
+                              static_cast<double*>(c->W), c->stream, ev);
     } else {
-      StepTables<float> tb{c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
-      e = launch_step<float>(c->g, tb, rp, static_cast<const float*>(ucur), static_cast<const float*>(uoth),
+      StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+      e = launch_step<float>(c->g, tb, c->tiles32, rp, static_cast<const float*>(ucur), static_cast<const float*>(uoth),
                              static_cast<float*>(uoth), static_cast<const float*>(c->phi2), c->S,
-                             static_cast<float*>(c->W), c->stream);
+                             static_cast<float*>(c->W), c->stream, ev);
     }
     if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
     c->cur = 1 - c->cur;
@@ -359,6 +411,54 @@ sadi_status sadi_get_info(const sadi_ctx* c, int* fft_len, int* border_rank) {
   if (!c) return SADI_EINVAL;
   if (fft_len) *fft_len = c->g.Np;
   if (border_rank) *border_rank = c->g.r;
+  return SADI_OK;
+}
+
+sadi_status sadi_set_tiles(sadi_ctx* c, int rows, int conv_cols, int solve_cols) {
+  if (!c) return SADI_EINVAL;
+  Tiles t{rows, conv_cols, solve_cols};
+  const bool f64 = c->prec == SADI_PREC_FP64;
+  if (rows == 0 && conv_cols == 0 && solve_cols == 0)
+    t = f64 ? default_tiles<double>(c->g.Np) : default_tiles<float>(c->g.Np);
+  const bool ok = f64 ? tiles_valid<double>(c->g, t) : tiles_valid<float>(c->g, t);
+  if (!ok) return fail(c, SADI_EINVAL, "tile sizes invalid for this N and precision");
+  if (f64) c->tiles64 = t;
+  else c->tiles32 = t;
+  return SADI_OK;
+}
+
+sadi_status sadi_get_tiles(const sadi_ctx* c, int tiles[3]) {
+  if (!c || !tiles) return SADI_EINVAL;
+  const Tiles& t = c->prec == SADI_PREC_FP64 ? c->tiles64 : c->tiles32;
+  tiles[0] = t.rows;
+  tiles[1] = t.conv_cols;
+  tiles[2] = t.solve_cols;
+  return SADI_OK;
+}
+
+sadi_status sadi_profile(sadi_ctx* c, int enable) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (enable && !c->profiling) {
+    CK(fold_events(c), "profile events");
+    for (double& v : c->phase_ms) v = 0.0;
+    c->phase_steps = 0;
+  }
+  c->profiling = enable != 0;
+  return SADI_OK;
+}
+
+sadi_status sadi_get_phase_times(sadi_ctx* c, double ms[4], long long* nsteps) {
+  if (!c) return SADI_EINVAL;
+  if (!ms) return fail(c, SADI_EINVAL, "ms is NULL");
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  CK(fold_events(c), "profile events");
+  for (int k = 0; k < 4; ++k) {
+    ms[k] = c->phase_ms[k];
+    c->phase_ms[k] = 0.0;
+  }
+  if (nsteps) *nsteps = c->phase_steps;
+  c->phase_steps = 0;
   return SADI_OK;
 }
 

@@ -25,19 +25,23 @@ struct RhsParams {
 
 // ---- setup (FP64), setup_kernels.cu ----------------------------------------
 cudaError_t launch_twiddles(double2* tw64, float2* tw32, int P, cudaStream_t st);
+// per-stage FFT twiddle tables of the length-2^logL plan (fft_plan)
+cudaError_t launch_stage_twiddles(double2* stw64, float2* stw32, int logL, cudaStream_t st);
 cudaError_t launch_riesz1d(double* a, int n, double alpha, cudaStream_t st);
 // 2D weights a_ij (0 <= i, j < N) by the trapezoid rule on grids M and 2M +
 // one Richardson step.  Scratch is allocated and freed inside.
-cudaError_t run_weights2d(double* a2d, const Geom& g, double alpha, int M, const double2* tw64,
+cudaError_t run_weights2d(double* a2d, const Geom& g, double alpha, int M, const double2* stw64,
                           cudaStream_t st);
 // Symbol of the block-circulant embedding: lnat[(Np+1) x (Np+1)] (unscaled,
 // natural order), and the bit-reversed conv tables lpb (scaled) in FP64/FP32.
-cudaError_t run_lambda(const double* a2d, const Geom& g, const double2* tw64, double scale, double* lnat,
+cudaError_t run_lambda(const double* a2d, const Geom& g, const double2* stw64, const double2* tw64, double scale,
+                       double* lnat,
                        double* lpb64, float* lpb32, cudaStream_t st);
 // Gohberg-Semencul generator of H' = I + s T(a_0..a_{Np-1}): c' (Np), spectra
 // lam_c, lam_s (bit-reversed, scaled) and border correction G (N x r).
 // *status_host receives 0 on success, 1 if the Durbin recursion broke down.
-cudaError_t run_generator(const double* a1, const Geom& g, double s, const double2* tw64, double* cgen,
+cudaError_t run_generator(const double* a1, const Geom& g, double s, const double2* stw64, const double2* tw64,
+                          double* cgen,
                           double2* lamc64, double2* lams64, float2* lamc32, float2* lams32, double* G64,
                           float* G32, int* status_host, cudaStream_t st);
 cudaError_t launch_convert_d2f(const double* src, float* dst, size_t n, cudaStream_t st);
@@ -46,6 +50,7 @@ cudaError_t launch_convert_f2d(const float* src, double* dst, size_t n, cudaStre
 // ---- per-step kernels, step_kernels.cu --------------------------------------
 template <typename T>
 struct StepTables {
+  const void* stw;     // cx<T>[plan.total]  per-stage FFT twiddles
   const void* tw;      // cx<T>[P]
   const T* lpb;        // [(Np+1) * 2 * Np]
   const void* lam_s;   // cx<T>[Np]
@@ -53,13 +58,28 @@ struct StepTables {
   const T* G;          // [N * r]
 };
 
+// Work decomposition of the four step kernels.
+struct Tiles {
+  int rows;        // grid rows per block (row kernels)
+  int conv_cols;   // spectrum slots per block (column convolution)
+  int solve_cols;  // grid columns per block (y sweep)
+};
+
+template <typename T>
+Tiles default_tiles(int Np);
+template <typename T>
+bool tiles_valid(const Geom& g, const Tiles& t);
+
 template <typename T>
 cudaError_t step_setup_attributes();
 
 // One S-ADI step: u_next (may alias u_prev) from u_cur, u_prev.
 // S: N x Np complex scratch, W: N x N scratch.
+// ev (optional, 5 events): recorded before the first kernel and after each
+// of the four kernels.
 template <typename T>
-cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const RhsParams& rp, const T* u_cur,
-                        const T* u_prev, T* u_next, const T* phi2, void* S, T* W, cudaStream_t st);
+cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
+                        const T* u_prev, T* u_next, const T* phi2, void* S, T* W, cudaStream_t st,
+                        cudaEvent_t* ev = nullptr);
 
 }  // namespace sadi

@@ -32,6 +32,29 @@ __global__ void k_twiddles(double2* tw64, float2* tw32, int P) {
   tw32[k] = make_float2((float)c, (float)-s);
 }
 
+// Per-stage twiddles of the length-2^logL plan: entry (q-1) * m + j of the
+// stage with span S and radix R (m = S/R) is exp(-2 pi i j brev_R(q) / S).
+__global__ void k_stage_twiddles(double2* out64, float2* out32, int logL) {
+  const int ns = plan_stages(logL);
+  const int total = fft_plan(logL).total;
+  const int e = blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= total) return;
+  int s = ns - 1;
+  while (s > 0 && e < plan_stage(logL, s).off) --s;
+  const Stage stg = plan_stage(logL, s);
+  const int local = e - stg.off;
+  const int logm = stg.logS - stg.logR;
+  const int q = (local >> logm) + 1;
+  const int j = local & ((1 << logm) - 1);
+  const int lr = stg.logR;
+  const int bq = lr == 1 ? q : lr == 2 ? (((q & 1) << 1) | (q >> 1)) : (((q & 1) << 2) | (q & 2) | (q >> 2));
+  const long long ex = (long long)j * bq;                 // < S
+  double sn, cs;
+  sincospi(2.0 * (double)ex / (double)(1 << stg.logS), &sn, &cs);
+  out64[e] = make_double2(cs, -sn);
+  out32[e] = make_float2((float)cs, (float)-sn);
+}
+
 __global__ void k_unit_roots(double2* w, int M) {
   const int k = blockIdx.x * blockDim.x + threadIdx.x;
   if (k >= M) return;
@@ -67,7 +90,7 @@ __global__ void k_riesz1d(double* a, int n, double alpha) {
 //   mode 1: block = i in [0, N); f[l] = GT[i * ldg + l] (folded);
 //           writes A[i * N + j] = X[j] * outscale.
 __global__ void k_trap_pass(int mode, double alpha, int Mg, const double* __restrict__ s2,
-                            const double2* __restrict__ twM, Geom g, const double2* __restrict__ tw,
+                            const double2* __restrict__ twM, Geom g, const double2* __restrict__ stw,
                             double* GT, int ldg, double* A, double outscale, int NVB) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* buf = reinterpret_cast<double2*>(smem_raw);
@@ -98,7 +121,7 @@ __global__ void k_trap_pass(int mode, double alpha, int Mg, const double* __rest
       buf[bv * vs + padi(q)] = make_double2(f0, f1);
     }
     __syncthreads();
-    fft_dif<double>(buf, logL, nb, vs, tw, g.logP);
+    fft_dif<double>(buf, logL, nb, vs, stw);
     for (int p = threadIdx.x; p < L; p += blockDim.x) {
       const int i = brev(p, logL);
       if (i >= N) continue;
@@ -138,8 +161,8 @@ __global__ void k_richardson(const double* A1, const double* A2, double* out, si
 //   mode 0: block j in [0, N):   x[m] = a2d[dist(m) * N + j]       -> dst[j * (Np+1) + k]
 //   mode 1: block k1 in [0, Np]: x[m] = src[dist(m) * (Np+1) + k1] -> dst[k1 * (Np+1) + k]
 // dist(m) = min(m, P - m), entries with dist > N - 1 are zero.
-__global__ void k_lambda_pass(int mode, const double* __restrict__ src, Geom g, const double2* __restrict__ tw,
-                              double* __restrict__ dst) {
+__global__ void k_lambda_pass(int mode, const double* __restrict__ src, Geom g, const double2* __restrict__ stw,
+                              const double2* __restrict__ tw, double* __restrict__ dst) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* buf = reinterpret_cast<double2*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp, P = g.P;
@@ -155,7 +178,7 @@ __global__ void k_lambda_pass(int mode, const double* __restrict__ src, Geom g, 
     buf[padi(n)] = make_double2(v[0], v[1]);
   }
   __syncthreads();
-  fft_dif<double>(buf, logNp, 1, vec_stride(Np), tw, g.logP);
+  fft_dif<double>(buf, logNp, 1, vec_stride(Np), stw);
   for (int s = threadIdx.x; s < Np; s += blockDim.x) {
     const int k = brev(s, logNp);
     const int sp = brev((Np - k) & (Np - 1), logNp);
@@ -252,8 +275,8 @@ __global__ void k_durbin(const double* __restrict__ a1, int Np, double s, double
 
 // which = 0: lambda_c = fft(c') / (2 p1 Np); which = 1: lambda_s = fft(Q s') / Np;
 // bit-reversed order, s' = [p1, -p_Np, ..., -p_2], Q = diag(exp(-i pi k / Np)).
-__global__ void k_gs_table(int which, const double* __restrict__ c, Geom g, const double2* __restrict__ tw,
-                           double2* out64, float2* out32) {
+__global__ void k_gs_table(int which, const double* __restrict__ c, Geom g, const double2* __restrict__ stw,
+                           const double2* __restrict__ tw, double2* out64, float2* out32) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   double2* buf = reinterpret_cast<double2*>(smem_raw);
   const int Np = g.Np;
@@ -266,7 +289,7 @@ __global__ void k_gs_table(int which, const double* __restrict__ c, Geom g, cons
     }
   }
   __syncthreads();
-  fft_dif<double>(buf, g.logNp, 1, vec_stride(Np), tw, g.logP);
+  fft_dif<double>(buf, g.logNp, 1, vec_stride(Np), stw);
   const double sc = (which == 0) ? 1.0 / (2.0 * c[0] * (double)Np) : 1.0 / (double)Np;
   for (int p = threadIdx.x; p < Np; p += blockDim.x) {
     const double2 a = cscale(buf[padi(p)], sc);
@@ -348,6 +371,12 @@ cudaError_t launch_twiddles(double2* tw64, float2* tw32, int P, cudaStream_t st)
   return cudaGetLastError();
 }
 
+cudaError_t launch_stage_twiddles(double2* stw64, float2* stw32, int logL, cudaStream_t st) {
+  const int total = fft_plan(logL).total;
+  k_stage_twiddles<<<nblk(total, 256), 256, 0, st>>>(stw64, stw32, logL);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_riesz1d(double* a, int n, double alpha, cudaStream_t st) {
   k_riesz1d<<<1, 32, 0, st>>>(a, n, alpha);
   return cudaGetLastError();
@@ -370,7 +399,7 @@ cudaError_t launch_convert_f2d(const float* s, double* d, size_t n, cudaStream_t
     if (e_ != cudaSuccess) { err = e_; goto done; } \
   } while (0)
 
-cudaError_t run_weights2d(double* a2d, const Geom& g, double alpha, int M, const double2* tw64, cudaStream_t st) {
+cudaError_t run_weights2d(double* a2d, const Geom& g, double alpha, int M, const double2* stw64, cudaStream_t st) {
   cudaError_t err = cudaSuccess;
   const int M2 = 2 * M;
   const int ldg = M2 / 2 + 1;
@@ -396,9 +425,9 @@ cudaError_t run_weights2d(double* a2d, const Geom& g, double alpha, int M, const
     k_sinsq<<<nblk(Mg / 2 + 1, 256), 256, 0, st>>>(s2, Mg);
     k_unit_roots<<<nblk(Mg, 256), 256, 0, st>>>(twM, Mg);
     const int nb = NVB;
-    k_trap_pass<<<Mg / 2 + 1, 256, nb * vbytes + accbytes, st>>>(0, alpha, Mg, s2, twM, g, tw64, GT, ldg, nullptr,
+    k_trap_pass<<<Mg / 2 + 1, 256, nb * vbytes + accbytes, st>>>(0, alpha, Mg, s2, twM, g, stw64, GT, ldg, nullptr,
                                                                    0.0, nb);
-    k_trap_pass<<<g.N, 256, nb * vbytes + accbytes, st>>>(1, alpha, Mg, s2, twM, g, tw64, GT, ldg, A,
+    k_trap_pass<<<g.N, 256, nb * vbytes + accbytes, st>>>(1, alpha, Mg, s2, twM, g, stw64, GT, ldg, A,
                                                           1.0 / ((double)Mg * (double)Mg), nb);
     SADI_TRY(cudaGetLastError());
   }
@@ -414,15 +443,15 @@ done:
   return err;
 }
 
-cudaError_t run_lambda(const double* a2d, const Geom& g, const double2* tw64, double scale, double* lnat,
-                       double* lpb64, float* lpb32, cudaStream_t st) {
+cudaError_t run_lambda(const double* a2d, const Geom& g, const double2* stw64, const double2* tw64, double scale,
+                       double* lnat, double* lpb64, float* lpb32, cudaStream_t st) {
   cudaError_t err = cudaSuccess;
   double* TA = nullptr;
   const size_t sm = (size_t)vec_stride(g.Np) * sizeof(double2);
   SADI_TRY(cudaFuncSetAttribute(k_lambda_pass, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
   SADI_TRY(cudaMalloc(&TA, sizeof(double) * (size_t)g.N * (g.Np + 1)));
-  k_lambda_pass<<<g.N, 256, sm, st>>>(0, a2d, g, tw64, TA);
-  k_lambda_pass<<<g.Np + 1, 256, sm, st>>>(1, TA, g, tw64, lnat);
+  k_lambda_pass<<<g.N, 256, sm, st>>>(0, a2d, g, stw64, tw64, TA);
+  k_lambda_pass<<<g.Np + 1, 256, sm, st>>>(1, TA, g, stw64, tw64, lnat);
   {
     const size_t total = (size_t)(g.Np + 1) * 2 * g.Np;
     k_lambda_arrange<<<nblk(total, 256), 256, 0, st>>>(lnat, g, scale, lpb64, lpb32);
@@ -434,7 +463,8 @@ done:
   return err;
 }
 
-cudaError_t run_generator(const double* a1, const Geom& g, double s, const double2* tw64, double* cgen,
+cudaError_t run_generator(const double* a1, const Geom& g, double s, const double2* stw64, const double2* tw64,
+                          double* cgen,
                           double2* lamc64, double2* lams64, float2* lamc32, float2* lams32, double* G64,
                           float* G32, int* status_host, cudaStream_t st) {
   cudaError_t err = cudaSuccess;
@@ -450,8 +480,8 @@ cudaError_t run_generator(const double* a1, const Geom& g, double s, const doubl
   k_durbin<<<1, 1024, smd, st>>>(a1, g.Np, s, cgen, dstat);
   SADI_TRY(cudaGetLastError());
   if (smt > 227 * 1024) { err = cudaErrorInvalidConfiguration; goto done; }
-  k_gs_table<<<1, 256, smt, st>>>(0, cgen, g, tw64, lamc64, lamc32);
-  k_gs_table<<<1, 256, smt, st>>>(1, cgen, g, tw64, lams64, lams32);
+  k_gs_table<<<1, 256, smt, st>>>(0, cgen, g, stw64, tw64, lamc64, lamc32);
+  k_gs_table<<<1, 256, smt, st>>>(1, cgen, g, stw64, tw64, lams64, lams32);
   SADI_TRY(cudaGetLastError());
   if (g.r > 0) {
     const int r = g.r;

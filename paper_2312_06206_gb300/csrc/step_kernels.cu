@@ -50,31 +50,43 @@ __device__ __forceinline__ T real_view(const cx<T>* v, int k) {
 // lam_s, lam_c carry 1/Np and 1/(2 p1 Np); Q = diag(exp(-i pi k / Np)).
 // ---------------------------------------------------------------------------
 template <typename T>
-__device__ void gs_core(cx<T>* buf, int nvec, int vs, const Geom& g, const cx<T>* __restrict__ tw,
-                        const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c) {
+__device__ void gs_core(cx<T>* buf, int nvec, int vs, const Geom& g, const cx<T>* __restrict__ stw,
+                        const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s,
+                        const cx<T>* __restrict__ lam_c) {
   const int Np = g.Np, logNp = g.logNp;
-  fft_dif<T>(buf, logNp, nvec, vs, tw, g.logP);
+  const int ns = plan_stages(logNp);
+  if (ns >= 2) {
+    dif_stages<T>(buf, logNp, nvec, vs, stw, 0, ns - 1);
+    fused8<T>(buf, logNp, nvec, vs, lam_s, 0);           // x lambda_s between DIF and DIT
+    dit_stages<T>(buf, logNp, nvec, vs, stw, 1, ns - 1);
+    fusedL<T>(buf, logNp, nvec, vs, stw, tw);             // Q^H between DIT and DIF
+    dif_stages<T>(buf, logNp, nvec, vs, stw, 1, ns - 1);
+    fused8<T>(buf, logNp, nvec, vs, lam_c, 0);            // x lambda_c between DIF and DIT
+    dit_stages<T>(buf, logNp, nvec, vs, stw, 0, ns - 1);
+    return;
+  }
+  fft_dif<T>(buf, logNp, nvec, vs, stw);
   for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
     const int v = t >> logNp, p = t & (Np - 1);
     cx<T>* e = buf + v * vs + padi(p);
     *e = cmul(*e, __ldg(&lam_s[p]));
   }
   __syncthreads();
-  fft_dit<T>(buf, logNp, nvec, vs, tw, g.logP);
+  fft_dit<T>(buf, logNp, nvec, vs, stw);
   for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
     const int v = t >> logNp, k = t & (Np - 1);
     cx<T>* e = buf + v * vs + padi(k);
     *e = cmulc(*e, __ldg(&tw[k]));       // Q^H
   }
   __syncthreads();
-  fft_dif<T>(buf, logNp, nvec, vs, tw, g.logP);
+  fft_dif<T>(buf, logNp, nvec, vs, stw);
   for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
     const int v = t >> logNp, p = t & (Np - 1);
     cx<T>* e = buf + v * vs + padi(p);
     *e = cmul(*e, __ldg(&lam_c[p]));
   }
   __syncthreads();
-  fft_dit<T>(buf, logNp, nvec, vs, tw, g.logP);
+  fft_dit<T>(buf, logNp, nvec, vs, stw);
 }
 
 // (H^-1 v)[k] for k < N from vhat: Re vhat[k] + Im vhat[Np-1-k] plus the
@@ -97,7 +109,8 @@ __device__ __forceinline__ T gs_out(const cx<T>* vh, int k, const Geom& g, const
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ tw, int NR) {
+k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw,
+           const cx<T>* __restrict__ tw, int NR) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
@@ -115,7 +128,7 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
     buf[v * vs + padi(n)] = mkc(a, b);
   }
   __syncthreads();
-  fft_dif<T>(buf, logNp, NR, vs, tw, g.logP);
+  fft_dif<T>(buf, logNp, NR, vs, stw);
   const T half = T(0.5);
   for (int t = threadIdx.x; t < (nrows << logNp); t += blockDim.x) {
     const int v = t >> logNp, s = t & (Np - 1);
@@ -143,7 +156,8 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ tw, const T* __restrict__ lpb, int CT) {
+k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
+            const T* __restrict__ lpb, int CT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
@@ -157,34 +171,42 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ tw, const T
     buf[(2 * c + 1) * vs + padi(j)] = cmul(val, __ldg(&tw[j]));
   }
   __syncthreads();
-  fft_dif<T>(buf, logNp, 2 * CT, vs, tw, g.logP);
-  for (int t = threadIdx.x; t < ((2 * CT) << logNp); t += blockDim.x) {
-    const int vec = t >> logNp, p = t & (Np - 1);
-    const int slot = s0 + (vec >> 1), h = vec & 1;
-    if (slot == 0) continue;
-    cx<T>* e = buf + vec * vs + padi(p);
-    *e = cscale(*e, __ldg(&lpb[((size_t)slot * 2 + h) * Np + p]));
-  }
-  if (s0 == 0) {
-    // slot 0: pairs (p, partner) in each half, handled by one thread each.
-    for (int t = threadIdx.x; t < 2 * Np; t += blockDim.x) {
-      const int h = t >> logNp, p = t & (Np - 1);
-      const int pp = (h == 0) ? brev((Np - brev(p, logNp)) & (Np - 1), logNp) : (Np - 1 - p);
-      if (pp < p) continue;
-      cx<T>* e = buf + h * vs;
-      const cx<T> Y = e[padi(p)], Yp = e[padi(pp)];
-      const T A = __ldg(&lpb[(size_t)h * Np + p]);
-      const T B = __ldg(&lpb[((size_t)Np * 2 + h) * Np + p]);
-      e[padi(p)] = cadd(cscale(Y, A), cscale(cconj(Yp), B));
-      if (pp != p) {
-        const T Ap = __ldg(&lpb[(size_t)h * Np + pp]);
-        const T Bp = __ldg(&lpb[((size_t)Np * 2 + h) * Np + pp]);
-        e[padi(pp)] = cadd(cscale(Yp, Ap), cscale(cconj(Y), Bp));
+  const int ns = plan_stages(logNp);
+  if (s0 != 0 && ns >= 2) {
+    // symbol multiply fused between the forward and the inverse transform
+    dif_stages<T>(buf, logNp, 2 * CT, vs, stw, 0, ns - 1);
+    fused8<T>(buf, logNp, 2 * CT, vs, lpb + (size_t)s0 * 2 * Np, Np);
+    dit_stages<T>(buf, logNp, 2 * CT, vs, stw, 0, ns - 1);
+  } else {
+    fft_dif<T>(buf, logNp, 2 * CT, vs, stw);
+    for (int t = threadIdx.x; t < ((2 * CT) << logNp); t += blockDim.x) {
+      const int vec = t >> logNp, p = t & (Np - 1);
+      const int slot = s0 + (vec >> 1), h = vec & 1;
+      if (slot == 0) continue;
+      cx<T>* e = buf + vec * vs + padi(p);
+      *e = cscale(*e, __ldg(&lpb[((size_t)slot * 2 + h) * Np + p]));
+    }
+    if (s0 == 0) {
+      // slot 0: pairs (p, partner) in each half, handled by one thread each.
+      for (int t = threadIdx.x; t < 2 * Np; t += blockDim.x) {
+        const int h = t >> logNp, p = t & (Np - 1);
+        const int pp = (h == 0) ? brev((Np - brev(p, logNp)) & (Np - 1), logNp) : (Np - 1 - p);
+        if (pp < p) continue;
+        cx<T>* e = buf + h * vs;
+        const cx<T> Y = e[padi(p)], Yp = e[padi(pp)];
+        const T A = __ldg(&lpb[(size_t)h * Np + p]);
+        const T B = __ldg(&lpb[((size_t)Np * 2 + h) * Np + p]);
+        e[padi(p)] = cadd(cscale(Y, A), cscale(cconj(Yp), B));
+        if (pp != p) {
+          const T Ap = __ldg(&lpb[(size_t)h * Np + pp]);
+          const T Bp = __ldg(&lpb[((size_t)Np * 2 + h) * Np + pp]);
+          e[padi(pp)] = cadd(cscale(Yp, Ap), cscale(cconj(Y), Bp));
+        }
       }
     }
+    __syncthreads();
+    fft_dit<T>(buf, logNp, 2 * CT, vs, stw);
   }
-  __syncthreads();
-  fft_dit<T>(buf, logNp, 2 * CT, vs, tw, g.logP);
   for (int t = threadIdx.x; t < CT * N; t += blockDim.x) {
     const int c = t % CT, j = t / CT;
     const cx<T> ye = buf[(2 * c) * vs + padi(j)];
@@ -201,8 +223,8 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ tw, const T
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ phi2, T* __restrict__ W,
-             Geom g, RhsParams rp, const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s,
-             const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR) {
+             Geom g, RhsParams rp, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
+             const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
@@ -244,7 +266,7 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
     }
   }
   __syncthreads();
-  fft_dit<T>(buf, logNp, NR, vs, tw, g.logP);
+  fft_dit<T>(buf, logNp, NR, vs, stw);
   // B^n and v1 = Q (v' + i J v'), staged through registers (in place).
   const int halfNp = Np >> 1;
   const int npairs = NR * halfNp;
@@ -286,7 +308,7 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
     }
   }
   __syncthreads();
-  gs_core<T>(buf, NR, vs, g, tw, lam_s, lam_c);
+  gs_core<T>(buf, NR, vs, g, stw, tw, lam_s, lam_c);
   for (int t = threadIdx.x; t < nrows * N; t += blockDim.x) {
     const int v = t / N, k = t % N;
     W[(size_t)(row0 + v) * N + k] = gs_out<T>(buf + v * vs, k, g, G);
@@ -302,11 +324,11 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cols_solve(const T* __restrict__ W, const T* __restrict__ u_cur, const T* u_prev, T* u_next, Geom g, int first,
-             const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c,
-             const T* __restrict__ G, int CT) {
+             const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s,
+             const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int CT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
-  const int N = g.N, Np = g.Np, logNp = g.logNp;
+  const int N = g.N, Np = g.Np;
   const int vs = vec_stride(Np);
   const int i0 = blockIdx.x * CT;
   for (int t = threadIdx.x; t < CT * Np; t += blockDim.x) {
@@ -320,7 +342,7 @@ k_cols_solve(const T* __restrict__ W, const T* __restrict__ u_cur, const T* u_pr
     buf[c * vs + padi(k)] = cmul(mkc(a, b), __ldg(&tw[k]));
   }
   __syncthreads();
-  gs_core<T>(buf, CT, vs, g, tw, lam_s, lam_c);
+  gs_core<T>(buf, CT, vs, g, stw, tw, lam_s, lam_c);
   for (int t = threadIdx.x; t < CT * N; t += blockDim.x) {
     const int c = t % CT, j = t / CT;
     const int i = i0 + c;
@@ -331,14 +353,6 @@ k_cols_solve(const T* __restrict__ W, const T* __restrict__ u_cur, const T* u_pr
     u_next[idx] = first ? uc + uh : (T(2) * uc - u_prev[idx]) + uh;
   }
 }
-
-template <typename T>
-struct Cfg {
-  // rows per block of the row kernels, slots/columns per block of the column kernels
-  static int rows(int Np) { int r = (int)(4096 * sizeof(float) / sizeof(T)) / Np; return r < 1 ? 1 : r; }
-  static int conv_cols(int Np) { int c = (int)(2048 * sizeof(float) / sizeof(T)) / Np; return c < 1 ? 1 : (c > 8 ? 8 : c); }
-  static int solve_cols(int Np) { int c = (int)(8192 * sizeof(float) / sizeof(T)) / Np; return c < 1 ? 1 : (c > 16 ? 16 : c); }
-};
 
 }  // namespace
 
@@ -354,31 +368,72 @@ cudaError_t step_setup_attributes() {
 }
 
 template <typename T>
-cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const RhsParams& rp, const T* u_cur,
-                        const T* u_prev, T* u_next, const T* phi2, void* Sv, T* W, cudaStream_t st) {
+Tiles default_tiles(int Np) {
+  // rows per block of the row kernels and slots/columns per block of the
+  // column kernels: about two resident blocks of 256 threads per SM at N' = 1024
+  const int es = (int)sizeof(T) / 4;   // 1 (float) or 2 (double)
+  Tiles t;
+  t.rows = 2048 / es / Np;
+  t.conv_cols = 1024 / es / Np;
+  t.solve_cols = 2048 / es / Np;
+  if (t.rows < 1) t.rows = 1;
+  if (t.conv_cols < 1) t.conv_cols = 1;
+  if (t.solve_cols < 1) t.solve_cols = 1;
+  if (t.conv_cols > 8) t.conv_cols = 8;
+  if (t.solve_cols > 16) t.solve_cols = 16;
+  return t;
+}
+
+template <typename T>
+bool tiles_valid(const Geom& g, const Tiles& t) {
+  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  const size_t lim = 227 * 1024;
+  if (t.rows < 1 || t.conv_cols < 1 || t.solve_cols < 1) return false;
+  if (g.Np % t.conv_cols != 0) return false;
+  if (t.rows * (g.Np / 2) > kMaxPairs * kThreads) return false;
+  if (t.rows * vbytes > lim || 2 * t.conv_cols * vbytes > lim || t.solve_cols * vbytes > lim) return false;
+  return true;
+}
+
+template <typename T>
+cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
+                        const T* u_prev, T* u_next, const T* phi2, void* Sv, T* W, cudaStream_t st,
+                        cudaEvent_t* ev) {
+  const cx<T>* stw = reinterpret_cast<const cx<T>*>(tb.stw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
   const cx<T>* ls = reinterpret_cast<const cx<T>*>(tb.lam_s);
   const cx<T>* lc = reinterpret_cast<const cx<T>*>(tb.lam_c);
   cx<T>* S = reinterpret_cast<cx<T>*>(Sv);
   const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
-  const int NR = Cfg<T>::rows(g.Np);
-  const int CTc = Cfg<T>::conv_cols(g.Np);
-  const int CTs = Cfg<T>::solve_cols(g.Np);
-  if (NR * (g.Np / 2) > kMaxPairs * kThreads) return cudaErrorInvalidConfiguration;
+  if (!tiles_valid<T>(g, tl)) return cudaErrorInvalidConfiguration;
+  const int NR = tl.rows, CTc = tl.conv_cols, CTs = tl.solve_cols;
   const int rblocks = (g.N + NR - 1) / NR;
-  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, tw, NR);
-  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, tw, tb.lpb, CTc);
-  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, tw, ls, lc, tb.G, NR);
-  k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, g, rp.first, tw,
-                                                                          ls, lc, tb.G, CTs);
+  if (ev) cudaEventRecord(ev[0], st);
+  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, stw, tw, NR);
+  if (ev) cudaEventRecord(ev[1], st);
+  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
+  if (ev) cudaEventRecord(ev[2], st);
+  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR);
+  if (ev) cudaEventRecord(ev[3], st);
+  k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, g, rp.first,
+                                                                          stw, tw, ls, lc, tb.G, CTs);
+  if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }
 
 template cudaError_t step_setup_attributes<float>();
 template cudaError_t step_setup_attributes<double>();
-template cudaError_t launch_step<float>(const Geom&, const StepTables<float>&, const RhsParams&, const float*,
-                                        const float*, float*, const float*, void*, float*, cudaStream_t);
-template cudaError_t launch_step<double>(const Geom&, const StepTables<double>&, const RhsParams&, const double*,
-                                         const double*, double*, const double*, void*, double*, cudaStream_t);
+template Tiles default_tiles<float>(int);
+template Tiles default_tiles<double>(int);
+template bool tiles_valid<float>(const Geom&, const Tiles&);
+template bool tiles_valid<double>(const Geom&, const Tiles&);
+template cudaError_t launch_step<float>(const Geom&, const StepTables<float>&, const Tiles&, const RhsParams&,
+                                        const float*,
+                                        const float*, float*, const float*, void*, float*, cudaStream_t,
+                                        cudaEvent_t*);
+template cudaError_t launch_step<double>(const Geom&, const StepTables<double>&, const Tiles&, const RhsParams&,
+                                         const double*,
+                                         const double*, double*, const double*, void*, double*, cudaStream_t,
+                                         cudaEvent_t*);
 
 }  // namespace sadi

@@ -33,6 +33,10 @@ _SIGS = {
     "sadi_get_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sadi_get_setup": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "sadi_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
+    "sadi_set_tiles": (C.c_int, [C.c_void_p, C.c_int, C.c_int, C.c_int]),
+    "sadi_get_tiles": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "sadi_profile": (C.c_int, [C.c_void_p, C.c_int]),
+    "sadi_get_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "sadi_last_error": (C.c_char_p, [C.c_void_p]),
     "sadi_destroy": (None, [C.c_void_p]),
 }
@@ -130,6 +134,23 @@ class Sadi:
         a, b = C.c_int(), C.c_int()
         _check(lib().sadi_get_info(self.ctx, C.byref(a), C.byref(b)), self.ctx)
         return a.value, b.value
+
+    def sadi_set_tiles(self, rows: int = 0, conv_cols: int = 0, solve_cols: int = 0):
+        _check(lib().sadi_set_tiles(self.ctx, int(rows), int(conv_cols), int(solve_cols)), self.ctx)
+
+    def sadi_get_tiles(self):
+        t = (C.c_int * 3)()
+        _check(lib().sadi_get_tiles(self.ctx, t), self.ctx)
+        return tuple(t)
+
+    def sadi_profile(self, enable: bool):
+        _check(lib().sadi_profile(self.ctx, 1 if enable else 0), self.ctx)
+
+    def sadi_get_phase_times(self):
+        ms = (C.c_double * 4)()
+        n = C.c_longlong()
+        _check(lib().sadi_get_phase_times(self.ctx, ms, C.byref(n)), self.ctx)
+        return list(ms), int(n.value)
 
     def sadi_last_error(self) -> str:
         return lib().sadi_last_error(self.ctx).decode()
