@@ -51,6 +51,8 @@ def _args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=N_DEFAULT)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--acc-steps", type=int, default=1000,
+                    help="steps of the accuracy check (FP32 form vs plain FP64 from the same data)")
     return ap.parse_args()
 
 
@@ -194,6 +196,20 @@ def run_reference(a):
 
 # ------------------------------------------------------------- our arm -------
 
+def aggregate(times, world_size, pts_per_step, steps_list, reduce_max=None):
+    """Whole-job throughput from per-rank times.  times: this rank's
+    [ms_fp32, ms_fp64, s_e2e]; reduce_max(list) -> element-wise max over ranks
+    (identity on one rank).  Every rank advances its own copy of the workload
+    (weak scaling), so value = world_size * points * steps / slowest time."""
+    mx = reduce_max(list(times)) if reduce_max else list(times)
+    ms32, ms64, e2e = mx
+    k32, k64, ke = steps_list
+    return {"value": world_size * pts_per_step * k32 / (ms32 / 1e3),
+            "value64": world_size * pts_per_step * k64 / (ms64 / 1e3),
+            "e2e": world_size * pts_per_step * ke / e2e,
+            "ms32": ms32, "ms64": ms64, "e2e_s": e2e}
+
+
 def algorithmic(N, Np, es):
     """Per-launch algorithmic work of each kernel (one instance), for the
     roofline: (bytes, flops).  FFT flops are the nominal 5 L log2 L of a
@@ -247,33 +263,30 @@ def main():
             ctxs.append(s)
         return ctxs
 
+    def step_all(ctxs):
+        S.sadi_batch_step(ctxs, 1)
+
     def timed(ctxs, K, W, profile=False):
         for _ in range(W):
-            for s in ctxs:
-                s.step(1)
+            step_all(ctxs)
         if profile:
-            for s in ctxs:
-                s.sadi_profile(True)
+            ctxs[0].sadi_profile(True)
         barrier()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         for k in range(K):
             flush.zero_()
             evs[k][0].record(stream)
-            for s in ctxs:
-                s.step(1)
+            step_all(ctxs)
             evs[k][1].record(stream)
         barrier()
         ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         phases = None
         if profile:
-            tot = [0.0] * 4
-            nst = 0
-            for s in ctxs:
-                p, n = s.sadi_get_phase_times()
-                s.sadi_profile(False)
-                tot = [x + y for x, y in zip(tot, p)]
-                nst += n
-            phases = ([t / nst for t in tot], nst)
+            # the batched FP32 kernels cover all instances; their events are
+            # recorded on the first context
+            p, n = ctxs[0].sadi_get_phase_times()
+            ctxs[0].sadi_profile(False)
+            phases = ([t / n for t in p], n)
         return ms, phases
 
     # plain FP64 GS-FFT path
@@ -304,7 +317,7 @@ def main():
     _, (phase_ms, _) = timed(c32, Kp, 0, profile=True)
     names = ["k_rows_r2c", "k_cols_conv", "k_rows_solve", "k_cols_solve"]
     Np = c32[0].sadi_get_info()[0]
-    alg = algorithmic(N, Np, 4)
+    alg = {k: (b * len(ALPHAS), f * len(ALPHAS)) for k, (b, f) in algorithmic(N, Np, 4).items()}
     dom = max(range(4), key=lambda k: phase_ms[k])
     dname = names[dom]
     dur_s = phase_ms[dom] / 1e3
@@ -339,23 +352,36 @@ def main():
     for s in c32:
         st = lib.sadi_set_initial(s.ctx, ctypes.c_void_p(pin_in.data_ptr()), None)
         assert st == 0, s.sadi_last_error()
+    arr = (ctypes.c_void_p * len(c32))(*[s.ctx for s in c32])
     for k in range(Ke):
+        assert lib.sadi_batch_step(arr, len(c32), 1) == 0
         for i, s in enumerate(c32):
-            assert lib.sadi_step(s.ctx, 1) == 0
             assert lib.sadi_get(s.ctx, ctypes.c_void_p(pin_out[i].data_ptr()), ctypes.byref(nll)) == 0
     dt_e2e = time.perf_counter() - t0
     barrier()
     h2d = len(ALPHAS) * N * N * 8 / Ke
     d2h = len(ALPHAS) * N * N * 8
+    # accuracy at the workload's full step count: both forms from phi1
+    rel_full = None
+    if a.acc_steps > 0:
+        for s in c64 + c32:
+            s.set_initial(phi1, None)
+        S.sadi_batch_step(c64 + c32, a.acc_steps)
+        rel_full = []
+        for s64, s32 in zip(c64, c32):
+            u64, _ = s64.get()
+            u32, _ = s32.get()
+            rel_full.append(float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)))
     # aggregate over ranks (max time)
-    t32 = torch.tensor([ms32, ms64, dt_e2e], dtype=torch.float64, device=dev)
-    if ws > 1:
-        torch.distributed.all_reduce(t32, op=torch.distributed.ReduceOp.MAX)
-    ms32m, ms64m, e2em = [float(x) for x in t32.tolist()]
+    def reduce_max(vals):
+        tt = torch.tensor(vals, dtype=torch.float64, device=dev)
+        if ws > 1:
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        return [float(x) for x in tt.tolist()]
     pts = N * N * len(ALPHAS)
-    value = ws * pts * a.steps / (ms32m / 1e3)
-    value64 = ws * pts * K64 / (ms64m / 1e3)
-    e2e_val = ws * pts * Ke / e2em
+    agg = aggregate([ms32, ms64, dt_e2e], ws, pts, (a.steps, K64, Ke), reduce_max)
+    ms32m, ms64m = agg["ms32"], agg["ms64"]
+    value, value64, e2e_val = agg["value"], agg["value64"], agg["e2e"]
     if rank == 0:
         cpu = None
         rel_oracle = None
@@ -383,14 +409,17 @@ def main():
             "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64m / K64, "steps": K64},
             "speedup_vs_fp64": value / value64,
             "rel_l2_fp32_vs_fp64": max(rels), "rel_l2_steps": nsteps_cmp,
+            "rel_l2_fp32_vs_fp64_full": None if rel_full is None else
+            {"steps": a.acc_steps, "per_alpha": dict(zip([str(x) for x in ALPHAS], rel_full)),
+             "max": max(rel_full)},
             "rel_l2_vs_oracle_4steps": None if rel_oracle is None else
             {"fp64": rel_oracle, "fp32": rel_oracle32, "alpha": 1.5},
-            "roofline": roofline,
+            "roofline": roofline, "batched": "one launch per kernel covers the three instances (sadi_batch_step)",
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
-                    "how": "C ABI with pinned host buffers: sadi_set_initial once, then per step sadi_step(1) + "
-                           "sadi_get of u^{n+1} for each instance; wall clock"},
-            "gpu_launches": 4 * len(ALPHAS) * a.steps,
+                    "how": "C ABI with pinned host buffers: sadi_set_initial once, then per step "
+                           "sadi_batch_step(1) + sadi_get of u^{n+1} for each instance; wall clock"},
+            "gpu_launches": 4 * a.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

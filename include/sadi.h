@@ -91,6 +91,17 @@ sadi_status sadi_set_initial(sadi_ctx *ctx, const double *phi1, const double *ph
  * B^n = -tau^2 kappa L_h u^n + tau^2 g(u^n)). */
 sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
 
+/* Advance each of count contexts by nsteps time steps (asynchronous), as
+ * sadi_step would, but batched: FP32 contexts with FFT length N' <= 1024 are
+ * grouped by N' and each group runs one launch per kernel for all its members
+ * (independent problems of possibly different N, alpha, kappa, tau and g);
+ * the other contexts step one after another.  All contexts must be
+ * initialised and distinct (SADI_EINVAL / SADI_ESTATE otherwise).  The work
+ * is issued on the first context's stream, ordered after the work already
+ * queued on the other contexts' streams and before their later work (event
+ * waits).  Results are identical to stepping each context alone. */
+sadi_status sadi_batch_step(sadi_ctx **ctxs, int count, int nsteps);
+
 /* Copy u^n to the host (N*N doubles) after the stream's pending work; *n_out
  * (may be NULL) receives n.  Synchronous. */
 sadi_status sadi_get(sadi_ctx *ctx, double *u_out, long long *n_out);

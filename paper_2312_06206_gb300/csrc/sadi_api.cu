@@ -33,6 +33,12 @@ struct sadi_ctx {
   double2* stw64 = nullptr;  // per-stage FFT twiddles
   float2* stw32 = nullptr;
   Tiles tiles64{}, tiles32{};
+  // FP32 register-FFT path tables (N' <= 1024)
+  float2* rtw1 = nullptr;
+  float* rlreg = nullptr;
+  float2* rlamc = nullptr;
+  float2* rlams = nullptr;
+  bool reg_path = false;
   double* lpb64 = nullptr;   // (Np+1) 2 Np
   float* lpb32 = nullptr;
   double2* lamc64 = nullptr;
@@ -42,7 +48,11 @@ struct sadi_ctx {
   double* G64 = nullptr;     // N x r
   float* G32 = nullptr;
   // state (element type per prec)
+  // FP64: ubuf[cur] = u^n, ubuf[1-cur] = u^{n-1} (ping-pong).
+  // FP32: ubuf[0] = hi part of u^n, ubuf[1] = d = u^n - u^{n-1}, ulo = lo part
+  // (double-float state, updated in place; cur stays 0).
   void* ubuf[2] = {nullptr, nullptr};
+  float* ulo = nullptr;
   void* phi2 = nullptr;
   void* S = nullptr;         // N x Np complex
   void* W = nullptr;         // N x N
@@ -58,6 +68,7 @@ struct sadi_ctx {
   std::vector<std::array<cudaEvent_t, 5>> ev_free;
   double phase_ms[4] = {0, 0, 0, 0};
   long long phase_steps = 0;
+  cudaEvent_t order_ev = nullptr;   // cross-stream ordering in sadi_batch_step
 };
 
 static thread_local std::string g_create_err;
@@ -92,9 +103,9 @@ T* dalloc(size_t n, cudaError_t* e) {
 }
 
 void free_all(sadi_ctx* c) {
-  void* ptrs[] = {c->stw64, c->stw32, c->a1,     c->a2d,    c->cgen,   c->lnat,   c->tw64,   c->tw32, c->lpb64,
+  void* ptrs[] = {c->rtw1, c->rlreg, c->rlamc, c->rlams, c->stw64, c->stw32, c->a1,     c->a2d,    c->cgen,   c->lnat,   c->tw64,   c->tw32, c->lpb64,
                   c->lpb32,  c->lamc64, c->lams64, c->lamc32, c->lams32, c->G64,  c->G32,
-                  c->ubuf[0], c->ubuf[1], c->phi2, c->S,      c->W,      c->stage};
+                  c->ubuf[0], c->ubuf[1], c->ulo, c->phi2, c->S,      c->W,      c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& a : c->ev_pool)
@@ -103,6 +114,7 @@ void free_all(sadi_ctx* c) {
     for (auto e : a) cudaEventDestroy(e);
   c->ev_pool.clear();
   c->ev_free.clear();
+  if (c->order_ev) cudaEventDestroy(c->order_ev);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
 }
 
@@ -141,6 +153,9 @@ sadi_status alloc_state(sadi_ctx* c) {
     c->ubuf[k] = nullptr;
     CK(cudaMalloc(&c->ubuf[k], nn * es), "cudaMalloc(state)");
   }
+  if (c->ulo) cudaFree(c->ulo);
+  c->ulo = nullptr;
+  if (c->prec == SADI_PREC_FP32) CK(cudaMalloc(&c->ulo, nn * sizeof(float)), "cudaMalloc(state lo)");
   if (c->phi2) cudaFree(c->phi2);
   if (c->S) cudaFree(c->S);
   if (c->W) cudaFree(c->W);
@@ -222,6 +237,10 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
       {(void**)&c->G64, sizeof(double) * ((size_t)N * g.r + 1)},
       {(void**)&c->G32, sizeof(float) * ((size_t)N * g.r + 1)},
       {(void**)&c->stage, sizeof(double) * nn},
+      {(void**)&c->rtw1, sizeof(float2) * Np},
+      {(void**)&c->rlreg, sizeof(float) * nlpb},
+      {(void**)&c->rlamc, sizeof(float2) * Np},
+      {(void**)&c->rlams, sizeof(float2) * Np},
   };
   for (auto& al : allocs) {
     e = cudaMalloc(al.p, al.bytes);
@@ -247,6 +266,9 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
     c->err = "sadi_create: Durbin recursion broke down (H not numerically SPD)";
     return bail(SADI_ENOTSPD);
   }
+  c->reg_path = reg_path_supported(g.logNp);
+  if ((e = run_reg_tables(g, c->lnat, scale, c->lamc64, c->lams64, c->rtw1, c->rlreg, c->rlamc, c->rlams, st)))
+    return bail(cuda_fail(c, e, "register-path tables"));
   if ((e = step_setup_attributes<float>())) return bail(cuda_fail(c, e, "kernel attributes"));
   if ((e = step_setup_attributes<double>())) return bail(cuda_fail(c, e, "kernel attributes"));
   c->tiles64 = default_tiles<double>(Np);
@@ -293,7 +315,8 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   if (c->prec == SADI_PREC_FP64) {
     CK(cudaMemcpyAsync(c->ubuf[0], c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "phi1");
   } else {
-    CK(launch_convert_d2f(c->stage, static_cast<float*>(c->ubuf[0]), nn, st), "phi1 convert");
+    CK(launch_split_d2ff(c->stage, static_cast<float*>(c->ubuf[0]), c->ulo, nn, st), "phi1 split");
+    CK(cudaMemsetAsync(c->ubuf[1], 0, nn * sizeof(float), st), "increment zero");
   }
   if (phi2) {
     CK(cudaMemcpyAsync(c->stage, phi2, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy phi2");
@@ -310,42 +333,184 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   return SADI_OK;
 }
 
-sadi_status sadi_step(sadi_ctx* c, int nsteps) {
-  if (!c) return SADI_EINVAL;
-  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
-  if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_step before sadi_set_initial");
-  if (nsteps < 0) return fail(c, SADI_EINVAL, "nsteps must be >= 0");
-  for (int it = 0; it < nsteps; ++it) {
-    RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0};
-    cudaEvent_t* ev = nullptr;
-    if (c->profiling) {
-      if (c->ev_pool.size() >= 512) CK(fold_events(c), "profile events");
-      if (c->ev_free.empty()) {
-        std::array<cudaEvent_t, 5> a{};
-        for (auto& e : a) CK(cudaEventCreate(&e), "cudaEventCreate");
-        c->ev_free.push_back(a);
-      }
-      c->ev_pool.push_back(c->ev_free.back());
-      c->ev_free.pop_back();
-      ev = c->ev_pool.back().data();
-    }
+}  // extern "C"
+
+namespace {
+
+// Profiling events for one step of ctx (nullptr when not profiling).
+sadi_status next_events(sadi_ctx* c, cudaEvent_t** out) {
+  *out = nullptr;
+  if (!c->profiling) return SADI_OK;
+  if (c->ev_pool.size() >= 512) CK(fold_events(c), "profile events");
+  if (c->ev_free.empty()) {
+    std::array<cudaEvent_t, 5> a{};
+    for (auto& e : a) CK(cudaEventCreate(&e), "cudaEventCreate");
+    c->ev_free.push_back(a);
+  }
+  c->ev_pool.push_back(c->ev_free.back());
+  c->ev_free.pop_back();
+  *out = c->ev_pool.back().data();
+  return SADI_OK;
+}
+
+RegInst reg_inst(const sadi_ctx* c) {
+  RegInst r{};
+  r.tw1 = c->rtw1;
+  r.tw = c->tw32;
+  r.lam_s = c->rlams;
+  r.lam_c = c->rlamc;
+  r.lreg = c->rlreg;
+  r.G = c->G32;
+  r.u_hi = static_cast<float*>(c->ubuf[0]);
+  r.u_d = static_cast<float*>(c->ubuf[1]);
+  r.u_lo = c->ulo;
+  r.phi2 = static_cast<const float*>(c->phi2);
+  r.S = static_cast<float2*>(c->S);
+  r.W = static_cast<float*>(c->W);
+  r.N = c->g.N;
+  r.r = c->g.r;
+  r.tau = (float)c->tau;
+  r.tau2 = (float)(c->tau * c->tau);
+  r.gkind = c->gkind;
+  r.first = c->n == 0 ? 1 : 0;
+  return r;
+}
+
+bool uses_reg_path(const sadi_ctx* c) { return c->prec == SADI_PREC_FP32 && c->reg_path; }
+
+// One step of a context on the shared-memory engine (FP64, or FP32 N' > 1024),
+// on stream st.
+sadi_status step_smem(sadi_ctx* c, cudaEvent_t* ev, cudaStream_t st) {
+  RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0};
+  cudaError_t e;
+  if (c->prec == SADI_PREC_FP64) {
     void* ucur = c->ubuf[c->cur];
     void* uoth = c->ubuf[1 - c->cur];
-    cudaError_t e;
-    if (c->prec == SADI_PREC_FP64) {
-      StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
-      e = launch_step<double>(c->g, tb, c->tiles64, rp, static_cast<const double*>(ucur), static_cast<const double*>(uoth),
-                              static_cast<double*>(uoth), static_cast<const double*>(c->phi2), c->S,
-                              static_cast<double*>(c->W), c->stream, ev);
+    StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
+    e = launch_step<double>(c->g, tb, c->tiles64, rp, static_cast<const double*>(ucur), static_cast<double*>(uoth),
+                            static_cast<double*>(uoth), nullptr, static_cast<const double*>(c->phi2), c->S,
+                            static_cast<double*>(c->W), st, ev);
+  } else {
+    StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+    float* hi = static_cast<float*>(c->ubuf[0]);
+    e = launch_step<float>(c->g, tb, c->tiles32, rp, hi, static_cast<float*>(c->ubuf[1]), hi, c->ulo,
+                           static_cast<const float*>(c->phi2), c->S, static_cast<float*>(c->W), st, ev);
+  }
+  if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
+  if (c->prec == SADI_PREC_FP64) c->cur = 1 - c->cur;
+  c->n += 1;
+  return SADI_OK;
+}
+
+// One step of up to kMaxBatch register-path contexts with equal FFT length,
+// in one launch per kernel on stream st.
+sadi_status step_reg_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
+  static thread_local RegBatch b;
+  b.count = count;
+  int max_n = 0;
+  for (int k = 0; k < count; ++k) {
+    b.in[k] = reg_inst(cs[k]);
+    if (cs[k]->g.N > max_n) max_n = cs[k]->g.N;
+  }
+  sadi_ctx* c = cs[0];
+  cudaEvent_t* ev = nullptr;
+  sadi_status st = next_events(c, &ev);
+  if (st != SADI_OK) return st;
+  const cudaError_t e = launch_step_reg(b, c->g.logNp, max_n, st_, ev);
+  if (e != cudaSuccess) {
+    for (int k = 0; k < count; ++k) cuda_fail(cs[k], e, "step launch");
+    return SADI_ECUDA;
+  }
+  for (int k = 0; k < count; ++k) cs[k]->n += 1;
+  return SADI_OK;
+}
+
+sadi_status check_steppable(sadi_ctx* c) {
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_step before sadi_set_initial");
+  return SADI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+sadi_status sadi_step(sadi_ctx* c, int nsteps) {
+  if (!c) return SADI_EINVAL;
+  sadi_status st = check_steppable(c);
+  if (st != SADI_OK) return st;
+  if (nsteps < 0) return fail(c, SADI_EINVAL, "nsteps must be >= 0");
+  for (int it = 0; it < nsteps; ++it) {
+    if (uses_reg_path(c)) {
+      st = step_reg_group(&c, 1, c->stream);
     } else {
-      StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
-      e = launch_step<float>(c->g, tb, c->tiles32, rp, static_cast<const float*>(ucur), static_cast<const float*>(uoth),
-                             static_cast<float*>(uoth), static_cast<const float*>(c->phi2), c->S,
-                             static_cast<float*>(c->W), c->stream, ev);
+      cudaEvent_t* ev = nullptr;
+      st = next_events(c, &ev);
+      if (st == SADI_OK) st = step_smem(c, ev, c->stream);
     }
-    if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
-    c->cur = 1 - c->cur;
-    c->n += 1;
+    if (st != SADI_OK) return st;
+  }
+  return SADI_OK;
+}
+
+sadi_status sadi_batch_step(sadi_ctx** ctxs, int count, int nsteps) {
+  if (!ctxs || count < 1 || nsteps < 0) return SADI_EINVAL;
+  for (int k = 0; k < count; ++k) {
+    if (!ctxs[k]) return SADI_EINVAL;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(ctxs[k], SADI_EINVAL, "a context appears twice in the batch");
+    sadi_status st = check_steppable(ctxs[k]);
+    if (st != SADI_OK) return st;
+  }
+  // group register-path contexts by FFT length (insertion order kept)
+  std::vector<std::vector<sadi_ctx*>> groups;
+  std::vector<sadi_ctx*> others;
+  for (int k = 0; k < count; ++k) {
+    sadi_ctx* c = ctxs[k];
+    if (!uses_reg_path(c)) {
+      others.push_back(c);
+      continue;
+    }
+    bool placed = false;
+    for (auto& gr : groups)
+      if (gr[0]->g.logNp == c->g.logNp && (int)gr.size() < kMaxBatch) {
+        gr.push_back(c);
+        placed = true;
+        break;
+      }
+    if (!placed) groups.push_back({c});
+  }
+  // everything runs on the first context's stream, ordered after and before
+  // the pending work of the other contexts' streams
+  cudaStream_t s0 = ctxs[0]->stream;
+  for (int k = 0; k < count; ++k) {
+    sadi_ctx* c = ctxs[k];
+    if (c->stream == s0) continue;
+    if (!c->order_ev) CK(cudaEventCreateWithFlags(&c->order_ev, cudaEventDisableTiming), "cudaEventCreate");
+    CK(cudaEventRecord(c->order_ev, c->stream), "cudaEventRecord");
+    CK(cudaStreamWaitEvent(s0, c->order_ev, 0), "cudaStreamWaitEvent");
+  }
+  for (int it = 0; it < nsteps; ++it) {
+    for (auto& gr : groups) {
+      sadi_status st = step_reg_group(gr.data(), (int)gr.size(), s0);
+      if (st != SADI_OK) return st;
+    }
+    for (sadi_ctx* c : others) {
+      cudaEvent_t* ev = nullptr;
+      sadi_status st = next_events(c, &ev);
+      if (st == SADI_OK) st = step_smem(c, ev, s0);
+      if (st != SADI_OK) return st;
+    }
+  }
+  sadi_ctx* c0 = ctxs[0];
+  bool any_other = false;
+  for (int k = 0; k < count; ++k) any_other |= ctxs[k]->stream != s0;
+  if (any_other) {
+    sadi_ctx* c = c0;
+    if (!c0->order_ev) CK(cudaEventCreateWithFlags(&c0->order_ev, cudaEventDisableTiming), "cudaEventCreate");
+    CK(cudaEventRecord(c0->order_ev, s0), "cudaEventRecord");
+    for (int k = 0; k < count; ++k)
+      if (ctxs[k]->stream != s0) CK(cudaStreamWaitEvent(ctxs[k]->stream, c0->order_ev, 0), "cudaStreamWaitEvent");
   }
   return SADI_OK;
 }
@@ -360,7 +525,7 @@ sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {
   if (c->prec == SADI_PREC_FP64) {
     CK(cudaMemcpyAsync(u_out, c->ubuf[c->cur], nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   } else {
-    CK(launch_convert_f2d(static_cast<const float*>(c->ubuf[c->cur]), c->stage, nn, st), "u convert");
+    CK(launch_join_ff2d(static_cast<const float*>(c->ubuf[0]), c->ulo, c->stage, nn, st), "u join");
     CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   }
   CK(cudaStreamSynchronize(st), "sadi_get");
@@ -381,8 +546,9 @@ sadi_status sadi_get_device(sadi_ctx* c, void* dst, int dtype) {
     if (dtype == 0) CK(cudaMemcpyAsync(dst, src, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
     else CK(launch_convert_d2f(static_cast<const double*>(src), static_cast<float*>(dst), nn, st), "convert");
   } else {
-    if (dtype == 1) CK(cudaMemcpyAsync(dst, src, nn * sizeof(float), cudaMemcpyDeviceToDevice, st), "copy");
-    else CK(launch_convert_f2d(static_cast<const float*>(src), static_cast<double*>(dst), nn, st), "convert");
+    const float* hi = static_cast<const float*>(c->ubuf[0]);
+    if (dtype == 1) CK(launch_join_ff2f(hi, c->ulo, static_cast<float*>(dst), nn, st), "join");
+    else CK(launch_join_ff2d(hi, c->ulo, static_cast<double*>(dst), nn, st), "join");
   }
   return SADI_OK;
 }

@@ -46,6 +46,10 @@ cudaError_t run_generator(const double* a1, const Geom& g, double s, const doubl
                           float* G32, int* status_host, cudaStream_t st);
 cudaError_t launch_convert_d2f(const double* src, float* dst, size_t n, cudaStream_t st);
 cudaError_t launch_convert_f2d(const float* src, double* dst, size_t n, cudaStream_t st);
+// double -> (hi, lo) float pair; (hi, lo) -> double hi + lo (optionally also a float copy)
+cudaError_t launch_split_d2ff(const double* src, float* hi, float* lo, size_t n, cudaStream_t st);
+cudaError_t launch_join_ff2d(const float* hi, const float* lo, double* dst, size_t n, cudaStream_t st);
+cudaError_t launch_join_ff2f(const float* hi, const float* lo, float* dst, size_t n, cudaStream_t st);
 
 // ---- per-step kernels, step_kernels.cu --------------------------------------
 template <typename T>
@@ -73,13 +77,49 @@ bool tiles_valid(const Geom& g, const Tiles& t);
 template <typename T>
 cudaError_t step_setup_attributes();
 
+// FP32 register-FFT path (FFT length N' <= 1024).  One instance of a batch:
+// natural-order tables and the in-place double-float state.
+struct RegInst {
+  const float2* tw1;    // [N'] two-level FFT twiddles exp(-2 pi i t k1 / N') at [k1 * TT + t]
+  const float2* tw;     // [2N'] exp(-2 pi i k / 2N')
+  const float2* lam_s;  // [N'] natural order, scaled as the bit-reversed tables
+  const float2* lam_c;  // [N']
+  const float* lreg;    // [(N'+1) * 2 * N'] symbol rows by x-frequency, even/odd halves, scaled
+  const float* G;       // [N * r] border correction
+  float* u_hi;          // state: u = u_hi + u_lo (double-float), u_d = u^n - u^{n-1}
+  float* u_lo;
+  float* u_d;
+  const float* phi2;
+  float2* S;            // N x N' spectrum scratch
+  float* W;             // N x N sweep scratch
+  int N, r;
+  float tau, tau2;
+  int gkind, first;
+};
+constexpr int kMaxBatch = 32;
+// passed by value as a __grid_constant__ kernel parameter (about 4 KB)
+struct RegBatch {
+  int count;
+  RegInst in[kMaxBatch];
+};
+bool reg_path_supported(int logNp);
+// One step of every instance of the batch (all with FFT length 2^logNp);
+// max_n = the largest N in the batch.
+cudaError_t launch_step_reg(const RegBatch& b, int logNp, int max_n, cudaStream_t st, cudaEvent_t* ev);
+// natural-order FP32 tables of the register path from the FP64 setup products
+cudaError_t run_reg_tables(const Geom& g, const double* lnat, double scale, const double2* lamc64,
+                           const double2* lams64, float2* tw1, float* lreg, float2* lamc_nat, float2* lams_nat,
+                           cudaStream_t st);
+
 // One S-ADI step: u_next (may alias u_prev) from u_cur, u_prev.
 // S: N x Np complex scratch, W: N x N scratch.
 // ev (optional, 5 events): recorded before the first kernel and after each
-// of the four kernels.
+// of the four kernels.  u_lo == nullptr: plain leapfrog u_next = 2u_cur - u_prev
+// + uhat (u_next may alias u_prev).  u_lo != nullptr: compensated form, u_cur ==
+// u_next = hi part, u_lo = lo part, u_prev = increment d, all in place.
 template <typename T>
 cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
-                        const T* u_prev, T* u_next, const T* phi2, void* S, T* W, cudaStream_t st,
+                        T* u_prev, T* u_next, T* u_lo, const T* phi2, void* S, T* W, cudaStream_t st,
                         cudaEvent_t* ev = nullptr);
 
 }  // namespace sadi

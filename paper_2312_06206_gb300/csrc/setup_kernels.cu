@@ -353,6 +353,37 @@ __global__ void k_border_G(const double* __restrict__ X, const double* __restric
   G32[idx] = (float)(-acc);
 }
 
+// Register-path tables.  tw1: exp(-2 pi i t k1 / Np) at [k1 * TT + t] with
+// TT = 2^floor(logNp/2); lreg[(k1 * 2 + h) * Np + m] = scale * Lambda(k1, 2m + h)
+// (natural order, k2 folded into [0, Np]); lam*_nat[k] = lam*[brev(k)].
+__global__ void k_reg_tables(Geom g, const double* __restrict__ lnat, double scale,
+                             const double2* __restrict__ lamc64, const double2* __restrict__ lams64, float2* tw1,
+                             float* lreg, float2* lamc_nat, float2* lams_nat) {
+  const int Np = g.Np, logNp = g.logNp, P = g.P;
+  const int logT = logNp / 2;
+  const int TT = 1 << logT;
+  const size_t nl = (size_t)(Np + 1) * 2 * Np;
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx < (size_t)Np) {
+    const int k = (int)idx;
+    const int t = k & (TT - 1), k1 = k >> logT;
+    double sn, cs;
+    sincospi(2.0 * (double)((long long)t * k1 % Np) / (double)Np, &sn, &cs);
+    tw1[k] = make_float2((float)cs, (float)-sn);
+    const double2 a = lamc64[brev(k, logNp)], b = lams64[brev(k, logNp)];
+    lamc_nat[k] = make_float2((float)a.x, (float)a.y);
+    lams_nat[k] = make_float2((float)b.x, (float)b.y);
+  }
+  if (idx < nl) {
+    const int m = (int)(idx % Np);
+    const int h = (int)((idx / Np) % 2);
+    const int k1 = (int)(idx / (2 * (size_t)Np));
+    int k2 = 2 * m + h;
+    if (k2 > Np) k2 = P - k2;
+    lreg[idx] = (float)(scale * lnat[(size_t)k1 * (Np + 1) + k2]);
+  }
+}
+
 __global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, size_t n) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k < n) d[k] = (float)s[k];
@@ -360,6 +391,25 @@ __global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, size_
 __global__ void k_f2d(const float* __restrict__ s, double* __restrict__ d, size_t n) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
   if (k < n) d[k] = (double)s[k];
+}
+
+__global__ void k_split_d2ff(const double* __restrict__ s, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k < n) {
+    const float h = (float)s[k];
+    hi[k] = h;
+    lo[k] = (float)(s[k] - (double)h);
+  }
+}
+__global__ void k_join_ff2d(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ d,
+                            size_t n) {
+  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k < n) d[k] = (double)hi[k] + (double)lo[k];
+}
+__global__ void k_join_ff2f(const float* __restrict__ hi, const float* __restrict__ lo, float* __restrict__ d,
+                            size_t n) {
+  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (k < n) d[k] = hi[k] + lo[k];
 }
 
 inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -377,6 +427,14 @@ cudaError_t launch_stage_twiddles(double2* stw64, float2* stw32, int logL, cudaS
   return cudaGetLastError();
 }
 
+cudaError_t run_reg_tables(const Geom& g, const double* lnat, double scale, const double2* lamc64,
+                           const double2* lams64, float2* tw1, float* lreg, float2* lamc_nat, float2* lams_nat,
+                           cudaStream_t st) {
+  const size_t nl = (size_t)(g.Np + 1) * 2 * g.Np;
+  k_reg_tables<<<nblk(nl, 256), 256, 0, st>>>(g, lnat, scale, lamc64, lams64, tw1, lreg, lamc_nat, lams_nat);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_riesz1d(double* a, int n, double alpha, cudaStream_t st) {
   k_riesz1d<<<1, 32, 0, st>>>(a, n, alpha);
   return cudaGetLastError();
@@ -387,6 +445,22 @@ cudaError_t launch_convert_d2f(const double* s, float* d, size_t n, cudaStream_t
   k_d2f<<<nblk(n, 256), 256, 0, st>>>(s, d, n);
   return cudaGetLastError();
 }
+cudaError_t launch_split_d2ff(const double* s, float* hi, float* lo, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_split_d2ff<<<nblk(n, 256), 256, 0, st>>>(s, hi, lo, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_join_ff2d(const float* hi, const float* lo, double* d, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_join_ff2d<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n);
+  return cudaGetLastError();
+}
+cudaError_t launch_join_ff2f(const float* hi, const float* lo, float* d, size_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  k_join_ff2f<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_convert_f2d(const float* s, double* d, size_t n, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   k_f2d<<<nblk(n, 256), 256, 0, st>>>(s, d, n);

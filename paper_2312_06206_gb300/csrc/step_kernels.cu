@@ -37,6 +37,23 @@ __device__ __forceinline__ T g_of(int kind, T u) {
   return T(0);
 }
 
+// u^{n+1} = u^n + d^{n+1}, d^{n+1} = d^n + uhat, with u a double-float pair
+// (hi = uc, lo); two-sum and fast-two-sum keep the rounding of the sum in lo.
+template <typename T>
+__device__ __forceinline__ void leapfrog_comp(T hi, T uh, int first, size_t idx, T* dbuf, T* hibuf, T* lobuf) {
+  const T d = first ? uh : dbuf[idx] + uh;
+  const T lo = lobuf[idx];
+  const T s = hi + d;
+  const T bb = s - hi;
+  const T err = (hi - (s - bb)) + (d - bb);
+  const T l2 = lo + err;
+  const T h2 = s + l2;
+  const T lo2 = l2 - (h2 - s);
+  hibuf[idx] = h2;
+  lobuf[idx] = lo2;
+  dbuf[idx] = d;
+}
+
 template <typename T>
 __device__ __forceinline__ T real_view(const cx<T>* v, int k) {
   const T* f = reinterpret_cast<const T*>(v + padi(k >> 1));
@@ -319,11 +336,14 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
 // k_cols_solve: per column i: y sweep uhat = H^-1 W_{:,i}, then the leapfrog
 // u^{n+1} = 2u^n - u^{n-1} + uhat (n >= 1) or u^1 = u^0 + uhat (n = 0).
 // u_next may alias u_prev (each element is read before it is written, by the
-// same thread).
+// same thread).  Compensated form (u_lo != nullptr, FP32): the state is the
+// double-float pair u = u_cur + u_lo and the increment d = u^n - u^{n-1} held
+// in u_prev; d^{n+1} = d^n + uhat (d^1 = uhat) and u^{n+1} = u^n + d^{n+1} by
+// an error-free two-sum, written in place (u_next == u_cur).
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
-k_cols_solve(const T* __restrict__ W, const T* __restrict__ u_cur, const T* u_prev, T* u_next, Geom g, int first,
+k_cols_solve(const T* __restrict__ W, const T* u_cur, T* u_prev, T* u_next, T* u_lo, Geom g, int first,
              const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s,
              const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int CT) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -350,7 +370,11 @@ k_cols_solve(const T* __restrict__ W, const T* __restrict__ u_cur, const T* u_pr
     const T uh = gs_out<T>(buf + c * vs, j, g, G);
     const size_t idx = (size_t)j * N + i;
     const T uc = u_cur[idx];
-    u_next[idx] = first ? uc + uh : (T(2) * uc - u_prev[idx]) + uh;
+    if (u_lo) {
+      leapfrog_comp<T>(uc, uh, first, idx, u_prev, u_next, u_lo);
+    } else {
+      u_next[idx] = first ? uc + uh : (T(2) * uc - u_prev[idx]) + uh;
+    }
   }
 }
 
@@ -397,7 +421,7 @@ bool tiles_valid(const Geom& g, const Tiles& t) {
 
 template <typename T>
 cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
-                        const T* u_prev, T* u_next, const T* phi2, void* Sv, T* W, cudaStream_t st,
+                        T* u_prev, T* u_next, T* u_lo, const T* phi2, void* Sv, T* W, cudaStream_t st,
                         cudaEvent_t* ev) {
   const cx<T>* stw = reinterpret_cast<const cx<T>*>(tb.stw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
@@ -415,7 +439,7 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   if (ev) cudaEventRecord(ev[2], st);
   k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR);
   if (ev) cudaEventRecord(ev[3], st);
-  k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, g, rp.first,
+  k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, u_lo, g, rp.first,
                                                                           stw, tw, ls, lc, tb.G, CTs);
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
@@ -428,12 +452,10 @@ template Tiles default_tiles<double>(int);
 template bool tiles_valid<float>(const Geom&, const Tiles&);
 template bool tiles_valid<double>(const Geom&, const Tiles&);
 template cudaError_t launch_step<float>(const Geom&, const StepTables<float>&, const Tiles&, const RhsParams&,
-                                        const float*,
-                                        const float*, float*, const float*, void*, float*, cudaStream_t,
-                                        cudaEvent_t*);
+                                        const float*, float*, float*, float*, const float*, void*, float*,
+                                        cudaStream_t, cudaEvent_t*);
 template cudaError_t launch_step<double>(const Geom&, const StepTables<double>&, const Tiles&, const RhsParams&,
-                                         const double*,
-                                         const double*, double*, const double*, void*, double*, cudaStream_t,
-                                         cudaEvent_t*);
+                                         const double*, double*, double*, double*, const double*, void*, double*,
+                                         cudaStream_t, cudaEvent_t*);
 
 }  // namespace sadi

@@ -1,0 +1,467 @@
+// step_reg.cuh -- the S-ADI step (Sec. 3, eq. "ADI scheme equivalent") for
+// FFT lengths N' <= 1024 with the register-resident two-level FFT of
+// regfft.cuh.  Same four kernels and the same mathematics as step_kernels.cu:
+//   kr_rows_r2c    rows of u^n -> half spectrum along x (natural slots)
+//   kr_cols_conv   per x frequency: y FFT (even/odd halves) x symbol, inverse
+//   kr_rows_solve  inverse real FFT + B^n epilogue + x sweep (Algorithm 1)
+//   kr_cols_solve  y sweep (Algorithm 1) + leapfrog
+// Spectra are in natural order here (slot k holds x-frequency k, slot 0 holds
+// X[0] + i X[N']); all spectral tables are natural-order copies of the FP64
+// setup products.
+#pragma once
+#include <cuda_runtime.h>
+
+#include "regfft.cuh"
+#include "sadi_internal.h"
+
+namespace sadi {
+namespace regk {
+
+using rf::static_for;
+
+template <typename T>
+__device__ __forceinline__ T g_of_r(int kind, T u) {
+  if (kind == 1) return -u * u * u;
+  if (kind == 2) return -sin(u);
+  return T(0);
+}
+
+__host__ __device__ constexpr int pad32(int k) { return k + (k >> 5); }
+
+// elements of one vector's shared buffer, rounded so that buffers of
+// consecutive vectors start on staggered banks (8-byte elements, 16 per 128 B)
+template <int LOGL>
+__host__ __device__ constexpr int vec_smem(int res) {
+  using F = rf::RegFFT<float, LOGL>;
+  int n = F::E * F::ROW;
+  if (n < pad32(F::L) + 1) n = pad32(F::L) + 1;
+  while ((n & 15) != res) ++n;
+  return n;
+}
+template <int LOGL, int BLOCK>
+struct RowCfg {
+  using F = rf::RegFFT<float, LOGL>;
+  static constexpr int VB = BLOCK / F::TT;                    // vectors (rows) per block
+  static constexpr int SMV = vec_smem<LOGL>(F::TT & 15);      // transform buffer (float2)
+  static constexpr int STG = F::L;                            // staged u / phi2 row (floats)
+  static constexpr size_t bytes_r2c = (size_t)VB * SMV * sizeof(float2);
+  static constexpr size_t bytes_solve = (size_t)VB * (SMV * sizeof(float2) + 2 * STG * sizeof(float));
+};
+template <int LOGL, int BLOCK>
+struct ColCfg {
+  using F = rf::RegFFT<float, LOGL>;
+  static constexpr int CT = BLOCK / F::TT;                    // vectors (columns) per block
+  static constexpr int SMV = vec_smem<LOGL>(CT >= 32 ? 1 : (32 / CT) & 15);
+  static constexpr int STG = F::L;                            // staged state column (floats)
+  static constexpr size_t bytes_conv = (size_t)CT * SMV * sizeof(float2);
+  static constexpr size_t bytes_solve = (size_t)CT * (SMV * sizeof(float2) + 3 * STG * sizeof(float));
+};
+
+// Asynchronous global -> shared copies (Ampere+ cp.async); a false predicate
+// zero-fills the destination without reading global memory.
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = pred ? 4 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = pred ? 8 : 0;
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Gohberg-Semencul core (Algorithm 1 on the bordered matrix): x natural
+// (x[q] = Q v1 at t + TT q) -> x natural (vhat).  lam tables natural order.
+template <int LOGL>
+__device__ __forceinline__ void gs_reg(float2* x, float2* sm, int t, const float2* __restrict__ tw1,
+                                       const float2* __restrict__ tw, const float2* __restrict__ lam_s,
+                                       const float2* __restrict__ lam_c) {
+  using F = rf::RegFFT<float, LOGL>;
+  // round 0: x lambda_s then Q^H; round 1: x lambda_c.  Rolled so that the
+  // kernel holds one forward and one inverse transform body.
+#pragma unroll 1
+  for (int round = 0; round < 2; ++round) {
+    const float2* lam = round == 0 ? lam_s : lam_c;
+    F::fwd(x, sm, t, tw1);
+    static_for<0, F::E>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      x[r] = cmul(x[r], __ldg(&lam[F::template freq_index<r>(t)]));
+    });
+    F::inv(x, sm, t, tw1);
+    if (round == 0) {
+      static_for<0, F::E>([&](auto qc) {
+        constexpr int q = decltype(qc)::value;
+        x[q] = cmulc(x[q], __ldg(&tw[t + F::TT * q]));       // Q^H
+      });
+    }
+  }
+}
+
+// Register <-> shared-memory moves (the only per-element code that is
+// unrolled; all per-element arithmetic outside the transforms runs in
+// runtime loops over shared memory to keep the kernels small).
+template <int LOGL>
+__device__ __forceinline__ void store_nat(const float2* x, float2* sm, int t) {
+  using F = rf::RegFFT<float, LOGL>;
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    sm[pad32(t + F::TT * q)] = x[q];
+  });
+}
+template <int LOGL>
+__device__ __forceinline__ void load_nat(float2* x, const float2* sm, int t) {
+  using F = rf::RegFFT<float, LOGL>;
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    x[q] = sm[pad32(t + F::TT * q)];
+  });
+}
+template <int LOGL>
+__device__ __forceinline__ void store_freq(const float2* x, float2* sm, int t) {
+  using F = rf::RegFFT<float, LOGL>;
+  static_for<0, F::E>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    sm[pad32(F::template freq_index<r>(t))] = x[r];
+  });
+}
+template <int LOGL>
+__device__ __forceinline__ void load_freq(float2* x, const float2* sm, int t) {
+  using F = rf::RegFFT<float, LOGL>;
+  static_for<0, F::E>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    x[r] = sm[pad32(F::template freq_index<r>(t))];
+  });
+}
+__device__ __forceinline__ float real_at(const float2* sm, int k) {
+  return reinterpret_cast<const float*>(sm + pad32(k >> 1))[k & 1];
+}
+
+// ---------------------------------------------------------------------------
+// Every kernel handles one instance per blockIdx.y (a batch of independent
+// problems with the same FFT length); blocks beyond an instance's extent exit.
+template <int LOGL, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ RegBatch B) {
+  using F = rf::RegFFT<float, LOGL>;
+  using C = RowCfg<LOGL, BLOCK>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RegInst& I = B.in[blockIdx.y];
+  const int N = I.N;
+  if ((int)blockIdx.x * C::VB >= N) return;
+  const int v = threadIdx.x / F::TT, t = threadIdx.x % F::TT;
+  const int row = blockIdx.x * C::VB + v;
+  const bool valid = row < N;
+  float2* sm = reinterpret_cast<float2*>(smem_raw) + v * C::SMV;
+  const float* ur = I.u_hi + (size_t)(valid ? row : 0) * N;
+  float2 x[F::E];
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int n = t + F::TT * q;
+    const float a = (valid && 2 * n < N) ? ur[2 * n] : 0.f;
+    const float b = (valid && 2 * n + 1 < N) ? ur[2 * n + 1] : 0.f;
+    x[q] = make_float2(a, b);
+  });
+  F::fwd(x, sm, t, I.tw1);
+  store_freq<LOGL>(x, sm, t);
+  __syncthreads();
+  if (!valid) return;
+  float2* srow = I.S + (size_t)row * F::L;
+#pragma unroll 2
+  for (int q = 0; q < F::E; ++q) {
+    const int k = t + F::TT * q;
+    const float2 Z = sm[pad32(k)];
+    const float2 Zc = cconj(sm[pad32((F::L - k) & (F::L - 1))]);
+    const float2 Ev = cscale(cadd(Z, Zc), 0.5f);
+    const float2 Ov = cscale(cmul_mi(csub(Z, Zc)), 0.5f);
+    srow[k] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(__ldg(&I.tw[k]), Ov));
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Items: 0 = x-frequency 0 (real part of slot 0), 1 = x-frequency N' (imag part
+// of slot 0), i >= 2 = x-frequency i - 1 (slot i - 1).  Each item has two
+// vectors (even / odd y-frequency halves) in consecutive columns c = 2 i + h.
+template <int LOGL, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__ RegBatch B) {
+  using F = rf::RegFFT<float, LOGL>;
+  using C = ColCfg<LOGL, BLOCK>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RegInst& I = B.in[blockIdx.y];
+  const int N = I.N, Np = F::L;
+  const int c = threadIdx.x % C::CT, t = threadIdx.x / C::CT;
+  const int item = blockIdx.x * (C::CT / 2) + (c >> 1);
+  const int h = c & 1;
+  const bool valid = item <= Np;
+  const int k1 = (item == 0) ? 0 : (item == 1 ? Np : item - 1);
+  const int slot = (item <= 1 || !valid) ? 0 : item - 1;
+  float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int j = t + F::TT * q;
+    const bool in = valid && j < N;
+    cp_async8(&sm[pad32(j)], I.S + (size_t)(in ? j : 0) * Np + slot, in);
+  });
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  float2 x[F::E];
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int j = t + F::TT * q;
+    float2 val = sm[pad32(j)];
+    if (item == 0) val.y = 0.f;
+    else if (item == 1) val = make_float2(val.y, 0.f);
+    if (h) val = cmul(val, __ldg(&I.tw[j]));
+    x[q] = val;
+  });
+  __syncthreads();
+  F::fwd(x, sm, t, I.tw1);
+  const float* lrow = I.lreg + ((size_t)(valid ? k1 : 0) * 2 + h) * Np;
+  static_for<0, F::E>([&](auto rc) {
+    constexpr int r = decltype(rc)::value;
+    x[r] = cscale(x[r], __ldg(&lrow[F::template freq_index<r>(t)]));
+  });
+  F::inv(x, sm, t, I.tw1);
+  store_nat<LOGL>(x, sm, t);
+  __syncthreads();
+  if (!valid || h != 0 || item == 1) return;
+  const float2* smo = sm + C::SMV;
+#pragma unroll 2
+  for (int q = 0; q < F::E; ++q) {
+    const int j = t + F::TT * q;
+    if (j < N) {
+      const float2 w = __ldg(&I.tw[j]);
+      const float2 y = cadd(sm[pad32(j)], cmulc(smo[pad32(j)], w));
+      if (item == 0) {
+        // the x-frequency N' result lives in the next item's two vectors
+        const float2 yn = cadd(sm[2 * C::SMV + pad32(j)], cmulc(sm[3 * C::SMV + pad32(j)], w));
+        I.S[(size_t)j * Np] = make_float2(y.x, yn.x);
+      } else {
+        I.S[(size_t)j * Np + slot] = y;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int LOGL, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant__ RegBatch B) {
+  using F = rf::RegFFT<float, LOGL>;
+  using C = RowCfg<LOGL, BLOCK>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RegInst& I = B.in[blockIdx.y];
+  const int N = I.N, Np = F::L;
+  if ((int)blockIdx.x * C::VB >= N) return;
+  const int v = threadIdx.x / F::TT, t = threadIdx.x % F::TT;
+  const int row = blockIdx.x * C::VB + v;
+  const bool valid = row < N;
+  const int rrow = valid ? row : 0;
+  float2* sm = reinterpret_cast<float2*>(smem_raw) + v * C::SMV;
+  float* us = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV) + v * 2 * C::STG;
+  float* ps = us + C::STG;
+  // stage the spectrum row, u^n row and (first step) phi2 row
+  const float2* srow = I.S + (size_t)rrow * Np;
+  const float* ur = I.u_hi + (size_t)rrow * N;
+  const float* pr = I.phi2 + (size_t)rrow * N;
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int k = t + F::TT * q;
+    cp_async8(&sm[pad32(k)], srow + k, valid);
+    cp_async4(&us[k], ur + (k < N ? k : 0), valid && k < N);
+    if (I.first) cp_async4(&ps[k], pr + (k < N ? k : 0), valid && k < N);
+  });
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncthreads();
+  // half spectrum X[k] -> Z[k] = E + i O (spectrum of z[n] = x[2n] + i x[2n+1]),
+  // in place on partner pairs (k, Np - k)
+#pragma unroll 2
+  for (int q = 0; q <= F::E / 2; ++q) {
+    const int k = t + F::TT * q;
+    if (k > Np / 2 || (q == F::E / 2 && k != Np / 2)) continue;
+    if (k == 0) {
+      const float2 X0 = sm[pad32(0)];
+      sm[pad32(0)] = make_float2(0.5f * (X0.x + X0.y), 0.5f * (X0.x - X0.y));
+      continue;
+    }
+    const int kp = Np - k;
+    const float2 X = sm[pad32(k)], Xq = sm[pad32(kp)];
+    const float2 Ev = cscale(cadd(X, cconj(Xq)), 0.5f);
+    const float2 Ov = cscale(cmulc(csub(X, cconj(Xq)), __ldg(&I.tw[k])), 0.5f);
+    sm[pad32(k)] = cadd(Ev, cmul_pi(Ov));
+    if (kp != k) {
+      const float2 Eq = cscale(cadd(Xq, cconj(X)), 0.5f);
+      const float2 Oq = cscale(cmulc(csub(Xq, cconj(X)), __ldg(&I.tw[kp])), 0.5f);
+      sm[pad32(kp)] = cadd(Eq, cmul_pi(Oq));
+    }
+  }
+  __syncthreads();
+  float2 x[F::E];
+  load_freq<LOGL>(x, sm, t);
+  __syncthreads();
+  F::inv(x, sm, t, I.tw1);
+  store_nat<LOGL>(x, sm, t);
+  __syncthreads();
+  // B^n in place: sm[n] holds the convolution at 2n, 2n+1 (real view)
+  const float tau = I.tau, tau2 = I.tau2;
+#pragma unroll 1
+  for (int q = 0; q < F::E; ++q) {
+    const int n = t + F::TT * q;
+    const float2 cv = sm[pad32(n)];
+    float b0 = 0.f, b1 = 0.f;
+    if (valid && 2 * n < N) {
+      const float gg = tau2 * g_of_r<float>(I.gkind, us[2 * n]);
+      b0 = I.first ? tau * ps[2 * n] + 0.5f * (cv.x + gg) : cv.x + gg;
+    }
+    if (valid && 2 * n + 1 < N) {
+      const float gg = tau2 * g_of_r<float>(I.gkind, us[2 * n + 1]);
+      b1 = I.first ? tau * ps[2 * n + 1] + 0.5f * (cv.y + gg) : cv.y + gg;
+    }
+    sm[pad32(n)] = make_float2(b0, b1);
+  }
+  __syncthreads();
+  // v1 = Q (B' + i J B')
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int k = t + F::TT * q;
+    x[q] = cmul(make_float2(real_at(sm, k), real_at(sm, Np - 1 - k)), __ldg(&I.tw[k]));
+  });
+  __syncthreads();
+  gs_reg<LOGL>(x, sm, t, I.tw1, I.tw, I.lam_s, I.lam_c);
+  store_nat<LOGL>(x, sm, t);
+  __syncthreads();
+  if (!valid) return;
+  // (H^-1 B)[k] = Re vhat[k] + Im vhat[Np-1-k] + sum_q G[k,q] ybot[q],
+  // ybot[q] = Re vhat[N+q] + Im vhat[r-1-q]
+  const int r = I.r;
+  float* wrow = I.W + (size_t)row * N;
+#pragma unroll 2
+  for (int q = 0; q < F::E; ++q) {
+    const int k = t + F::TT * q;
+    if (k < N) {
+      float y = sm[pad32(k)].x + sm[pad32(Np - 1 - k)].y;
+      for (int qq = 0; qq < r; ++qq)
+        y += __ldg(&I.G[(size_t)k * r + qq]) * (sm[pad32(N + qq)].x + sm[pad32(r - 1 - qq)].y);
+      wrow[k] = y;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+template <int LOGL, int BLOCK>
+__global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant__ RegBatch B) {
+  using F = rf::RegFFT<float, LOGL>;
+  using C = ColCfg<LOGL, BLOCK>;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const RegInst& I = B.in[blockIdx.y];
+  const int N = I.N, Np = F::L;
+  if ((int)blockIdx.x * C::CT >= N) return;
+  const int c = threadIdx.x % C::CT, t = threadIdx.x / C::CT;
+  const int i = blockIdx.x * C::CT + c;
+  const bool valid = i < N;
+  const int ii = valid ? i : 0;
+  float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
+  // 4-byte staging arrays are interleaved by column ([k * CT + c]) so that a
+  // warp (CT columns x 32/CT consecutive k) touches 32 consecutive words.
+  float* st = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::CT * C::SMV);
+  float* s_hi = st;
+  float* s_lo = st + C::CT * C::STG;
+  float* s_d = st + 2 * C::CT * C::STG;
+  float* wc = reinterpret_cast<float*>(smem_raw);       // W column, in the transform buffers
+  // stage the W column (needed now) and the state column (needed at the end)
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int k = t + F::TT * q;
+    const bool in = valid && k < N;
+    const size_t gi = (size_t)(in ? k : 0) * N + ii;
+    cp_async4(&wc[k * C::CT + c], I.W + gi, in);
+  });
+  cp_async_commit();
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int k = t + F::TT * q;
+    const bool in = valid && k < N;
+    const size_t gi = (size_t)(in ? k : 0) * N + ii;
+    cp_async4(&s_hi[k * C::CT + c], I.u_hi + gi, in);
+    cp_async4(&s_lo[k * C::CT + c], I.u_lo + gi, in);
+    cp_async4(&s_d[k * C::CT + c], I.u_d + gi, in && !I.first);
+  });
+  cp_async_commit();
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // the W column has landed
+  __syncthreads();
+  float2 x[F::E];
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int k = t + F::TT * q;
+    x[q] = cmul(make_float2(wc[k * C::CT + c], wc[(Np - 1 - k) * C::CT + c]), __ldg(&I.tw[k]));
+  });
+  __syncthreads();
+  gs_reg<LOGL>(x, sm, t, I.tw1, I.tw, I.lam_s, I.lam_c);
+  store_nat<LOGL>(x, sm, t);
+  cp_async_wait_all();
+  __syncthreads();
+  if (!valid) return;
+  const int r = I.r;
+  const int first = I.first;
+#pragma unroll 2
+  for (int q = 0; q < F::E; ++q) {
+    const int j = t + F::TT * q;
+    if (j < N) {
+      float uh = sm[pad32(j)].x + sm[pad32(Np - 1 - j)].y;
+      for (int qq = 0; qq < r; ++qq)
+        uh += __ldg(&I.G[(size_t)j * r + qq]) * (sm[pad32(N + qq)].x + sm[pad32(r - 1 - qq)].y);
+      // compensated leapfrog: d^{n+1} = d^n + uhat (d^1 = uhat), u^{n+1} = u^n + d^{n+1}
+      // with u = u_hi + u_lo kept as a double-float pair (two-sum)
+      const float d = first ? uh : s_d[j * C::CT + c] + uh;
+      const float hi = s_hi[j * C::CT + c], lo = s_lo[j * C::CT + c];
+      const float s = hi + d;
+      const float bb = s - hi;
+      const float err = (hi - (s - bb)) + (d - bb);
+      const float l2 = lo + err;
+      const float h2 = s + l2;
+      const size_t idx = (size_t)j * N + i;
+      I.u_hi[idx] = h2;
+      I.u_lo[idx] = l2 - (h2 - s);
+      I.u_d[idx] = d;
+    }
+  }
+}
+
+constexpr int kRowBlock = 128;
+constexpr int kColBlock = 128;
+
+template <int LOGL>
+cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev) {
+  using RC = RowCfg<LOGL, kRowBlock>;
+  using CC = ColCfg<LOGL, kColBlock>;
+  constexpr int Np = 1 << LOGL;
+  static bool attr_done = false;
+  if (!attr_done) {
+    cudaFuncSetAttribute(kr_rows_r2c<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RC::bytes_r2c);
+    cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RC::bytes_solve);
+    cudaFuncSetAttribute(kr_cols_conv<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)CC::bytes_conv);
+    cudaFuncSetAttribute(kr_cols_solve<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)CC::bytes_solve);
+    attr_done = true;
+  }
+  const dim3 rgrid((max_n + RC::VB - 1) / RC::VB, b.count);
+  const dim3 cgrid((Np + 1 + CC::CT / 2 - 1) / (CC::CT / 2), b.count);
+  const dim3 sgrid((max_n + CC::CT - 1) / CC::CT, b.count);
+  if (ev) cudaEventRecord(ev[0], st);
+  kr_rows_r2c<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_r2c, st>>>(b);
+  if (ev) cudaEventRecord(ev[1], st);
+  kr_cols_conv<LOGL, kColBlock><<<cgrid, kColBlock, CC::bytes_conv, st>>>(b);
+  if (ev) cudaEventRecord(ev[2], st);
+  kr_rows_solve<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
+  if (ev) cudaEventRecord(ev[3], st);
+  kr_cols_solve<LOGL, kColBlock><<<sgrid, kColBlock, CC::bytes_solve, st>>>(b);
+  if (ev) cudaEventRecord(ev[4], st);
+  return cudaGetLastError();
+}
+
+}  // namespace regk
+}  // namespace sadi

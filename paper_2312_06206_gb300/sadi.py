@@ -29,6 +29,7 @@ _SIGS = {
     "sadi_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sadi_set_initial": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sadi_step": (C.c_int, [C.c_void_p, C.c_int]),
+    "sadi_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
     "sadi_get": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
     "sadi_get_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sadi_get_setup": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
@@ -81,6 +82,15 @@ def _f64(a, N):
     if a.shape != (N, N):
         raise ValueError(f"expected shape {(N, N)}, got {a.shape}")
     return a
+
+
+def sadi_batch_step(instances, nsteps: int = 1):
+    """Advance several Sadi instances together (same stream); see sadi.h."""
+    arr = (C.c_void_p * len(instances))(*[s.ctx for s in instances])
+    st = lib().sadi_batch_step(arr, len(instances), int(nsteps))
+    if st != SADI_OK:
+        msgs = [s.sadi_last_error() for s in instances]
+        raise SadiError(st, "; ".join(m for m in msgs if m) or "invalid batch")
 
 
 class Sadi:

@@ -143,3 +143,57 @@ def test_state_errors(S):
         s.step(0)
         u, n = s.get()
         assert n == 0 and not u.any()
+
+
+def test_batch_step_matches_single_contexts(S):
+    # FP32 contexts of equal FFT length (N = 63, 50, 33 -> N' = 64) go through
+    # one batched launch per kernel; an FP64 context steps on its own.  The
+    # batch must reproduce single-context stepping bitwise.
+    specs = [(63, 1.5, 1.0, 0.02, 1, 1), (50, 1.2, 0.7, 0.03, 2, 1), (33, 1.8, 1.3, 0.01, 0, 1),
+             (40, 1.6, 1.0, 0.02, 1, 0)]
+
+    def make():
+        out = []
+        for k, (N, al, ka, ta, g, prec) in enumerate(specs):
+            s = S.Sadi(N, al, ka, ta)
+            s.set_options(g, prec)
+            s.set_initial(WL.gaussian_bumps(N, 4, 300 + k), 0.3 * WL.random_field(N, 400 + k))
+            out.append(s)
+        return out
+    single = make()
+    for s in single:
+        s.step(6)
+    ref = [s.get()[0] for s in single]
+    batch = make()
+    S.sadi_batch_step(batch, 6)
+    for s, r in zip(batch, ref):
+        u, n = s.get()
+        assert n == 6 and np.array_equal(u, r)
+    for s in single + batch:
+        s.close()
+
+
+def test_batch_step_rejects_bad_batches(S):
+    a = S.Sadi(31, 1.5, 1.0, 0.1)
+    b = S.Sadi(31, 1.5, 1.0, 0.1)
+    a.set_initial(np.zeros((31, 31)))
+    with pytest.raises(S.SadiError):
+        S.sadi_batch_step([a, a], 1)          # duplicate
+    with pytest.raises(S.SadiError):
+        S.sadi_batch_step([a, b], 1)          # b not initialised
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("alpha,ref", [(1.1, 6.3150e-02), (1.5, 8.1276e-02), (1.9, 1.0716e-01)])
+def test_paper_table2_through_the_c_abi(S, alpha, ref):
+    # Sec. 6 Table 2 (Example 1, sine-Gordon, S-ADI): h = 1 (N = 19) against
+    # h = 1/2 (N = 39), tau = 1/100, t = 5, on Omega = (-10, 10)^2, FP64 path.
+    # N' = 32 and 64: border ranks r = 13 and 25 exercise the rank-r correction.
+    us = []
+    for N in (19, 39):
+        w = WL.paper_example1(N, alpha, 1 / 100)
+        us.append(_run_gpu(S, N, alpha, w.kappa, w.tau, w.g, w.phi1, w.phi2, w.steps, S.SADI_PREC_FP64,
+                           dom=(w.a, w.b)))
+    e = O.error2(1.0, us[0], us[1])
+    assert abs(e - ref) <= 0.5 * 10 ** (np.floor(np.log10(ref)) - 4), (e, ref)
