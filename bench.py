@@ -36,9 +36,22 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-N_DEFAULT = 1023
-ALPHAS = (1.2, 1.5, 1.8)
-KAPPA, TAU = 1.0, 1e-3
+# Workload presets (Omega = (-1, 1)^2, seeded Gaussian-bump phi1).  "n1023" is
+# the default bench workload; the others are single large instances run on
+# request (--workload).
+PRESETS = {
+    "n1023": dict(N=1023, alphas=(1.2, 1.5, 1.8), kappa=1.0, tau=1e-3, g=2, bumps=8, phi2=0.0, seed=2,
+                  total_steps=1000),
+    "n4095": dict(N=4095, alphas=(1.7,), kappa=0.5, tau=5e-4, g=1, bumps=8, phi2=0.0, seed=3, total_steps=2000),
+    "n8191": dict(N=8191, alphas=(1.6,), kappa=1.0, tau=2.5e-4, g=2, bumps=32, phi2=0.1, seed=5,
+                  total_steps=500),
+}
+CFG = PRESETS["n1023"]
+N_DEFAULT = CFG["N"]
+ALPHAS = CFG["alphas"]
+KAPPA, TAU = CFG["kappa"], CFG["tau"]
+GKIND = CFG["g"]
+GNAME = {0: "0", 1: "-u^3", 2: "-sin(u)"}
 METRIC = "grid-point updates/s (N^2*steps/s)"
 UNIT = "pt/s"
 
@@ -49,7 +62,8 @@ def _args():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--N", type=int, default=N_DEFAULT)
+    ap.add_argument("--workload", default="n1023", choices=sorted(PRESETS))
+    ap.add_argument("--N", type=int, default=None, help="override the preset's N")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--acc-steps", type=int, default=1000,
                     help="steps of the accuracy check (FP32 form vs plain FP64 from the same data)")
@@ -63,17 +77,31 @@ def _dist():
     return ws, rank, local
 
 
+def _select(a):
+    """Apply the chosen preset to the module-level workload constants."""
+    global CFG, ALPHAS, KAPPA, TAU, GKIND
+    CFG = dict(PRESETS[a.workload])
+    if a.N is not None:
+        CFG["N"] = a.N
+    a.N = CFG["N"]
+    ALPHAS, KAPPA, TAU, GKIND = CFG["alphas"], CFG["kappa"], CFG["tau"], CFG["g"]
+
+
 def _workload(N):
     from paper_2312_06206_gb300 import workloads as WL
-    phi1 = WL.gaussian_bumps(N, 8, WL.SEED_BASE + 2)
-    return phi1
+    return WL.gaussian_bumps(N, CFG["bumps"], WL.SEED_BASE + CFG["seed"])
+
+
+def _phi2(phi1):
+    return None if CFG["phi2"] == 0.0 else CFG["phi2"] * phi1
 
 
 def _config(N, extra=None):
-    cfg = {"workload": f"sadi-step N={N} alpha={{1.2,1.5,1.8}} kappa=1 tau=1e-3 g=-sin(u) "
-                       f"phi1=8 gaussian bumps phi2=0",
+    al = ",".join(str(x) for x in ALPHAS)
+    cfg = {"workload": f"sadi-step N={N} alpha={{{al}}} kappa={KAPPA:g} tau={TAU:g} g={GNAME[GKIND]} "
+                       f"phi1={CFG['bumps']} gaussian bumps phi2={CFG['phi2']:g}*phi1",
            "N": N, "instances": len(ALPHAS), "alphas": list(ALPHAS), "kappa": KAPPA, "tau": TAU,
-           "g": "-sin(u)", "domain": [-1.0, 1.0]}
+           "g": GNAME[GKIND], "domain": [-1.0, 1.0]}
     if extra:
         cfg.update(extra)
     return cfg
@@ -138,10 +166,11 @@ def cpu_baseline(N, phi1, nsteps=3, alpha=1.5):
     S-ADI steps (n >= 1 formula) of one instance; the problem set-up and the
     n = 0 start step are not timed."""
     from oracle import sadi as O
-    P = O.Problem(N, alpha, KAPPA, TAU, -1.0, 1.0, O.G_NEG_SIN)
+    P = O.Problem(N, alpha, KAPPA, TAU, -1.0, 1.0, GKIND)
     import numpy as np
     u0 = np.array(phi1)
-    u1 = O.step(P, None, u0, True, np.zeros_like(u0), tier="fft")
+    p2 = _phi2(phi1)
+    u1 = O.step(P, None, u0, True, np.zeros_like(u0) if p2 is None else p2, tier="fft")
     t0 = time.perf_counter()
     up, uc = u0, u1
     for _ in range(nsteps):
@@ -156,6 +185,7 @@ def cpu_baseline(N, phi1, nsteps=3, alpha=1.5):
 # --------------------------------------------------------- reference arm -----
 
 def run_reference(a):
+    _select(a)
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
@@ -163,11 +193,12 @@ def run_reference(a):
     from oracle import sadi as O
     N = a.N
     phi1 = _workload(N)
-    probs = [O.Problem(N, al, KAPPA, TAU, -1.0, 1.0, O.G_NEG_SIN) for al in ALPHAS]
+    probs = [O.Problem(N, al, KAPPA, TAU, -1.0, 1.0, GKIND) for al in ALPHAS]
     states = []
+    p2 = _phi2(phi1)
     for P in probs:
         u0 = phi1.copy()
-        u1 = O.step(P, None, u0, True, np.zeros_like(u0), tier="fft")
+        u1 = O.step(P, None, u0, True, np.zeros_like(u0) if p2 is None else p2, tier="fft")
         states.append([u0, u1])
 
     def one(k):
@@ -228,6 +259,7 @@ def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
+    _select(a)
     ws, rank, local = _dist()
     import numpy as np
     import torch
@@ -257,9 +289,9 @@ def main():
         ctxs = []
         for al in ALPHAS:
             s = S.Sadi(N, al, KAPPA, TAU, (-1.0, 1.0))
-            s.set_options(S.SADI_G_NEG_SIN, prec)
+            s.set_options(GKIND, prec)
             s.set_stream(stream.cuda_stream)
-            s.set_initial(phi1, None)
+            s.set_initial(phi1, _phi2(phi1))
             ctxs.append(s)
         return ctxs
 
@@ -292,9 +324,10 @@ def main():
     # plain FP64 GS-FFT path
     sampler = ClockSampler(local)
     sampler.start()
-    c64 = make(S.SADI_PREC_FP64)
+    has64 = N <= 4096                      # the FP64 step path supports N <= 4096
+    c64 = make(S.SADI_PREC_FP64) if has64 else []
     K64 = max(1, min(a.steps, 20))
-    ms64, _ = timed(c64, K64, a.warmup)
+    ms64 = timed(c64, K64, a.warmup)[0] if has64 else float("nan")
     # chosen form: FP32 FFTs and sweeps
     c32 = make(S.SADI_PREC_FP32)
     ms32, _ = timed(c32, a.steps, a.warmup)
@@ -302,16 +335,16 @@ def main():
     # accuracy of the chosen form against the plain FP64 path after the same
     # number of steps from the same data
     extra = a.warmup + a.steps - (a.warmup + K64)
-    for _ in range(max(0, extra)):
-        for s in c64:
-            s.step(1)
+    if has64 and extra > 0:
+        S.sadi_batch_step(c64, extra)
     rels = []
+    nsteps_cmp = None
     for s64, s32 in zip(c64, c32):
         u64, n64 = s64.get()
         u32, n32 = s32.get()
         assert n64 == n32
         rels.append(float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)))
-    nsteps_cmp = n32
+        nsteps_cmp = n32
     # per-kernel timing (separate profiled pass) for the roofline
     Kp = max(5, min(a.steps, 20))
     _, (phase_ms, _) = timed(c32, Kp, 0, profile=True)
@@ -342,6 +375,8 @@ def main():
     # e2e through the public API with host buffers: set_initial from pinned
     # host arrays, then every step sadi_step(1) + sadi_get into pinned host.
     pin_in = torch.from_numpy(phi1).pin_memory()
+    p2h = _phi2(phi1)
+    pin_in2 = None if p2h is None else torch.from_numpy(np.ascontiguousarray(p2h)).pin_memory()
     pin_out = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in ALPHAS]
     Ke = max(3, min(a.steps, 20))
     import ctypes
@@ -350,7 +385,8 @@ def main():
     barrier()
     t0 = time.perf_counter()
     for s in c32:
-        st = lib.sadi_set_initial(s.ctx, ctypes.c_void_p(pin_in.data_ptr()), None)
+        st = lib.sadi_set_initial(s.ctx, ctypes.c_void_p(pin_in.data_ptr()),
+                                  None if pin_in2 is None else ctypes.c_void_p(pin_in2.data_ptr()))
         assert st == 0, s.sadi_last_error()
     arr = (ctypes.c_void_p * len(c32))(*[s.ctx for s in c32])
     for k in range(Ke):
@@ -359,13 +395,13 @@ def main():
             assert lib.sadi_get(s.ctx, ctypes.c_void_p(pin_out[i].data_ptr()), ctypes.byref(nll)) == 0
     dt_e2e = time.perf_counter() - t0
     barrier()
-    h2d = len(ALPHAS) * N * N * 8 / Ke
+    h2d = len(ALPHAS) * N * N * 8 * (1 if pin_in2 is None else 2) / Ke
     d2h = len(ALPHAS) * N * N * 8
     # accuracy at the workload's full step count: both forms from phi1
     rel_full = None
-    if a.acc_steps > 0:
+    if a.acc_steps > 0 and has64:
         for s in c64 + c32:
-            s.set_initial(phi1, None)
+            s.set_initial(phi1, _phi2(phi1))
         S.sadi_batch_step(c64 + c32, a.acc_steps)
         rel_full = []
         for s64, s32 in zip(c64, c32):
@@ -379,24 +415,25 @@ def main():
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         return [float(x) for x in tt.tolist()]
     pts = N * N * len(ALPHAS)
-    agg = aggregate([ms32, ms64, dt_e2e], ws, pts, (a.steps, K64, Ke), reduce_max)
+    agg = aggregate([ms32, ms64 if has64 else 1.0, dt_e2e], ws, pts, (a.steps, K64, Ke), reduce_max)
     ms32m, ms64m = agg["ms32"], agg["ms64"]
     value, value64, e2e_val = agg["value"], agg["value64"], agg["e2e"]
     if rank == 0:
         cpu = None
         rel_oracle = None
-        if ws == 1 and not a.no_cpu_baseline:
-            cpu, (u0, u1, uK) = cpu_baseline(N, phi1)
+        rel_oracle32 = None
+        if ws == 1 and not a.no_cpu_baseline and a.workload == "n1023":
+            cpu, (u0, u1, uK) = cpu_baseline(N, phi1, alpha=ALPHAS[len(ALPHAS) // 2])
             # FP64 GPU path vs the oracle after the same 1 + 3 steps (alpha=1.5)
-            with S.Sadi(N, 1.5, KAPPA, TAU, (-1.0, 1.0)) as s:
-                s.set_options(S.SADI_G_NEG_SIN, S.SADI_PREC_FP64)
-                s.set_initial(phi1, None)
+            with S.Sadi(N, ALPHAS[len(ALPHAS) // 2], KAPPA, TAU, (-1.0, 1.0)) as s:
+                s.set_options(GKIND, S.SADI_PREC_FP64)
+                s.set_initial(phi1, _phi2(phi1))
                 s.step(4)
                 ug, _ = s.get()
                 rel_oracle = float(np.linalg.norm(ug - uK) / np.linalg.norm(uK))
-            with S.Sadi(N, 1.5, KAPPA, TAU, (-1.0, 1.0)) as s:
-                s.set_options(S.SADI_G_NEG_SIN, S.SADI_PREC_FP32)
-                s.set_initial(phi1, None)
+            with S.Sadi(N, ALPHAS[len(ALPHAS) // 2], KAPPA, TAU, (-1.0, 1.0)) as s:
+                s.set_options(GKIND, S.SADI_PREC_FP32)
+                s.set_initial(phi1, _phi2(phi1))
                 s.step(4)
                 ug32, _ = s.get()
                 rel_oracle32 = float(np.linalg.norm(ug32 - uK) / np.linalg.norm(uK))
@@ -406,14 +443,15 @@ def main():
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": _config(N, {"form": "FP32 FFT/sweeps, FP64 setup", "parallelism": f"replicas x{ws}",
                                   "l2": "flushed between timed steps (256 MiB write outside the step events)"}),
-            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64m / K64, "steps": K64},
-            "speedup_vs_fp64": value / value64,
-            "rel_l2_fp32_vs_fp64": max(rels), "rel_l2_steps": nsteps_cmp,
+            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64m / K64, "steps": K64}
+            if has64 else None,
+            "speedup_vs_fp64": value / value64 if has64 else None,
+            "rel_l2_fp32_vs_fp64": max(rels) if rels else None, "rel_l2_steps": nsteps_cmp,
             "rel_l2_fp32_vs_fp64_full": None if rel_full is None else
             {"steps": a.acc_steps, "per_alpha": dict(zip([str(x) for x in ALPHAS], rel_full)),
              "max": max(rel_full)},
             "rel_l2_vs_oracle_4steps": None if rel_oracle is None else
-            {"fp64": rel_oracle, "fp32": rel_oracle32, "alpha": 1.5},
+            {"fp64": rel_oracle, "fp32": rel_oracle32, "alpha": ALPHAS[len(ALPHAS) // 2]},
             "roofline": roofline, "batched": "one launch per kernel covers the three instances (sadi_batch_step)",
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,

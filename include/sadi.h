@@ -74,6 +74,16 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau,
  * (SADI_ESTATE otherwise). */
 sadi_status sadi_set_options(sadi_ctx *ctx, int g, int prec);
 
+/* Optional source term (an extension beyond the paper's problem statement,
+ * used for manufactured-solution checks): the equation becomes
+ * u_tt = -kappa (-Delta)^{alpha/2} u + g(u) + f with
+ *     f(x, y, t_n) = cos(omega t_n + phase) * F(x, y),  t_n = n tau,
+ * and f^n enters B^n exactly as g(u^n) does (tau^2 f^n for n >= 1,
+ * tau^2/2 f^0 at n = 0).  F: host N*N doubles (copied; layout above), or NULL
+ * to remove the source.  Call after sadi_set_options; changing the precision
+ * afterwards returns SADI_ESTATE. */
+sadi_status sadi_set_source(sadi_ctx *ctx, const double *F, double omega, double phase);
+
 /* Issue all further device work on cuda_stream (a cudaStream_t, e.g. a torch
  * stream's handle); NULL selects the context's own stream.  The caller keeps
  * ownership of the stream and must keep it alive while the context uses it. */

@@ -69,6 +69,9 @@ struct sadi_ctx {
   double phase_ms[4] = {0, 0, 0, 0};
   long long phase_steps = 0;
   cudaEvent_t order_ev = nullptr;   // cross-stream ordering in sadi_batch_step
+  // optional source term f^n = cos(omega t_n + phase) F(x)
+  void* F = nullptr;                // T, N x N
+  double f_omega = 0.0, f_phase = 0.0;
 };
 
 static thread_local std::string g_create_err;
@@ -105,7 +108,7 @@ T* dalloc(size_t n, cudaError_t* e) {
 void free_all(sadi_ctx* c) {
   void* ptrs[] = {c->rtw1, c->rlreg, c->rlamc, c->rlams, c->stw64, c->stw32, c->a1,     c->a2d,    c->cgen,   c->lnat,   c->tw64,   c->tw32, c->lpb64,
                   c->lpb32,  c->lamc64, c->lams64, c->lamc32, c->lams32, c->G64,  c->G32,
-                  c->ubuf[0], c->ubuf[1], c->ulo, c->phi2, c->S,      c->W,      c->stage};
+                  c->ubuf[0], c->ubuf[1], c->ulo, c->F, c->phi2, c->S,      c->W,      c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   for (auto& a : c->ev_pool)
@@ -290,9 +293,34 @@ sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
     return fail(c, SADI_EUNSUPPORTED, "the FP64 step path supports N <= 4096");
   c->gkind = g;
   if (prec != c->prec) {
+    if (c->F) return fail(c, SADI_ESTATE, "set the precision before sadi_set_source");
     c->prec = prec;
     return alloc_state(c);
   }
+  return SADI_OK;
+}
+
+sadi_status sadi_set_source(sadi_ctx* c, const double* F, double omega, double phase) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!std::isfinite(omega) || !std::isfinite(phase)) return fail(c, SADI_EINVAL, "omega and phase must be finite");
+  if (c->F) {
+    CK(cudaStreamSynchronize(c->stream), "sadi_set_source");
+    cudaFree(c->F);
+    c->F = nullptr;
+  }
+  if (!F) return SADI_OK;
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  CK(cudaMalloc(&c->F, nn * esize(c->prec)), "cudaMalloc(source)");
+  cudaStream_t st = c->stream;
+  CK(cudaMemcpyAsync(c->stage, F, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy source");
+  if (c->prec == SADI_PREC_FP64)
+    CK(cudaMemcpyAsync(c->F, c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "source");
+  else
+    CK(launch_convert_d2f(c->stage, static_cast<float*>(c->F), nn, st), "source convert");
+  CK(cudaStreamSynchronize(st), "sadi_set_source");
+  c->f_omega = omega;
+  c->f_phase = phase;
   return SADI_OK;
 }
 
@@ -373,6 +401,8 @@ RegInst reg_inst(const sadi_ctx* c) {
   r.tau2 = (float)(c->tau * c->tau);
   r.gkind = c->gkind;
   r.first = c->n == 0 ? 1 : 0;
+  r.F = static_cast<const float*>(c->F);
+  r.fsc = c->F ? (float)std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.f;
   return r;
 }
 
@@ -381,7 +411,8 @@ bool uses_reg_path(const sadi_ctx* c) { return c->prec == SADI_PREC_FP32 && c->r
 // One step of a context on the shared-memory engine (FP64, or FP32 N' > 1024),
 // on stream st.
 sadi_status step_smem(sadi_ctx* c, cudaEvent_t* ev, cudaStream_t st) {
-  RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0};
+  RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0, c->F,
+               c->F ? std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.0};
   cudaError_t e;
   if (c->prec == SADI_PREC_FP64) {
     void* ucur = c->ubuf[c->cur];

@@ -21,6 +21,8 @@ struct RhsParams {
   double tau, tau2;
   int g;
   int first;
+  const void* F;   // optional source field (T, N x N) or nullptr
+  double fsc;      // its time factor cos(omega t_n + phase) for this step
 };
 
 // ---- setup (FP64), setup_kernels.cu ----------------------------------------
@@ -92,8 +94,10 @@ struct RegInst {
   const float* phi2;
   float2* S;            // N x N' spectrum scratch
   float* W;             // N x N sweep scratch
+  const float* F;       // optional source field (N x N) or nullptr
   int N, r;
   float tau, tau2;
+  float fsc;            // time factor of the source for this step
   int gkind, first;
 };
 constexpr int kMaxBatch = 32;

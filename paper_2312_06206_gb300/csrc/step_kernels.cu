@@ -301,13 +301,17 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
         if (k < N) {
           const T conv = real_view<T>(e, k);
           const T uu = u[(size_t)row * N + k];
-          const T gg = T(rp.tau2) * g_of<T>(rp.g, uu);
+          T gsrc = g_of<T>(rp.g, uu);
+          if (rp.F) gsrc += T(rp.fsc) * static_cast<const T*>(rp.F)[(size_t)row * N + k];
+          const T gg = T(rp.tau2) * gsrc;
           ra[it] = rp.first ? T(rp.tau) * phi2[(size_t)row * N + k] + half * (conv + gg) : conv + gg;
         }
         if (k2 < N) {
           const T conv = real_view<T>(e, k2);
           const T uu = u[(size_t)row * N + k2];
-          const T gg = T(rp.tau2) * g_of<T>(rp.g, uu);
+          T gsrc = g_of<T>(rp.g, uu);
+          if (rp.F) gsrc += T(rp.fsc) * static_cast<const T*>(rp.F)[(size_t)row * N + k2];
+          const T gg = T(rp.tau2) * gsrc;
           rb[it] = rp.first ? T(rp.tau) * phi2[(size_t)row * N + k2] + half * (conv + gg) : conv + gg;
         }
       }

@@ -51,9 +51,12 @@ template <int LOGL, int BLOCK>
 struct ColCfg {
   using F = rf::RegFFT<float, LOGL>;
   static constexpr int CT = BLOCK / F::TT;                    // vectors (columns) per block
-  static constexpr int SMV = vec_smem<LOGL>(CT >= 32 ? 1 : (32 / CT) & 15);
+  // 8-byte accesses are served per half-warp (16 threads = CT columns x 16/CT
+  // consecutive t): a column stride of 16/CT (mod 16) float2 makes the 16
+  // bank pairs of a half-warp distinct
+  static constexpr int SMV = vec_smem<LOGL>(CT >= 16 ? 1 : 16 / CT);
   static constexpr int STG = F::L;                            // staged state column (floats)
-  static constexpr size_t bytes_conv = (size_t)CT * SMV * sizeof(float2);
+  static constexpr size_t bytes_conv = (size_t)CT * SMV * sizeof(float2) + (size_t)BLOCK * F::E * sizeof(float);
   static constexpr size_t bytes_solve = (size_t)CT * (SMV * sizeof(float2) + 3 * STG * sizeof(float));
 };
 
@@ -196,31 +199,32 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__
   const int k1 = (item == 0) ? 0 : (item == 1 ? Np : item - 1);
   const int slot = (item <= 1 || !valid) ? 0 : item - 1;
   float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    const int j = t + F::TT * q;
-    const bool in = valid && j < N;
-    cp_async8(&sm[pad32(j)], I.S + (size_t)(in ? j : 0) * Np + slot, in);
-  });
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncthreads();
+  float* ls = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::CT * C::SMV);
+  // the column and this thread's symbol values (frequency layout) are loaded
+  // together (all loads in flight), the symbol values parked in shared memory
+  const float* lrow = I.lreg + ((size_t)(valid ? k1 : 0) * 2 + h) * Np;
   float2 x[F::E];
+  float lv[F::E];
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int j = t + F::TT * q;
-    float2 val = sm[pad32(j)];
+    x[q] = (valid && j < N) ? I.S[(size_t)j * Np + slot] : make_float2(0.f, 0.f);
+    lv[q] = __ldg(lrow + F::template freq_index<q>(t));
+  });
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    const int j = t + F::TT * q;
+    float2 val = x[q];
     if (item == 0) val.y = 0.f;
     else if (item == 1) val = make_float2(val.y, 0.f);
     if (h) val = cmul(val, __ldg(&I.tw[j]));
     x[q] = val;
+    ls[q * BLOCK + threadIdx.x] = lv[q];
   });
-  __syncthreads();
   F::fwd(x, sm, t, I.tw1);
-  const float* lrow = I.lreg + ((size_t)(valid ? k1 : 0) * 2 + h) * Np;
   static_for<0, F::E>([&](auto rc) {
     constexpr int r = decltype(rc)::value;
-    x[r] = cscale(x[r], __ldg(&lrow[F::template freq_index<r>(t)]));
+    x[r] = cscale(x[r], ls[r * BLOCK + threadIdx.x]);
   });
   F::inv(x, sm, t, I.tw1);
   store_nat<LOGL>(x, sm, t);
@@ -311,11 +315,15 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
     const float2 cv = sm[pad32(n)];
     float b0 = 0.f, b1 = 0.f;
     if (valid && 2 * n < N) {
-      const float gg = tau2 * g_of_r<float>(I.gkind, us[2 * n]);
+      float gs = g_of_r<float>(I.gkind, us[2 * n]);
+      if (I.F) gs += I.fsc * I.F[(size_t)row * N + 2 * n];
+      const float gg = tau2 * gs;
       b0 = I.first ? tau * ps[2 * n] + 0.5f * (cv.x + gg) : cv.x + gg;
     }
     if (valid && 2 * n + 1 < N) {
-      const float gg = tau2 * g_of_r<float>(I.gkind, us[2 * n + 1]);
+      float gs = g_of_r<float>(I.gkind, us[2 * n + 1]);
+      if (I.F) gs += I.fsc * I.F[(size_t)row * N + 2 * n + 1];
+      const float gg = tau2 * gs;
       b1 = I.first ? tau * ps[2 * n + 1] + 0.5f * (cv.y + gg) : cv.y + gg;
     }
     sm[pad32(n)] = make_float2(b0, b1);
@@ -368,16 +376,8 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
   float* s_hi = st;
   float* s_lo = st + C::CT * C::STG;
   float* s_d = st + 2 * C::CT * C::STG;
-  float* wc = reinterpret_cast<float*>(smem_raw);       // W column, in the transform buffers
-  // stage the W column (needed now) and the state column (needed at the end)
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    const int k = t + F::TT * q;
-    const bool in = valid && k < N;
-    const size_t gi = (size_t)(in ? k : 0) * N + ii;
-    cp_async4(&wc[k * C::CT + c], I.W + gi, in);
-  });
-  cp_async_commit();
+  // the state column (needed at the end) is staged asynchronously; the W
+  // column (needed now) is loaded straight into registers, all loads in flight
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int k = t + F::TT * q;
@@ -388,13 +388,17 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
     cp_async4(&s_d[k * C::CT + c], I.u_d + gi, in && !I.first);
   });
   cp_async_commit();
-  asm volatile("cp.async.wait_group 1;\n" ::: "memory");   // the W column has landed
-  __syncthreads();
   float2 x[F::E];
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
-    const int k = t + F::TT * q;
-    x[q] = cmul(make_float2(wc[k * C::CT + c], wc[(Np - 1 - k) * C::CT + c]), __ldg(&I.tw[k]));
+    const int k = t + F::TT * q, k2 = Np - 1 - k;
+    const float a = (valid && k < N) ? I.W[(size_t)k * N + ii] : 0.f;
+    const float b = (valid && k2 < N) ? I.W[(size_t)k2 * N + ii] : 0.f;
+    x[q] = make_float2(a, b);
+  });
+  static_for<0, F::E>([&](auto qc) {
+    constexpr int q = decltype(qc)::value;
+    x[q] = cmul(x[q], __ldg(&I.tw[t + F::TT * q]));
   });
   __syncthreads();
   gs_reg<LOGL>(x, sm, t, I.tw1, I.tw, I.lam_s, I.lam_c);

@@ -26,6 +26,7 @@ _SIGS = {
     "sadi_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
                               C.POINTER(C.c_void_p)]),
     "sadi_set_options": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "sadi_set_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "sadi_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sadi_set_initial": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
     "sadi_step": (C.c_int, [C.c_void_p, C.c_int]),
@@ -107,6 +108,11 @@ class Sadi:
     # -- C ABI calls, same names -------------------------------------------
     def sadi_set_options(self, g: int = SADI_G_ZERO, prec: int = SADI_PREC_FP64):
         _check(lib().sadi_set_options(self.ctx, int(g), int(prec)), self.ctx)
+
+    def sadi_set_source(self, F=None, omega: float = 0.0, phase: float = 0.0):
+        f = None if F is None else _f64(F, self.N)
+        _check(lib().sadi_set_source(self.ctx, None if f is None else f.ctypes.data, float(omega),
+                                     float(phase)), self.ctx)
 
     def sadi_set_stream(self, stream_handle: int | None):
         _check(lib().sadi_set_stream(self.ctx, C.c_void_p(stream_handle or 0)), self.ctx)

@@ -197,3 +197,61 @@ def test_paper_table2_through_the_c_abi(S, alpha, ref):
                            dom=(w.a, w.b)))
     e = O.error2(1.0, us[0], us[1])
     assert abs(e - ref) <= 0.5 * 10 ** (np.floor(np.log10(ref)) - 4), (e, ref)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-5)])
+def test_source_term_parity(S, prec, tol):
+    # f^n = cos(omega t_n + phase) F enters B^n like g(u^n) (oracle `forcing`)
+    N, alpha, kappa, tau, g = 31, 1.4, 0.8, 0.04, 2
+    F = WL.random_field(N, 77)
+    om, ph = 2.3, 0.4
+    phi1 = WL.gaussian_bumps(N, 3, 78)
+    phi2 = 0.2 * WL.random_field(N, 79)
+    P = O.Problem(N, alpha, kappa, tau, -1.0, 1.0, g)
+    ref = O.run(P, phi1, phi2, 7, tier="direct", forcing=lambda n: np.cos(om * n * tau + ph) * F)
+    with S.Sadi(N, alpha, kappa, tau) as s:
+        s.set_options(g, prec)
+        s.sadi_set_source(F, om, ph)
+        s.set_initial(phi1, phi2)
+        s.step(7)
+        u, _ = s.get()
+    assert O.rel_l2(u, ref) <= tol
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_manufactured_solution_second_order_on_gpu(S, prec):
+    # U(t) = cos(t) phi solves u_tt = -kappa L_h u + f with g = 0 and
+    # f = cos(t) (kappa L_h phi - phi); the S-ADI step must converge to it at
+    # O(tau^2) (Sec. 5 convergence theorem).
+    N, alpha, kappa = 63, 1.5, 1.0
+    phi = WL.gaussian(N, 8.0)
+    errs = []
+    for M in (8, 16, 32):
+        tau = 1.0 / M
+        P = O.Problem(N, alpha, kappa, tau)
+        F = kappa * O.lh_direct(P, phi) - phi
+        with S.Sadi(N, alpha, kappa, tau) as s:
+            s.set_options(0, prec)
+            s.sadi_set_source(F, 1.0, 0.0)
+            s.set_initial(phi, None)
+            s.step(M)
+            u, _ = s.get()
+        errs.append(np.abs(u - np.cos(1.0) * phi).max())
+    orders = [np.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(1.9 < o < 2.15 for o in orders), (orders, errs)
+
+
+@pytest.mark.parametrize("N,alpha,g,steps", [(2047, 1.4, 1, 5), (4095, 1.7, 1, 3)])
+def test_large_n_fp32_against_fp64(S, N, alpha, g, steps):
+    # N' = 2048 and 4096 run on the shared-memory FFT engine in both precisions;
+    # the FP64 path is itself checked against the oracle at N = 2047 (2 steps).
+    tau, kappa = 5e-4, 0.5
+    phi1 = WL.gaussian_bumps(N, 8, 2000 + N)
+    u64 = _run_gpu(S, N, alpha, kappa, tau, g, phi1, None, steps, S.SADI_PREC_FP64)
+    u32 = _run_gpu(S, N, alpha, kappa, tau, g, phi1, None, steps, S.SADI_PREC_FP32)
+    assert O.rel_l2(u32, u64) <= 1e-5, O.rel_l2(u32, u64)
+    if N == 2047:
+        P = O.Problem(N, alpha, kappa, tau, -1.0, 1.0, g)
+        ref = O.run(P, phi1, np.zeros_like(phi1), 2, tier="fft")
+        u2 = _run_gpu(S, N, alpha, kappa, tau, g, phi1, None, 2, S.SADI_PREC_FP64)
+        assert O.rel_l2(u2, ref) <= 1e-10, O.rel_l2(u2, ref)
