@@ -170,6 +170,50 @@ const char *sadi_last_error(const sadi_ctx *ctx);
  * a no-op. */
 void sadi_destroy(sadi_ctx *ctx);
 
+/* One time step on caller-owned device state that allocates and frees no
+ * device memory.  The paper has no counterpart: this is a service entry point
+ * of the library.
+ *
+ * Who needs it: a caller that cannot allocate device memory while it steps,
+ * for example one whose free HBM is already reserved by another allocator (a
+ * framework's caching pool), or a latency-critical loop in which a cudaMalloc
+ * or cudaFree would synchronise the device and stall its other streams.  It
+ * also lets the caller keep the state in its own buffers instead of the
+ * context's.
+ *
+ * Computes u_next = u^{n+1} = 2 u^n - u^{n-1} + uhat^n by the n >= 1 formula
+ * of Sec. 3 (B^n = -tau^2 kappa L_h u^n + tau^2 g(u^n), plus tau^2 f^n with a
+ * source) from u_prev = u^{n-1} and u_cur = u^n, with the context's setup
+ * (N, alpha, kappa, tau, g, source, tiles) and its FP64 step kernels: the
+ * same arithmetic as sadi_step.  n >= 1 is the time level of u_cur; it only
+ * sets the source time t_n = n tau.  The context's own state (sadi_set_initial,
+ * sadi_step, sadi_get) is neither read nor changed; sadi_set_initial need not
+ * have been called.
+ *
+ * u_prev, u_cur, u_next: device memory on the context's device, N*N doubles
+ * each (layout above), owned by the caller.  u_next may equal u_prev (in
+ * place) but must not overlap u_cur; other overlaps are rejected
+ * (SADI_EINVAL).  The step is queued on the context's stream (asynchronous).
+ * The context's device must be current.  FP64 contexts only
+ * (SADI_EUNSUPPORTED otherwise).
+ *
+ * Scratch: a fixed 32 MiB array compiled into the library, which every GPU
+ * that loads the library's device code holds until the process exits.  A step
+ * needs 16 N N' + 8 N^2 bytes (+ alignment), N' the FFT length, so N <= 1024
+ * fits (25 MB at N = 1023); a larger N returns SADI_EINVAL naming both sizes.
+ * The array keeps what the previous call left in it; nothing in it has to
+ * start at zero, as each call writes every scratch element before reading it.
+ * All calls share the one array: calls that overlap in time (on several
+ * streams or host threads, whatever the contexts) race on it and produce
+ * wrong results, so order them (one stream, or events).
+ *
+ * The first call on a device does a per-device set-up (it looks up the
+ * array's device address, which can load the library's device code on that
+ * device); make that first call before any stream capture begins. */
+sadi_status sadi_step_noalloc(sadi_ctx *ctx, const double *u_prev,
+                              const double *u_cur, double *u_next,
+                              long long n);
+
 #ifdef __cplusplus
 }
 #endif

@@ -672,3 +672,68 @@ void sadi_destroy(sadi_ctx* c) {
 }
 
 }  // extern "C"
+
+// ---- sadi_step_noalloc: caller-owned state, fixed library scratch -----------
+
+namespace {
+
+sadi_status check_device_buffer(sadi_ctx* c, const void* p, const char* name) {
+  cudaPointerAttributes a{};
+  const cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SADI_EINVAL, std::string(name) + " is not a CUDA pointer");
+  }
+  if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != c->device)
+    return fail(c, SADI_EINVAL, std::string(name) + " must be device memory on the context's device");
+  return SADI_OK;
+}
+
+bool ranges_overlap(const void* p, const void* q, size_t bytes) {
+  const char* a = static_cast<const char*>(p);
+  const char* b = static_cast<const char*>(q);
+  return a < b + bytes && b < a + bytes;
+}
+
+}  // namespace
+
+extern "C" sadi_status sadi_step_noalloc(sadi_ctx* c, const double* u_prev, const double* u_cur, double* u_next,
+                                         long long n) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (c->prec != SADI_PREC_FP64)
+    return fail(c, SADI_EUNSUPPORTED, "sadi_step_noalloc: FP64 contexts only (select SADI_PREC_FP64)");
+  if (!u_prev || !u_cur || !u_next) return fail(c, SADI_EINVAL, "sadi_step_noalloc: a state pointer is NULL");
+  if (n < 1) return fail(c, SADI_EINVAL, "sadi_step_noalloc: n (time level of u_cur) must be >= 1");
+  const Geom& g = c->g;
+  const size_t nn = (size_t)g.N * g.N;
+  const size_t s_bytes = (size_t)g.N * g.Np * 2 * sizeof(double);
+  const size_t w_off = (s_bytes + 255) & ~size_t(255);
+  const size_t need = w_off + nn * sizeof(double);
+  if (need > kNoallocScratchBytes)
+    return fail(c, SADI_EINVAL,
+                "sadi_step_noalloc: this N needs " + std::to_string(need) + " bytes of scratch, above the fixed " +
+                    std::to_string(kNoallocScratchBytes) + " (N <= 1024 fits)");
+  const size_t ub = nn * sizeof(double);
+  if (ranges_overlap(u_next, u_cur, ub)) return fail(c, SADI_EINVAL, "sadi_step_noalloc: u_next overlaps u_cur");
+  if (u_next != u_prev && ranges_overlap(u_next, u_prev, ub))
+    return fail(c, SADI_EINVAL, "sadi_step_noalloc: u_next overlaps u_prev without being equal to it");
+  int dev = -1;
+  CK(cudaGetDevice(&dev), "cudaGetDevice");
+  if (dev != c->device) return fail(c, SADI_EINVAL, "sadi_step_noalloc: the context's device must be current");
+  sadi_status st = check_device_buffer(c, u_prev, "u_prev");
+  if (st == SADI_OK) st = check_device_buffer(c, u_cur, "u_cur");
+  if (st == SADI_OK) st = check_device_buffer(c, u_next, "u_next");
+  if (st != SADI_OK) return st;
+  void* scratch = nullptr;
+  CK(noalloc_scratch_address(dev, &scratch), "scratch address");
+  RhsParams rp{c->tau, c->tau * c->tau, c->gkind, 0, c->F,
+               c->F ? std::cos(c->f_omega * (double)n * c->tau + c->f_phase) : 0.0};
+  StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
+  double* W = reinterpret_cast<double*>(static_cast<char*>(scratch) + w_off);
+  // u_prev is only read by the plain (uncompensated) leapfrog form
+  CK(launch_step<double>(g, tb, c->tiles64, rp, u_cur, const_cast<double*>(u_prev), u_next, nullptr,
+                         static_cast<const double*>(c->phi2), scratch, W, c->stream, nullptr),
+     "step launch");
+  return SADI_OK;
+}

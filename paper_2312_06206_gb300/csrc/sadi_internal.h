@@ -126,4 +126,10 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
                         T* u_prev, T* u_next, T* u_lo, const T* phi2, void* S, T* W, cudaStream_t st,
                         cudaEvent_t* ev = nullptr);
 
+// ---- fixed scratch of sadi_step_noalloc, noalloc_scratch.cu ------------------
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
+// Device address of the fixed scratch array on `device`, which must be the
+// current device; looked up on the first call per device, cached afterwards.
+cudaError_t noalloc_scratch_address(int device, void** out);
+
 }  // namespace sadi

@@ -41,6 +41,7 @@ _SIGS = {
     "sadi_get_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "sadi_last_error": (C.c_char_p, [C.c_void_p]),
     "sadi_destroy": (None, [C.c_void_p]),
+    "sadi_step_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong]),
 }
 
 
@@ -167,6 +168,11 @@ class Sadi:
         n = C.c_longlong()
         _check(lib().sadi_get_phase_times(self.ctx, ms, C.byref(n)), self.ctx)
         return list(ms), int(n.value)
+
+    def sadi_step_noalloc(self, u_prev_ptr: int, u_cur_ptr: int, u_next_ptr: int, n: int):
+        """One step on caller-owned device buffers (N*N doubles each); no allocation."""
+        _check(lib().sadi_step_noalloc(self.ctx, C.c_void_p(u_prev_ptr), C.c_void_p(u_cur_ptr),
+                                       C.c_void_p(u_next_ptr), int(n)), self.ctx)
 
     def sadi_last_error(self) -> str:
         return lib().sadi_last_error(self.ctx).decode()

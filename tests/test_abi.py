@@ -63,3 +63,7 @@ def test_null_out_pointer_rejected(lib):
     assert lib.sadi_create(15, 1.5, 1.0, 0.01, None, ctypes.byref(ctypes.c_void_p())) == 1
     assert b"NULL" in lib.sadi_last_error(None)
     lib.sadi_destroy(None)  # no-op
+
+
+def test_noalloc_step_rejects_null_context_without_a_gpu(lib):
+    assert lib.sadi_step_noalloc(None, None, None, None, 1) == 1
