@@ -170,6 +170,21 @@ const char *sadi_last_error(const sadi_ctx *ctx);
  * a no-op. */
 void sadi_destroy(sadi_ctx *ctx);
 
+/* Split-BF16 tensor-core product (no paper counterpart: the contraction of the
+ * dense-inverse sweeps, exposed so that it can be tested on its own).
+ * A: M x K, B: N x K, C: M x N, all FP32, row-major, contiguous, device
+ * memory on the current device, owned by the caller.  Each operand is split
+ * into BF16 pairs X = X_hi + X_lo (X_hi = X rounded to nearest BF16, X_lo = the
+ * remainder rounded to BF16) and
+ *     C = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T
+ * is accumulated in FP32 by tcgen05 MMAs (the A_lo B_lo^T term is dropped).
+ * 1 <= M, N, K <= 65536.  Allocates and frees temporary device buffers (zero-
+ * padded operand copies); runs on `stream` (a cudaStream_t, NULL = the legacy
+ * default stream) and returns after it has finished.  SADI_ETIMEOUT if a
+ * bounded device wait ran out (C is then unspecified). */
+sadi_status sadi_gemm_split_bf16(const float *A, const float *B, float *C,
+                                 int M, int N, int K, void *stream);
+
 /* One time step on caller-owned device state that allocates and frees no
  * device memory.  The paper has no counterpart: this is a service entry point
  * of the library.

@@ -1,0 +1,416 @@
+// gemm_tc.cu -- split-BF16 GEMM on the 5th-generation tensor cores (tcgen05)
+// for the dense-inverse form of the two ADI sweeps.
+//
+// Computes ACC = A B^T (FP32 accumulate) where both FP32 operands are given as
+// BF16 pairs X = X_hi + X_lo (X_hi = BF16 round-to-nearest of X, X_lo = BF16
+// of the remainder):
+//     ACC = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T       (A_lo B_lo^T dropped)
+// All operands are K-major (row-major, K contiguous), zero-padded to whole
+// tiles.  Per-element representation error of a pair is <= 2^-16 relative, so
+// ACC carries about 2^-16 relative error on top of FP32 accumulation.
+//
+// One CTA computes one 128 x 256 output tile with 4 warps:
+//   * thread 0 streams 64-wide K blocks of A_hi, A_lo (128 rows) and B_hi,
+//     B_lo (256 rows) with TMA (cp.async.bulk.tensor, 128-byte swizzle) into
+//     a 2-stage ring guarded by mbarriers;
+//   * thread 32 issues tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator
+//     of 128 lanes x 256 columns in tensor memory) and returns each stage to
+//     the producer with tcgen05.commit;
+//   * all 4 warps read their 32 accumulator lanes back (tcgen05.ld 32x32b)
+//     and run the epilogue of the launch (plain store, or the two fused sweep
+//     epilogues of the dense S-ADI step).
+// A batch of independent problems of equal padded size runs as blockIdx.z.
+// Every mbarrier wait is bounded (about 1 s of %globaltimer); on expiry the
+// CTA sets *err, waits (bounded) for the copies it issued, frees its tensor
+// memory and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <cstring>
+
+#include "../../include/sadi.h"
+#include "sadi_internal.h"
+
+namespace sadi {
+namespace {
+
+constexpr int BM = kTcTileM, BN = kTcTileN, BK = kTcTileK;
+constexpr int STAGES = 2;
+constexpr int A_TILE = BM * BK * 2;                    // 16 KB
+constexpr int B_TILE = BN * BK * 2;                    // 32 KB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // 96 KB
+constexpr int TMEM_COLS = 256;
+constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 128;
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ uint64_t gtimer() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait until the phase with the given parity has completed; false after the limit.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > WAIT_LIMIT_NS) return false;
+  return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major tile written by TMA with the
+// 128-byte swizzle: rows of 128 B, 8-row core groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((saddr >> 4) & 0x3FFF);   // start address / 16
+  d |= (uint64_t)1 << 16;                    // leading-dimension offset (unused when swizzled, K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride-dimension offset: 8 rows x 128 B
+  d |= (uint64_t)1 << 46;                    // descriptor version of tcgen05
+  d |= (uint64_t)2 << 61;                    // 128-byte swizzle
+  return d;
+}
+
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), BF16
+// A and B (bits 7-9, 10-12 = 1), both K-major, N / 8 at bit 17, M / 16 at bit 24.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void split_bf16(float v, unsigned short* hi, unsigned short* lo) {
+  const __nv_bfloat16 h = __float2bfloat16_rn(v);
+  *hi = __bfloat16_as_ushort(h);
+  *lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
+}
+
+// Epilogue of one accumulator row segment: row `row`, columns col0 .. col0+31.
+__device__ __forceinline__ void epilogue(const TcEpi& e, int row, int col0, const uint32_t* r) {
+  if (row >= e.m_valid) return;
+  const int ncol = min(32, e.n_valid - col0);
+  if (ncol <= 0) return;
+  if (e.mode == kTcStore) {
+    float* dst = e.C + (size_t)row * e.ldc + col0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+      if (j < ncol) dst[j] = __uint_as_float(r[j]);
+  } else if (e.mode == kTcSweepX) {
+    // W = B + B E (in place over B), and the transposed BF16 split of W
+    float* w = e.C + (size_t)row * e.ldc + col0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= ncol) break;
+      const float v = w[j] + __uint_as_float(r[j]);
+      w[j] = v;
+      unsigned short hi, lo;
+      split_bf16(v, &hi, &lo);
+      const size_t t = (size_t)(col0 + j) * e.ldt + row;
+      e.t_hi[t] = hi;
+      e.t_lo[t] = lo;
+    }
+  } else {
+    // uhat = W + E W; compensated leapfrog d^{n+1} = d^n + uhat (d^1 = uhat),
+    // u^{n+1} = u^n + d^{n+1} with u = u_hi + u_lo (two-sum), in place
+    const float* w = e.C + (size_t)row * e.ldc + col0;
+    const size_t base = (size_t)row * e.ldu + col0;
+#pragma unroll
+    for (int j = 0; j < 32; ++j) {
+      if (j >= ncol) break;
+      const float uh = w[j] + __uint_as_float(r[j]);
+      const size_t idx = base + j;
+      const float d = e.first ? uh : e.u_d[idx] + uh;
+      const float hi = e.u_hi[idx], lo = e.u_lo[idx];
+      const float s = hi + d;
+      const float bb = s - hi;
+      const float err = (hi - (s - bb)) + (d - bb);
+      const float l2 = lo + err;
+      const float h2 = s + l2;
+      e.u_hi[idx] = h2;
+      e.u_lo[idx] = l2 - (h2 - s);
+      e.u_d[idx] = d;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int* err) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  const TcInst& in = bt.in[blockIdx.z];
+  uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES), tfull = su32(bars + 2 * STAGES);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nk = bt.K / BK;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(full0 + 8 * s, 1);
+      mbar_init(empty0 + 8 * s, 1);
+    }
+    mbar_init(tfull, 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---- TMA producer ----
+    int issued = 0;
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t use = (uint32_t)(kb / STAGES);
+      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1u)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = base + s * STAGE_BYTES;
+      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+      tma_load_2d(su32(st), &in.a_hi, kb * BK, m0, full0 + 8 * s);
+      tma_load_2d(su32(st + A_TILE), &in.a_lo, kb * BK, m0, full0 + 8 * s);
+      tma_load_2d(su32(st + 2 * A_TILE), &in.b_hi, kb * BK, n0, full0 + 8 * s);
+      tma_load_2d(su32(st + 2 * A_TILE + B_TILE), &in.b_lo, kb * BK, n0, full0 + 8 * s);
+      issued = kb + 1;
+    }
+    if (*abort_flag) {
+      // the copies already issued must land before the CTA may exit
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        (void)mbar_wait(full0 + 8 * (kb % STAGES), (uint32_t)(kb / STAGES) & 1u);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---- MMA issuer ----
+    constexpr uint32_t idesc = idesc_bf16(BM, BN);
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      if (!mbar_wait(full0 + 8 * s, (uint32_t)(kb / STAGES) & 1u) || *abort_flag) {
+        *abort_flag = 1;
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = su32(base + s * STAGE_BYTES);
+      const uint64_t a_hi = sw128_desc(st), a_lo = sw128_desc(st + A_TILE);
+      const uint64_t b_hi = sw128_desc(st + 2 * A_TILE), b_lo = sw128_desc(st + 2 * A_TILE + B_TILE);
+#pragma unroll
+      for (int p = 0; p < 3; ++p) {
+        const uint64_t a = (p < 2) ? a_hi : a_lo;
+        const uint64_t b = (p == 1) ? b_lo : b_hi;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          // K step of 16 BF16 = 32 bytes inside the 128-byte swizzled row
+          mma_bf16(tmem, a + (uint64_t)(2 * k), b + (uint64_t)(2 * k), idesc, (kb | p | k) != 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(empty0 + 8 * s);
+    }
+    mma_commit(tfull);
+  }
+  __syncwarp();
+  // ---- epilogue: tensor memory -> registers -> global ----
+  const bool done = mbar_wait(tfull, 0);
+  tc_fence_after();
+  if (done && !*abort_flag) {
+    const int row = m0 + warp * 32 + lane;
+#pragma unroll 1
+    for (int c = 0; c < BN / 32; ++c) {
+      uint32_t r[32];
+      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
+      epilogue(in.e, row, n0 + c * 32, r);
+    }
+  } else if (lane == 0) {
+    atomicExch(err, 1);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+}
+
+// FP32 (rows x cols, row-major, ld src_ld) -> BF16 hi/lo pair in a zero-padded
+// prow x pcol buffer.
+__global__ void k_split_pad(const float* __restrict__ src, int rows, int cols, int src_ld, unsigned short* hi,
+                            unsigned short* lo, int prow, int pcol) {
+  const size_t idx = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  if (idx >= (size_t)prow * pcol) return;
+  const int r = (int)(idx / pcol), c = (int)(idx % pcol);
+  const float v = (r < rows && c < cols) ? src[(size_t)r * src_ld + c] : 0.f;
+  split_bf16(v, hi + idx, lo + idx);
+}
+
+CUresult (*g_encode)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*, const cuuint64_t*,
+                     const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                     CUtensorMapL2promotion, CUtensorMapFloatOOBfill) = nullptr;
+
+cudaError_t get_encoder() {
+  if (g_encode) return cudaSuccess;
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+  g_encode = reinterpret_cast<decltype(g_encode)>(fn);
+  return cudaSuccess;
+}
+
+}  // namespace
+
+cudaError_t tc_encode(CUtensorMap* map, const void* base, int rows, int kdim, int box_rows) {
+  cudaError_t e = get_encoder();
+  if (e != cudaSuccess) return e;
+  // TMA needs a 16-byte aligned base and a row pitch that is a multiple of 16 B
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (kdim % 8) || kdim % BK || rows % box_rows)
+    return cudaErrorInvalidValue;
+  cuuint64_t dims[2] = {(cuuint64_t)kdim, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)kdim * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  const CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+                              estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, const void* b_hi, const void* b_lo,
+                            int M, int N, int K) {
+  cudaError_t e;
+  if ((e = tc_encode(&in->a_hi, a_hi, M, K, BM))) return e;
+  if ((e = tc_encode(&in->a_lo, a_lo, M, K, BM))) return e;
+  if ((e = tc_encode(&in->b_hi, b_hi, N, K, BN))) return e;
+  if ((e = tc_encode(&in->b_lo, b_lo, N, K, BN))) return e;
+  return cudaSuccess;
+}
+
+cudaError_t launch_tc_gemm(const TcBatch& b, int M, int N, int* err, cudaStream_t st) {
+  if (b.count < 1 || b.count > kTcMaxBatch || M % BM || N % BN || b.K % BK || b.K <= 0) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  const dim3 grid(N / BN, M / BM, b.count);
+  k_tc_gemm<<<grid, 128, SMEM_BYTES, st>>>(b, err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,
+                             cudaStream_t st) {
+  const size_t n = (size_t)prow * pcol;
+  if (n == 0) return cudaSuccess;
+  k_split_pad<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(src, rows, cols, src_ld, static_cast<unsigned short*>(hi),
+                                                            static_cast<unsigned short*>(lo), prow, pcol);
+  return cudaGetLastError();
+}
+
+}  // namespace sadi
+
+// ---- diagnostic entry point ---------------------------------------------------
+
+using namespace sadi;
+
+namespace {
+int round_up(int v, int m) { return (v + m - 1) / m * m; }
+}  // namespace
+
+extern "C" sadi_status sadi_gemm_split_bf16(const float* A, const float* B, float* C, int M, int N, int K,
+                                            void* stream) {
+  if (!A || !B || !C || M < 1 || N < 1 || K < 1 || M > 65536 || N > 65536 || K > 65536) return SADI_EINVAL;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  unsigned short* buf = nullptr;
+  int* err = nullptr;
+  const size_t na = (size_t)Mp * Kp, nb = (size_t)Np * Kp;
+  if (cudaMalloc(&buf, (2 * na + 2 * nb) * sizeof(unsigned short)) != cudaSuccess) return SADI_ENOMEM;
+  if (cudaMalloc(&err, sizeof(int)) != cudaSuccess) {
+    cudaFree(buf);
+    return SADI_ENOMEM;
+  }
+  unsigned short *ah = buf, *al = buf + na, *bh = buf + 2 * na, *bl = buf + 2 * na + nb;
+  static TcBatch bt;   // about 1.2 KB of tensor maps; built on the host only
+  std::memset(&bt, 0, sizeof(bt));
+  bt.count = 1;
+  bt.K = Kp;
+  TcEpi& e = bt.in[0].e;
+  e.mode = kTcStore;
+  e.m_valid = M;
+  e.n_valid = N;
+  e.C = C;
+  e.ldc = N;
+  sadi_status rs = SADI_OK;
+  int herr = 0;
+  if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||
+      launch_split_pad(A, M, K, K, ah, al, Mp, Kp, st) != cudaSuccess ||
+      launch_split_pad(B, N, K, K, bh, bl, Np, Kp, st) != cudaSuccess ||
+      tc_set_operands(&bt.in[0], ah, al, bh, bl, Mp, Np, Kp) != cudaSuccess ||
+      launch_tc_gemm(bt, Mp, Np, err, st) != cudaSuccess ||
+      cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+      cudaStreamSynchronize(st) != cudaSuccess) {
+    rs = SADI_ECUDA;
+  } else if (herr) {
+    rs = SADI_ETIMEOUT;
+  }
+  cudaFree(buf);
+  cudaFree(err);
+  return rs;
+}

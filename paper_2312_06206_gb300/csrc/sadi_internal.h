@@ -2,6 +2,7 @@
 // S-ADI library.  Not part of the public C ABI (include/sadi.h).
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -125,6 +126,47 @@ template <typename T>
 cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
                         T* u_prev, T* u_next, T* u_lo, const T* phi2, void* S, T* W, cudaStream_t st,
                         cudaEvent_t* ev = nullptr);
+
+// ---- split-BF16 tensor-core GEMM, gemm_tc.cu ----------------------------------
+// ACC = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T over K-major BF16 operands
+// (row-major, K contiguous, zero-padded to whole tiles), then an epilogue.
+constexpr int kTcTileM = 128, kTcTileN = 256, kTcTileK = 64;
+constexpr int kTcMaxBatch = 16;
+enum TcMode { kTcStore = 0, kTcSweepX = 1, kTcSweepY = 2 };
+struct TcEpi {
+  int mode;
+  int m_valid, n_valid;       // rows / columns of ACC that are written
+  float* C;                   // kTcStore: out; kTcSweepX: B in, W out; kTcSweepY: W in (row-major, ld ldc)
+  int ldc;
+  unsigned short* t_hi;       // kTcSweepX: BF16 split of W^T (ld ldt), the next GEMM's B operand
+  unsigned short* t_lo;
+  int ldt;
+  float* u_hi;                // kTcSweepY: double-float state and increment (ld ldu), updated in place
+  float* u_lo;
+  float* u_d;
+  int ldu;
+  int first;
+};
+struct TcInst {
+  CUtensorMap a_hi, a_lo;     // A operand (M rows), box 128 x 64
+  CUtensorMap b_hi, b_lo;     // B operand (N rows), box 256 x 64
+  TcEpi e;
+};
+// passed by value as a __grid_constant__ kernel parameter (about 10 KB)
+struct TcBatch {
+  int count;
+  int K;
+  TcInst in[kTcMaxBatch];
+};
+// tensor map of a rows x kdim BF16 matrix (row-major) with box box_rows x 64
+cudaError_t tc_encode(CUtensorMap* map, const void* base, int rows, int kdim, int box_rows);
+cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, const void* b_hi, const void* b_lo,
+                            int M, int N, int K);
+// one launch for all b.count problems (each M x N, K = b.K); *err set on a timed-out wait
+cudaError_t launch_tc_gemm(const TcBatch& b, int M, int N, int* err, cudaStream_t st);
+// FP32 rows x cols (ld src_ld) -> zero-padded prow x pcol BF16 hi / lo
+cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,
+                             cudaStream_t st);
 
 // ---- fixed scratch of sadi_step_noalloc, noalloc_scratch.cu ------------------
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;

@@ -41,6 +41,8 @@ _SIGS = {
     "sadi_get_phase_times": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "sadi_last_error": (C.c_char_p, [C.c_void_p]),
     "sadi_destroy": (None, [C.c_void_p]),
+    "sadi_gemm_split_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                        C.c_void_p]),
     "sadi_step_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong]),
 }
 
@@ -84,6 +86,14 @@ def _f64(a, N):
     if a.shape != (N, N):
         raise ValueError(f"expected shape {(N, N)}, got {a.shape}")
     return a
+
+
+def sadi_gemm_split_bf16(A_ptr: int, B_ptr: int, C_ptr: int, M: int, N: int, K: int, stream: int = 0):
+    """C = A B^T in split BF16 on the tensor cores (device FP32 pointers); see sadi.h."""
+    st = lib().sadi_gemm_split_bf16(C.c_void_p(A_ptr), C.c_void_p(B_ptr), C.c_void_p(C_ptr), int(M), int(N),
+                                    int(K), C.c_void_p(stream or 0))
+    if st != SADI_OK:
+        raise SadiError(st, "sadi_gemm_split_bf16 failed")
 
 
 def sadi_batch_step(instances, nsteps: int = 1):
