@@ -50,10 +50,18 @@ typedef enum {
 /* Nonlinearity g(u) of Sec. 1 (Sec. 6 uses -sin u and -u^3). */
 typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2 } sadi_g;
 
-/* Arithmetic of the per-step path.  Setup (weights, generator, spectra) is
- * always FP64.  SADI_PREC_FP64: FFTs, sweeps and state in double.
- * SADI_PREC_FP32: FFTs and sweeps in float; the state u^n, u^{n-1} in float. */
-typedef enum { SADI_PREC_FP64 = 0, SADI_PREC_FP32 = 1 } sadi_prec;
+/* Arithmetic of the per-step path.  Setup (weights, generator, spectra, the
+ * dense inverse) is always FP64.
+ * SADI_PREC_FP64: FFTs, sweeps and state in double.
+ * SADI_PREC_FP32: FFTs and Gohberg-Semencul sweeps in float; the state kept
+ *   as a double-float pair with a compensated leapfrog (float storage).
+ * SADI_PREC_FP32_DENSE: as FP32, but both sweeps apply the precomputed dense
+ *   inverse H^-1 = I + E to all rows / columns at once: W = B + B E and
+ *   uhat = W + E W, each product a split-BF16 GEMM on the tensor cores
+ *   (E and the right-hand side split into BF16 hi + lo pairs, three products,
+ *   FP32 accumulation).  E comes from the FP64 generator of the N x N matrix.
+ *   N <= 4096 (SADI_EUNSUPPORTED otherwise). */
+typedef enum { SADI_PREC_FP64 = 0, SADI_PREC_FP32 = 1, SADI_PREC_FP32_DENSE = 2 } sadi_prec;
 
 /* Create a context for N interior points per direction, fractional order
  * alpha in (1, 2] (2 = the classical wave equation limit; the paper states
@@ -102,10 +110,11 @@ sadi_status sadi_set_initial(sadi_ctx *ctx, const double *phi1, const double *ph
 sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
 
 /* Advance each of count contexts by nsteps time steps (asynchronous), as
- * sadi_step would, but batched: FP32 contexts with FFT length N' <= 1024 are
- * grouped by N' and each group runs one launch per kernel for all its members
- * (independent problems of possibly different N, alpha, kappa, tau and g);
- * the other contexts step one after another.  All contexts must be
+ * sadi_step would, but batched: FP32 and FP32_DENSE contexts with FFT length
+ * N' <= 1024 are grouped by precision and N' (at most 32 per group) and each
+ * group runs one launch per kernel for all its members (independent problems
+ * of possibly different N, alpha, kappa, tau and g; the dense sweeps in GEMM
+ * launches of up to 16 problems); the other contexts step one after another.  All contexts must be
  * initialised and distinct (SADI_EINVAL / SADI_ESTATE otherwise).  The work
  * is issued on the first context's stream, ordered after the work already
  * queued on the other contexts' streams and before their later work (event
@@ -113,7 +122,9 @@ sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
 sadi_status sadi_batch_step(sadi_ctx **ctxs, int count, int nsteps);
 
 /* Copy u^n to the host (N*N doubles) after the stream's pending work; *n_out
- * (may be NULL) receives n.  Synchronous. */
+ * (may be NULL) receives n.  Synchronous.  Returns SADI_ETIMEOUT (and the
+ * context becomes unusable) if a bounded wait inside a tensor-core sweep of
+ * the dense-inverse form ran out since the context was created. */
 sadi_status sadi_get(sadi_ctx *ctx, double *u_out, long long *n_out);
 
 /* Copy u^n device-to-device into dst (N*N contiguous elements of dtype 0 =
@@ -128,6 +139,10 @@ sadi_status sadi_get_device(sadi_ctx *ctx, void *dst, int dtype);
  *              H' = I + s T(a_0 .. a_{N'-1}), N' = the FFT length (count N')
  *   which = 3: symbol Lambda(k1, k2) of the block-circulant embedding of
  *              size 2N' x 2N' (unscaled), 0 <= k1, k2 <= N'  (count (N'+1)^2)
+ *   which = 4: E = H^-1 - I of the N x N matrix H = I + s T(a_0 .. a_{N-1})
+ *              as the dense-inverse form stores it (E_hi + E_lo, the BF16
+ *              pair, summed in double), row-major (count N*N); only after
+ *              SADI_PREC_FP32_DENSE was selected (SADI_ESTATE otherwise)
  * count must equal the stated size.  N' is returned by sadi_get_info. */
 sadi_status sadi_get_setup(sadi_ctx *ctx, int which, double *out, size_t count);
 

@@ -31,6 +31,7 @@
 #include <cstring>
 
 #include "../../include/sadi.h"
+#include "bf16split.cuh"
 #include "sadi_internal.h"
 
 namespace sadi {
@@ -128,12 +129,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-__device__ __forceinline__ void split_bf16(float v, unsigned short* hi, unsigned short* lo) {
-  const __nv_bfloat16 h = __float2bfloat16_rn(v);
-  *hi = __bfloat16_as_ushort(h);
-  *lo = __bfloat16_as_ushort(__float2bfloat16_rn(v - __bfloat162float(h)));
-}
-
 // Epilogue of one accumulator row segment: row `row`, columns col0 .. col0+31.
 __device__ __forceinline__ void epilogue(const TcEpi& e, int row, int col0, const uint32_t* r) {
   if (row >= e.m_valid) return;
@@ -185,6 +180,7 @@ __device__ __forceinline__ void epilogue(const TcEpi& e, int row, int col0, cons
 __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const TcInst& in = bt.in[blockIdx.z];
+  if ((int)blockIdx.x >= in.tiles_n || (int)blockIdx.y >= in.tiles_m) return;   // beyond this problem
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
@@ -192,7 +188,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcBa
   const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES), tfull = su32(bars + 2 * STAGES);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int nk = bt.K / BK;
+  const int nk = in.K / BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -278,7 +274,7 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcBa
       epilogue(in.e, row, n0 + c * 32, r);
     }
   } else if (lane == 0) {
-    atomicExch(err, 1);
+    atomicExch(in.e.err ? in.e.err : err, 1);
   }
   tc_fence_before();
   __syncthreads();
@@ -338,18 +334,29 @@ cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, cons
   if ((e = tc_encode(&in->a_lo, a_lo, M, K, BM))) return e;
   if ((e = tc_encode(&in->b_hi, b_hi, N, K, BN))) return e;
   if ((e = tc_encode(&in->b_lo, b_lo, N, K, BN))) return e;
+  if (M % BM || N % BN || K % BK || K <= 0) return cudaErrorInvalidValue;
+  in->K = K;
+  in->tiles_m = M / BM;
+  in->tiles_n = N / BN;
   return cudaSuccess;
 }
 
-cudaError_t launch_tc_gemm(const TcBatch& b, int M, int N, int* err, cudaStream_t st) {
-  if (b.count < 1 || b.count > kTcMaxBatch || M % BM || N % BN || b.K % BK || b.K <= 0) return cudaErrorInvalidValue;
+cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
+  if (b.count < 1 || b.count > kTcMaxBatch) return cudaErrorInvalidValue;
+  int tm = 0, tn = 0;
+  for (int k = 0; k < b.count; ++k) {
+    const TcInst& in = b.in[k];
+    if (in.K <= 0 || in.K % BK || in.tiles_m < 1 || in.tiles_n < 1) return cudaErrorInvalidValue;
+    tm = in.tiles_m > tm ? in.tiles_m : tm;
+    tn = in.tiles_n > tn ? in.tiles_n : tn;
+  }
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
     if (e != cudaSuccess) return e;
     attr = true;
   }
-  const dim3 grid(N / BN, M / BM, b.count);
+  const dim3 grid(tn, tm, b.count);
   k_tc_gemm<<<grid, 128, SMEM_BYTES, st>>>(b, err);
   return cudaGetLastError();
 }
@@ -390,7 +397,6 @@ extern "C" sadi_status sadi_gemm_split_bf16(const float* A, const float* B, floa
   static TcBatch bt;   // about 1.2 KB of tensor maps; built on the host only
   std::memset(&bt, 0, sizeof(bt));
   bt.count = 1;
-  bt.K = Kp;
   TcEpi& e = bt.in[0].e;
   e.mode = kTcStore;
   e.m_valid = M;
@@ -403,7 +409,7 @@ extern "C" sadi_status sadi_gemm_split_bf16(const float* A, const float* B, floa
       launch_split_pad(A, M, K, K, ah, al, Mp, Kp, st) != cudaSuccess ||
       launch_split_pad(B, N, K, K, bh, bl, Np, Kp, st) != cudaSuccess ||
       tc_set_operands(&bt.in[0], ah, al, bh, bl, Mp, Np, Kp) != cudaSuccess ||
-      launch_tc_gemm(bt, Mp, Np, err, st) != cudaSuccess ||
+      launch_tc_gemm(bt, err, st) != cudaSuccess ||
       cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
       cudaStreamSynchronize(st) != cudaSuccess) {
     rs = SADI_ECUDA;

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <cstring>
 #include <array>
+#include <memory>
 #include <string>
 #include <vector>
 
@@ -72,6 +73,12 @@ struct sadi_ctx {
   // optional source term f^n = cos(omega t_n + phase) F(x)
   void* F = nullptr;                // T, N x N
   double f_omega = 0.0, f_phase = 0.0;
+  // dense-inverse form (SADI_PREC_FP32_DENSE): BF16 pairs, npad x npad,
+  // zero-padded: E = H^-1 - I, B^n rows, W^T rows; tensor maps of the two GEMMs
+  int npad = 0;
+  unsigned short *Eh = nullptr, *El = nullptr, *Bh = nullptr, *Bl = nullptr, *WTh = nullptr, *WTl = nullptr;
+  int* tcerr = nullptr;             // device flag: a bounded wait in a GEMM ran out
+  std::unique_ptr<TcInst> tc_x, tc_y;
 };
 
 static thread_local std::string g_create_err;
@@ -111,6 +118,9 @@ void free_all(sadi_ctx* c) {
                   c->ubuf[0], c->ubuf[1], c->ulo, c->F, c->phi2, c->S,      c->W,      c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr};
+  for (void* p : dense)
+    if (p) cudaFree(p);
   for (auto& a : c->ev_pool)
     for (auto e : a) cudaEventDestroy(e);
   for (auto& a : c->ev_free)
@@ -145,7 +155,7 @@ int log2i(int v) {
   return l;
 }
 
-size_t esize(int prec) { return prec == SADI_PREC_FP32 ? sizeof(float) : sizeof(double); }
+size_t esize(int prec) { return prec == SADI_PREC_FP64 ? sizeof(double) : sizeof(float); }
 
 sadi_status alloc_state(sadi_ctx* c) {
   const size_t nn = (size_t)c->g.N * c->g.N;
@@ -158,7 +168,7 @@ sadi_status alloc_state(sadi_ctx* c) {
   }
   if (c->ulo) cudaFree(c->ulo);
   c->ulo = nullptr;
-  if (c->prec == SADI_PREC_FP32) CK(cudaMalloc(&c->ulo, nn * sizeof(float)), "cudaMalloc(state lo)");
+  if (c->prec != SADI_PREC_FP64) CK(cudaMalloc(&c->ulo, nn * sizeof(float)), "cudaMalloc(state lo)");
   if (c->phi2) cudaFree(c->phi2);
   if (c->S) cudaFree(c->S);
   if (c->W) cudaFree(c->W);
@@ -167,6 +177,34 @@ sadi_status alloc_state(sadi_ctx* c) {
   CK(cudaMalloc(&c->S, (size_t)c->g.N * c->g.Np * 2 * es), "cudaMalloc(spectrum)");
   CK(cudaMalloc(&c->W, nn * es), "cudaMalloc(sweep)");
   (void)e;
+  return SADI_OK;
+}
+
+// Buffers, dense inverse and GEMM tensor maps of the dense-inverse form (once).
+sadi_status setup_dense(sadi_ctx* c) {
+  if (c->Eh) return SADI_OK;
+  const int np = (c->g.N + kTcTileN - 1) / kTcTileN * kTcTileN;
+  const size_t bytes = (size_t)np * np * sizeof(unsigned short);
+  unsigned short** bufs[] = {&c->Eh, &c->El, &c->Bh, &c->Bl, &c->WTh, &c->WTl};
+  for (auto b : bufs) {
+    if (cudaMalloc(reinterpret_cast<void**>(b), bytes) != cudaSuccess)
+      return fail(c, SADI_ENOMEM, "cudaMalloc(dense-inverse buffers) failed");
+  }
+  CK(cudaMalloc(&c->tcerr, sizeof(int)), "cudaMalloc(error flag)");
+  cudaStream_t st = c->stream;
+  CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), st), "error flag");
+  for (int k = 2; k < 6; ++k) CK(cudaMemsetAsync(*bufs[k], 0, bytes, st), "dense padding");
+  int stat = 1;
+  CK(run_dense_inverse(c->a1, c->g.N, c->s, np, c->Eh, c->El, &stat, st), "dense inverse");
+  if (stat != 0) return fail(c, SADI_ENOTSPD, "Durbin recursion of the N x N generator broke down");
+  c->tc_x.reset(new (std::nothrow) TcInst());
+  c->tc_y.reset(new (std::nothrow) TcInst());
+  if (!c->tc_x || !c->tc_y) return fail(c, SADI_ENOMEM, "host allocation failed");
+  // x sweep: ACC[j][i] = sum_k B[j][k] E[i][k]; y sweep: ACC[j][i] = sum_k E[j][k] W^T[i][k]
+  CK(tc_set_operands(c->tc_x.get(), c->Bh, c->Bl, c->Eh, c->El, np, np, np), "tensor maps (x sweep)");
+  CK(tc_set_operands(c->tc_y.get(), c->Eh, c->El, c->WTh, c->WTl, np, np, np), "tensor maps (y sweep)");
+  CK(cudaStreamSynchronize(st), "dense setup");
+  c->npad = np;
   return SADI_OK;
 }
 
@@ -288,9 +326,17 @@ sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
   if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
   if (c->initialized) return fail(c, SADI_ESTATE, "sadi_set_options must precede sadi_set_initial");
   if (g < SADI_G_ZERO || g > SADI_G_NEG_SIN) return fail(c, SADI_EINVAL, "g must be 0, 1 or 2");
-  if (prec != SADI_PREC_FP64 && prec != SADI_PREC_FP32) return fail(c, SADI_EINVAL, "prec must be 0 or 1");
+  if (prec != SADI_PREC_FP64 && prec != SADI_PREC_FP32 && prec != SADI_PREC_FP32_DENSE)
+    return fail(c, SADI_EINVAL, "prec must be 0, 1 or 2");
   if (prec == SADI_PREC_FP64 && c->g.N > 4096)
     return fail(c, SADI_EUNSUPPORTED, "the FP64 step path supports N <= 4096");
+  if (prec == SADI_PREC_FP32_DENSE && c->g.N > 4096)
+    return fail(c, SADI_EUNSUPPORTED, "the dense-inverse form supports N <= 4096");
+  if (prec != c->prec && c->F) return fail(c, SADI_ESTATE, "set the precision before sadi_set_source");
+  if (prec == SADI_PREC_FP32_DENSE) {
+    const sadi_status ds = setup_dense(c);
+    if (ds != SADI_OK) return ds;
+  }
   c->gkind = g;
   if (prec != c->prec) {
     if (c->F) return fail(c, SADI_ESTATE, "set the precision before sadi_set_source");
@@ -403,10 +449,14 @@ RegInst reg_inst(const sadi_ctx* c) {
   r.first = c->n == 0 ? 1 : 0;
   r.F = static_cast<const float*>(c->F);
   r.fsc = c->F ? (float)std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.f;
+  r.Bh = c->Bh;
+  r.Bl = c->Bl;
+  r.ldp = c->npad;
   return r;
 }
 
 bool uses_reg_path(const sadi_ctx* c) { return c->prec == SADI_PREC_FP32 && c->reg_path; }
+bool is_dense(const sadi_ctx* c) { return c->prec == SADI_PREC_FP32_DENSE; }
 
 // One step of a context on the shared-memory engine (FP64, or FP32 N' > 1024),
 // on stream st.
@@ -456,6 +506,74 @@ sadi_status step_reg_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
   return SADI_OK;
 }
 
+// One step of count dense-form contexts with equal FFT length on stream st:
+// the FFT part batched (register path, N' <= 1024; count == 1 otherwise), then
+// the x-sweep and y-sweep GEMMs batched (at most kTcMaxBatch per launch).
+sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
+  sadi_ctx* c = cs[0];
+  cudaEvent_t* ev = nullptr;
+  sadi_status st = next_events(c, &ev);
+  if (st != SADI_OK) return st;
+  cudaError_t e;
+  if (c->reg_path) {
+    static thread_local RegBatch b;
+    b.count = count;
+    int max_n = 0;
+    for (int k = 0; k < count; ++k) {
+      b.in[k] = reg_inst(cs[k]);
+      if (cs[k]->g.N > max_n) max_n = cs[k]->g.N;
+    }
+    e = launch_step_reg(b, c->g.logNp, max_n, st_, ev, true);
+  } else {
+    if (count != 1) return fail(c, SADI_EINVAL, "internal: shared-memory dense group of more than one");
+    RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0, c->F,
+                 c->F ? std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.0};
+    StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+    e = launch_dense_rows(c->g, tb, c->tiles32, rp, static_cast<const float*>(c->ubuf[0]),
+                          static_cast<const float*>(c->phi2), c->S, static_cast<float*>(c->W), c->Bh, c->Bl, c->npad,
+                          st_, ev);
+  }
+  // x sweeps of all members, then y sweeps (each in launches of <= kTcMaxBatch)
+  static thread_local TcBatch tb;
+  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
+    for (int k0 = 0; e == cudaSuccess && k0 < count; k0 += kTcMaxBatch) {
+      const int m = count - k0 < kTcMaxBatch ? count - k0 : kTcMaxBatch;
+      tb.count = m;
+      for (int k = 0; k < m; ++k) {
+        const sadi_ctx* ck = cs[k0 + k];
+        tb.in[k] = pass == 0 ? *ck->tc_x : *ck->tc_y;
+        TcEpi& ep = tb.in[k].e;
+        ep = TcEpi{};
+        ep.m_valid = ep.n_valid = ck->g.N;
+        ep.C = static_cast<float*>(ck->W);
+        ep.ldc = ck->g.N;
+        ep.err = ck->tcerr;
+        if (pass == 0) {
+          ep.mode = kTcSweepX;
+          ep.t_hi = ck->WTh;
+          ep.t_lo = ck->WTl;
+          ep.ldt = ck->npad;
+        } else {
+          ep.mode = kTcSweepY;
+          ep.u_hi = static_cast<float*>(ck->ubuf[0]);
+          ep.u_lo = ck->ulo;
+          ep.u_d = static_cast<float*>(ck->ubuf[1]);
+          ep.ldu = ck->g.N;
+          ep.first = ck->n == 0 ? 1 : 0;
+        }
+      }
+      e = launch_tc_gemm(tb, cs[k0]->tcerr, st_);
+    }
+    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3 + pass], st_);
+  }
+  if (e != cudaSuccess) {
+    for (int k = 0; k < count; ++k) cuda_fail(cs[k], e, "dense step launch");
+    return SADI_ECUDA;
+  }
+  for (int k = 0; k < count; ++k) cs[k]->n += 1;
+  return SADI_OK;
+}
+
 sadi_status check_steppable(sadi_ctx* c) {
   if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
   if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_step before sadi_set_initial");
@@ -472,7 +590,9 @@ sadi_status sadi_step(sadi_ctx* c, int nsteps) {
   if (st != SADI_OK) return st;
   if (nsteps < 0) return fail(c, SADI_EINVAL, "nsteps must be >= 0");
   for (int it = 0; it < nsteps; ++it) {
-    if (uses_reg_path(c)) {
+    if (is_dense(c)) {
+      st = step_dense_group(&c, 1, c->stream);
+    } else if (uses_reg_path(c)) {
       st = step_reg_group(&c, 1, c->stream);
     } else {
       cudaEvent_t* ev = nullptr;
@@ -494,17 +614,19 @@ sadi_status sadi_batch_step(sadi_ctx** ctxs, int count, int nsteps) {
     if (st != SADI_OK) return st;
   }
   // group register-path contexts by FFT length (insertion order kept)
+  // (dense-form contexts on the register path form their own groups)
   std::vector<std::vector<sadi_ctx*>> groups;
   std::vector<sadi_ctx*> others;
   for (int k = 0; k < count; ++k) {
     sadi_ctx* c = ctxs[k];
-    if (!uses_reg_path(c)) {
+    const bool dense_reg = is_dense(c) && c->reg_path;
+    if (!uses_reg_path(c) && !dense_reg) {
       others.push_back(c);
       continue;
     }
     bool placed = false;
     for (auto& gr : groups)
-      if (gr[0]->g.logNp == c->g.logNp && (int)gr.size() < kMaxBatch) {
+      if (gr[0]->g.logNp == c->g.logNp && is_dense(gr[0]) == is_dense(c) && (int)gr.size() < kMaxBatch) {
         gr.push_back(c);
         placed = true;
         break;
@@ -523,10 +645,16 @@ sadi_status sadi_batch_step(sadi_ctx** ctxs, int count, int nsteps) {
   }
   for (int it = 0; it < nsteps; ++it) {
     for (auto& gr : groups) {
-      sadi_status st = step_reg_group(gr.data(), (int)gr.size(), s0);
+      sadi_status st = is_dense(gr[0]) ? step_dense_group(gr.data(), (int)gr.size(), s0)
+                                       : step_reg_group(gr.data(), (int)gr.size(), s0);
       if (st != SADI_OK) return st;
     }
     for (sadi_ctx* c : others) {
+      if (is_dense(c)) {
+        sadi_status st = step_dense_group(&c, 1, s0);
+        if (st != SADI_OK) return st;
+        continue;
+      }
       cudaEvent_t* ev = nullptr;
       sadi_status st = next_events(c, &ev);
       if (st == SADI_OK) st = step_smem(c, ev, s0);
@@ -560,6 +688,14 @@ sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {
     CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   }
   CK(cudaStreamSynchronize(st), "sadi_get");
+  if (c->tcerr) {
+    int flag = 0;
+    CK(cudaMemcpy(&flag, c->tcerr, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+    if (flag) {
+      c->broken = true;
+      return fail(c, SADI_ETIMEOUT, "a bounded wait in a tensor-core sweep ran out; the state is invalid");
+    }
+  }
   if (n_out) *n_out = c->n;
   return SADI_OK;
 }
@@ -596,7 +732,25 @@ sadi_status sadi_get_setup(sadi_ctx* c, int which, double* out, size_t count) {
     case 1: src = c->a2d; n = N * N; break;
     case 2: src = c->cgen; n = Np; break;
     case 3: src = c->lnat; n = (Np + 1) * (Np + 1); break;
-    default: return fail(c, SADI_EINVAL, "which must be 0..3");
+    case 4: {
+      if (!c->Eh) return fail(c, SADI_ESTATE, "which = 4 needs SADI_PREC_FP32_DENSE selected");
+      if (count != N * N) return fail(c, SADI_EINVAL, "count does not match the table size");
+      const size_t np = (size_t)c->npad;
+      std::vector<unsigned short> hi(np * np), lo(np * np);
+      CK(cudaMemcpyAsync(hi.data(), c->Eh, np * np * 2, cudaMemcpyDeviceToHost, c->stream), "copy E");
+      CK(cudaMemcpyAsync(lo.data(), c->El, np * np * 2, cudaMemcpyDeviceToHost, c->stream), "copy E");
+      CK(cudaStreamSynchronize(c->stream), "sadi_get_setup");
+      auto f = [](unsigned short b) {
+        const unsigned int w = (unsigned int)b << 16;
+        float v;
+        std::memcpy(&v, &w, sizeof(v));
+        return (double)v;
+      };
+      for (size_t i = 0; i < N; ++i)
+        for (size_t j = 0; j < N; ++j) out[i * N + j] = f(hi[i * np + j]) + f(lo[i * np + j]);
+      return SADI_OK;
+    }
+    default: return fail(c, SADI_EINVAL, "which must be 0..4");
   }
   if (count != n) return fail(c, SADI_EINVAL, "count does not match the table size");
   CK(cudaMemcpyAsync(out, src, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream), "copy setup table");

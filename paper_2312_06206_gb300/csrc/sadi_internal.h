@@ -96,6 +96,9 @@ struct RegInst {
   float2* S;            // N x N' spectrum scratch
   float* W;             // N x N sweep scratch
   const float* F;       // optional source field (N x N) or nullptr
+  unsigned short* Bh;   // dense-inverse form: BF16 split of B^n (ld ldp, zero-padded)
+  unsigned short* Bl;
+  int ldp;
   int N, r;
   float tau, tau2;
   float fsc;            // time factor of the source for this step
@@ -109,8 +112,11 @@ struct RegBatch {
 };
 bool reg_path_supported(int logNp);
 // One step of every instance of the batch (all with FFT length 2^logNp);
-// max_n = the largest N in the batch.
-cudaError_t launch_step_reg(const RegBatch& b, int logNp, int max_n, cudaStream_t st, cudaEvent_t* ev);
+// max_n = the largest N in the batch.  dense: only the row FFT, the column
+// convolution and the B^n kernel run (events 0..2), the latter writing B^n to
+// W and its BF16 split to Bh / Bl; the sweeps are left to the GEMMs.
+cudaError_t launch_step_reg(const RegBatch& b, int logNp, int max_n, cudaStream_t st, cudaEvent_t* ev,
+                            bool dense = false);
 // natural-order FP32 tables of the register path from the FP64 setup products
 cudaError_t run_reg_tables(const Geom& g, const double* lnat, double scale, const double2* lamc64,
                            const double2* lams64, float2* tw1, float* lreg, float2* lamc_nat, float2* lams_nat,
@@ -126,6 +132,19 @@ template <typename T>
 cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
                         T* u_prev, T* u_next, T* u_lo, const T* phi2, void* S, T* W, cudaStream_t st,
                         cudaEvent_t* ev = nullptr);
+
+// Dense-inverse form on the shared-memory engine (FP32): row FFT, column
+// convolution and B^n (events 0..2); B^n goes to W (N x N) and its BF16 split
+// to Bh / Bl (ld ldp).
+cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const Tiles& tl, const RhsParams& rp,
+                              const float* u_cur, const float* phi2, void* S, float* W, unsigned short* Bh,
+                              unsigned short* Bl, int ldp, cudaStream_t st, cudaEvent_t* ev);
+// H^-1 - I of the N x N Toeplitz matrix H = I + s T(a_0 .. a_{N-1}) as a
+// zero-padded npad x npad BF16 pair (Eh, El), from the generator c = H^-1 e_1
+// (Durbin recursion) and the Gohberg-Semencul diagonal recurrence, in FP64.
+// *status_host: 0 on success, 1 if the recursion broke down.
+cudaError_t run_dense_inverse(const double* a1, int N, double s, int npad, void* Eh, void* El, int* status_host,
+                              cudaStream_t st);
 
 // ---- split-BF16 tensor-core GEMM, gemm_tc.cu ----------------------------------
 // ACC = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T over K-major BF16 operands
@@ -146,24 +165,29 @@ struct TcEpi {
   float* u_d;
   int ldu;
   int first;
+  int* err;                   // set to 1 if a bounded wait of this problem's CTAs ran out (or nullptr)
 };
 struct TcInst {
   CUtensorMap a_hi, a_lo;     // A operand (M rows), box 128 x 64
   CUtensorMap b_hi, b_lo;     // B operand (N rows), box 256 x 64
   TcEpi e;
+  int K;                      // padded contraction length (multiple of 64)
+  int tiles_m, tiles_n;       // padded M / 128 and N / 256 of this problem
 };
 // passed by value as a __grid_constant__ kernel parameter (about 10 KB)
 struct TcBatch {
   int count;
-  int K;
   TcInst in[kTcMaxBatch];
 };
 // tensor map of a rows x kdim BF16 matrix (row-major) with box box_rows x 64
 cudaError_t tc_encode(CUtensorMap* map, const void* base, int rows, int kdim, int box_rows);
+// tensor maps and extents of one problem: A is M x K, B is N x K (padded sizes)
 cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, const void* b_hi, const void* b_lo,
                             int M, int N, int K);
-// one launch for all b.count problems (each M x N, K = b.K); *err set on a timed-out wait
-cudaError_t launch_tc_gemm(const TcBatch& b, int M, int N, int* err, cudaStream_t st);
+// one launch for all b.count problems (blockIdx.z); the grid covers the largest
+// problem and the CTAs beyond a smaller one exit at once; *err set on a
+// timed-out wait
+cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st);
 // FP32 rows x cols (ld src_ld) -> zero-padded prow x pcol BF16 hi / lo
 cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,
                              cudaStream_t st);

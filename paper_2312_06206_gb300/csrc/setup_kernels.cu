@@ -14,6 +14,7 @@
 //     exact solver gives the same c'), the spectra lambda_c = fft(c'),
 //     lambda_s = fft(Q s') (eq. "eigenvalue of CS"), and the correction that
 //     turns the bordered solve into H^-1.
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
@@ -467,6 +468,33 @@ cudaError_t launch_convert_f2d(const float* s, double* d, size_t n, cudaStream_t
   return cudaGetLastError();
 }
 
+// H^-1 - I from the generator c = H^-1 e_1 of the symmetric Toeplitz H (n x n),
+// by the Gohberg-Semencul identity H^-1 = (1/c_0)(L(c) L(c)^T - L(y) L(y)^T),
+// y = (0, c_{n-1}, ..., c_1), read along diagonals:
+//   (H^-1)[d + j][j] = (H^-1)[d + j - 1][j - 1] + (c_{d+j} c_j - y_{d+j} y_j) / c_0,
+//   (H^-1)[d][0] = c_d.
+// One thread per diagonal d; both triangles written (symmetry), as BF16 pairs.
+__global__ void k_dense_inverse(const double* __restrict__ c, int n, int npad, unsigned short* Eh,
+                                unsigned short* El) {
+  const int d = blockIdx.x * blockDim.x + threadIdx.x;
+  if (d >= n) return;
+  const double c0 = c[0];
+  double v = c[d];
+  for (int j = 0; j < n - d; ++j) {
+    if (j > 0) v += (c[d + j] * c[j] - c[n - d - j] * c[n - j]) / c0;
+    const double e = (d == 0) ? v - 1.0 : v;
+    const float ef = (float)e;
+    const __nv_bfloat16 h = __float2bfloat16_rn(ef);
+    const unsigned short hb = __bfloat16_as_ushort(h);
+    const unsigned short lb = __bfloat16_as_ushort(__float2bfloat16_rn((float)(e - (double)__bfloat162float(h))));
+    const size_t a = (size_t)(d + j) * npad + j, b = (size_t)j * npad + (d + j);
+    Eh[a] = hb;
+    El[a] = lb;
+    Eh[b] = hb;
+    El[b] = lb;
+  }
+}
+
 #define SADI_TRY(x)                        \
   do {                                     \
     cudaError_t e_ = (x);                  \
@@ -575,6 +603,33 @@ done:
   cudaFree(X);
   cudaFree(Mb);
   cudaFree(Inv);
+  return err;
+}
+
+cudaError_t run_dense_inverse(const double* a1, int N, double s, int npad, void* Eh, void* El, int* status_host,
+                              cudaStream_t st) {
+  cudaError_t err = cudaSuccess;
+  int* dstat = nullptr;
+  double* c = nullptr;
+  *status_host = 1;
+  const size_t smd = sizeof(double) * (2 * (size_t)N + 1 + 32);
+  const size_t ne = (size_t)npad * npad * sizeof(unsigned short);
+  SADI_TRY(cudaFuncSetAttribute(k_durbin, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024));
+  if (smd > 227 * 1024) { err = cudaErrorInvalidConfiguration; goto done; }
+  SADI_TRY(cudaMalloc(&dstat, sizeof(int)));
+  SADI_TRY(cudaMalloc(&c, sizeof(double) * N));
+  k_durbin<<<1, 1024, smd, st>>>(a1, N, s, c, dstat);
+  SADI_TRY(cudaGetLastError());
+  SADI_TRY(cudaMemsetAsync(Eh, 0, ne, st));
+  SADI_TRY(cudaMemsetAsync(El, 0, ne, st));
+  k_dense_inverse<<<nblk(N, 128), 128, 0, st>>>(c, N, npad, static_cast<unsigned short*>(Eh),
+                                                static_cast<unsigned short*>(El));
+  SADI_TRY(cudaGetLastError());
+  SADI_TRY(cudaMemcpyAsync(status_host, dstat, sizeof(int), cudaMemcpyDeviceToHost, st));
+  SADI_TRY(cudaStreamSynchronize(st));
+done:
+  cudaFree(dstat);
+  cudaFree(c);
   return err;
 }
 

@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
+#include "bf16split.cuh"
 #include "sadi_internal.h"
 
 namespace sadi {
@@ -237,11 +238,14 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
 // (gives -kappa tau^2 L_h u^n, the scale being folded into the symbol),
 // B^n epilogue with g(u^n) (and phi2 when n = 0), then the x sweep W_j = H^-1 B_j.
 // ---------------------------------------------------------------------------
-template <typename T>
+// DENSE: the dense-inverse form stops after B^n, which it writes to W and,
+// split into BF16 pairs, to Bh / Bl (ld ldp).
+template <typename T, bool DENSE = false>
 __global__ void __launch_bounds__(kThreads)
 k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ phi2, T* __restrict__ W,
              Geom g, RhsParams rp, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-             const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR) {
+             const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR,
+             unsigned short* Bh = nullptr, unsigned short* Bl = nullptr, int ldp = 0) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
@@ -316,6 +320,27 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
         }
       }
     }
+  }
+  if constexpr (DENSE) {
+#pragma unroll
+    for (int it = 0; it < kMaxPairs; ++it) {
+      const int t = threadIdx.x + it * blockDim.x;
+      if (t < npairs) {
+        const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
+        if (v < nrows) {
+          const size_t row = (size_t)(row0 + v);
+          if (k < N) {
+            W[row * N + k] = ra[it];
+            split_bf16(ra[it], Bh + row * ldp + k, Bl + row * ldp + k);
+          }
+          if (k2 < N) {
+            W[row * N + k2] = rb[it];
+            split_bf16(rb[it], Bh + row * ldp + k2, Bl + row * ldp + k2);
+          }
+        }
+      }
+    }
+    return;
   }
   __syncthreads();
 #pragma unroll
@@ -392,6 +417,9 @@ cudaError_t step_setup_attributes() {
   if ((e = cudaFuncSetAttribute(k_cols_conv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_rows_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_cols_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if constexpr (sizeof(T) == 4) {
+    if ((e = cudaFuncSetAttribute(k_rows_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  }
   return cudaSuccess;
 }
 
@@ -461,5 +489,28 @@ template cudaError_t launch_step<float>(const Geom&, const StepTables<float>&, c
 template cudaError_t launch_step<double>(const Geom&, const StepTables<double>&, const Tiles&, const RhsParams&,
                                          const double*, double*, double*, double*, const double*, void*, double*,
                                          cudaStream_t, cudaEvent_t*);
+
+cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const Tiles& tl, const RhsParams& rp,
+                              const float* u_cur, const float* phi2, void* Sv, float* W, unsigned short* Bh,
+                              unsigned short* Bl, int ldp, cudaStream_t st, cudaEvent_t* ev) {
+  using T = float;
+  const cx<T>* stw = reinterpret_cast<const cx<T>*>(tb.stw);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
+  const cx<T>* ls = reinterpret_cast<const cx<T>*>(tb.lam_s);
+  const cx<T>* lc = reinterpret_cast<const cx<T>*>(tb.lam_c);
+  cx<T>* S = reinterpret_cast<cx<T>*>(Sv);
+  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  if (!tiles_valid<T>(g, tl)) return cudaErrorInvalidConfiguration;
+  const int NR = tl.rows, CTc = tl.conv_cols;
+  const int rblocks = (g.N + NR - 1) / NR;
+  if (ev) cudaEventRecord(ev[0], st);
+  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, stw, tw, NR);
+  if (ev) cudaEventRecord(ev[1], st);
+  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
+  if (ev) cudaEventRecord(ev[2], st);
+  k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR,
+                                                                 Bh, Bl, ldp);
+  return cudaGetLastError();
+}
 
 }  // namespace sadi

@@ -4,22 +4,22 @@
 namespace sadi {
 namespace regk {
 template <int LOGL>
-cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev);
+cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev, bool dense);
 }  // namespace regk
 
 bool reg_path_supported(int logNp) { return logNp >= 3 && logNp <= 10; }
 
-cudaError_t launch_step_reg(const RegBatch& b, int logNp, int max_n, cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t launch_step_reg(const RegBatch& b, int logNp, int max_n, cudaStream_t st, cudaEvent_t* ev, bool dense) {
   if (b.count < 1 || b.count > kMaxBatch) return cudaErrorInvalidValue;
   switch (logNp) {
-    case 3: return regk::launch_reg_impl<3>(b, max_n, st, ev);
-    case 4: return regk::launch_reg_impl<4>(b, max_n, st, ev);
-    case 5: return regk::launch_reg_impl<5>(b, max_n, st, ev);
-    case 6: return regk::launch_reg_impl<6>(b, max_n, st, ev);
-    case 7: return regk::launch_reg_impl<7>(b, max_n, st, ev);
-    case 8: return regk::launch_reg_impl<8>(b, max_n, st, ev);
-    case 9: return regk::launch_reg_impl<9>(b, max_n, st, ev);
-    case 10: return regk::launch_reg_impl<10>(b, max_n, st, ev);
+    case 3: return regk::launch_reg_impl<3>(b, max_n, st, ev, dense);
+    case 4: return regk::launch_reg_impl<4>(b, max_n, st, ev, dense);
+    case 5: return regk::launch_reg_impl<5>(b, max_n, st, ev, dense);
+    case 6: return regk::launch_reg_impl<6>(b, max_n, st, ev, dense);
+    case 7: return regk::launch_reg_impl<7>(b, max_n, st, ev, dense);
+    case 8: return regk::launch_reg_impl<8>(b, max_n, st, ev, dense);
+    case 9: return regk::launch_reg_impl<9>(b, max_n, st, ev, dense);
+    case 10: return regk::launch_reg_impl<10>(b, max_n, st, ev, dense);
     default: return cudaErrorInvalidValue;
   }
 }

@@ -11,6 +11,7 @@
 #pragma once
 #include <cuda_runtime.h>
 
+#include "bf16split.cuh"
 #include "regfft.cuh"
 #include "sadi_internal.h"
 
@@ -249,7 +250,9 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__
 }
 
 // ---------------------------------------------------------------------------
-template <int LOGL, int BLOCK>
+// DENSE: the dense-inverse form stops after B^n, which it writes to W (FP32)
+// and, split into BF16 pairs, to Bh / Bl (the first sweep GEMM's A operand).
+template <int LOGL, int BLOCK, bool DENSE = false>
 __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant__ RegBatch B) {
   using F = rf::RegFFT<float, LOGL>;
   using C = RowCfg<LOGL, BLOCK>;
@@ -329,6 +332,22 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
     sm[pad32(n)] = make_float2(b0, b1);
   }
   __syncthreads();
+  if constexpr (DENSE) {
+    if (!valid) return;
+    float* wrow = I.W + (size_t)row * N;
+    unsigned short* bh = I.Bh + (size_t)row * I.ldp;
+    unsigned short* bl = I.Bl + (size_t)row * I.ldp;
+#pragma unroll 2
+    for (int q = 0; q < F::E; ++q) {
+      const int k = t + F::TT * q;
+      if (k < N) {
+        const float b = real_at(sm, k);
+        wrow[k] = b;
+        split_bf16(b, bh + k, bl + k);
+      }
+    }
+    return;
+  }
   // v1 = Q (B' + i J B')
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
@@ -436,7 +455,7 @@ constexpr int kRowBlock = 128;
 constexpr int kColBlock = 128;
 
 template <int LOGL>
-cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev) {
+cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev, bool dense) {
   using RC = RowCfg<LOGL, kRowBlock>;
   using CC = ColCfg<LOGL, kColBlock>;
   constexpr int Np = 1 << LOGL;
@@ -445,6 +464,8 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
     cudaFuncSetAttribute(kr_rows_r2c<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)RC::bytes_r2c);
     cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)RC::bytes_solve);
+    cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)RC::bytes_solve);
     cudaFuncSetAttribute(kr_cols_conv<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)CC::bytes_conv);
@@ -460,6 +481,10 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
   if (ev) cudaEventRecord(ev[1], st);
   kr_cols_conv<LOGL, kColBlock><<<cgrid, kColBlock, CC::bytes_conv, st>>>(b);
   if (ev) cudaEventRecord(ev[2], st);
+  if (dense) {
+    kr_rows_solve<LOGL, kRowBlock, true><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
+    return cudaGetLastError();
+  }
   kr_rows_solve<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
   if (ev) cudaEventRecord(ev[3], st);
   kr_cols_solve<LOGL, kColBlock><<<sgrid, kColBlock, CC::bytes_solve, st>>>(b);

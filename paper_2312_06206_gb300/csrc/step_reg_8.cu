@@ -3,6 +3,6 @@
 
 namespace sadi {
 namespace regk {
-template cudaError_t launch_reg_impl<8>(const RegBatch&, int, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_reg_impl<8>(const RegBatch&, int, cudaStream_t, cudaEvent_t*, bool);
 }  // namespace regk
 }  // namespace sadi

@@ -3,10 +3,10 @@
 
 namespace sadi {
 namespace regk {
-template cudaError_t launch_reg_impl<3>(const RegBatch&, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_reg_impl<4>(const RegBatch&, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_reg_impl<5>(const RegBatch&, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_reg_impl<6>(const RegBatch&, int, cudaStream_t, cudaEvent_t*);
-template cudaError_t launch_reg_impl<7>(const RegBatch&, int, cudaStream_t, cudaEvent_t*);
+template cudaError_t launch_reg_impl<3>(const RegBatch&, int, cudaStream_t, cudaEvent_t*, bool);
+template cudaError_t launch_reg_impl<4>(const RegBatch&, int, cudaStream_t, cudaEvent_t*, bool);
+template cudaError_t launch_reg_impl<5>(const RegBatch&, int, cudaStream_t, cudaEvent_t*, bool);
+template cudaError_t launch_reg_impl<6>(const RegBatch&, int, cudaStream_t, cudaEvent_t*, bool);
+template cudaError_t launch_reg_impl<7>(const RegBatch&, int, cudaStream_t, cudaEvent_t*, bool);
 }  // namespace regk
 }  // namespace sadi

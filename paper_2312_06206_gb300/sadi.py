@@ -19,7 +19,7 @@ SADI_OK, SADI_EINVAL, SADI_ENOMEM, SADI_ECUDA, SADI_ENOTSPD, SADI_ESTATE, SADI_E
 STATUS_NAMES = {0: "SADI_OK", 1: "SADI_EINVAL", 2: "SADI_ENOMEM", 3: "SADI_ECUDA", 4: "SADI_ENOTSPD",
                 5: "SADI_ESTATE", 6: "SADI_ETIMEOUT", 7: "SADI_ENONFINITE", 8: "SADI_EUNSUPPORTED"}
 SADI_G_ZERO, SADI_G_NEG_CUBE, SADI_G_NEG_SIN = 0, 1, 2
-SADI_PREC_FP64, SADI_PREC_FP32 = 0, 1
+SADI_PREC_FP64, SADI_PREC_FP32, SADI_PREC_FP32_DENSE = 0, 1, 2
 
 # every symbol include/sadi.h declares, with its ctypes signature
 _SIGS = {
@@ -148,10 +148,10 @@ class Sadi:
 
     def sadi_get_setup(self, which: int):
         Np, _ = self.sadi_get_info()
-        n = {0: self.N, 1: self.N * self.N, 2: Np, 3: (Np + 1) ** 2}[which]
+        n = {0: self.N, 1: self.N * self.N, 2: Np, 3: (Np + 1) ** 2, 4: self.N * self.N}[which]
         out = np.empty(n, dtype=np.float64)
         _check(lib().sadi_get_setup(self.ctx, int(which), out.ctypes.data, n), self.ctx)
-        if which == 1:
+        if which in (1, 4):
             return out.reshape(self.N, self.N)
         if which == 3:
             return out.reshape(Np + 1, Np + 1)

@@ -1,0 +1,149 @@
+"""The dense-inverse form (SADI_PREC_FP32_DENSE): both sweeps as split-BF16
+tensor-core GEMMs with H^-1 = I + E, against the FP64 oracle.
+
+Tolerances: the stored E (a BF16 pair) to 2^-16 of each entry; whole steps
+1e-5 relative L2 as for the FP32 form."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import sadi as O
+from oracle import weights as OW
+from paper_2312_06206_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_06206_gb300 import build
+    build.build()
+    from paper_2312_06206_gb300 import sadi
+    return sadi
+
+
+def _run(S, N, alpha, kappa, tau, g, phi1, phi2, steps, prec, dom=(-1.0, 1.0), F=None, om=0.0, ph=0.0):
+    with S.Sadi(N, alpha, kappa, tau, dom) as s:
+        s.set_options(g, prec)
+        if F is not None:
+            s.sadi_set_source(F, om, ph)
+        s.set_initial(phi1, phi2)
+        s.step(steps)
+        u, n = s.get()
+    assert n == steps
+    return u
+
+
+@pytest.mark.parametrize("N,alpha,tau", [(1, 1.5, 0.1), (7, 1.3, 0.05), (63, 1.5, 0.02), (200, 1.8, 0.01),
+                                         (1023, 1.2, 1e-3)])
+def test_dense_inverse_matches_oracle_inverse(S, N, alpha, tau):
+    kappa = 1.0
+    with S.Sadi(N, alpha, kappa, tau) as s:
+        s.set_options(0, S.SADI_PREC_FP32_DENSE)
+        E = s.sadi_get_setup(4)
+    h = 2.0 / (N + 1)
+    sc = kappa * tau ** 2 / (2 * h ** alpha)
+    H = np.eye(N) + sc * scipy.linalg.toeplitz(OW.riesz_1d(alpha, N))
+    Eref = scipy.linalg.cho_solve(scipy.linalg.cho_factor(H), np.eye(N)) - np.eye(N)
+    # the BF16 pair keeps 16 bits of each entry (plus the FP64 recurrence error)
+    assert np.all(np.abs(E - Eref) <= 2.0 ** -16 * np.abs(Eref) + 1e-13 * np.abs(Eref).max())
+    assert np.array_equal(E, E.T)
+
+
+def test_dense_setup_requires_the_dense_form(S):
+    with S.Sadi(15, 1.5, 1.0, 0.1) as s:
+        with pytest.raises(S.SadiError) as ei:
+            s.sadi_get_setup(4)
+        assert ei.value.status == S.SADI_ESTATE
+    with S.Sadi(4097, 1.5, 1.0, 1e-3) as s:
+        with pytest.raises(S.SadiError) as ei:
+            s.set_options(0, S.SADI_PREC_FP32_DENSE)
+        assert ei.value.status == S.SADI_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("N,alpha,g", [(1, 1.5, 1), (2, 1.3, 2), (5, 1.9, 0), (8, 1.6, 1), (9, 1.4, 2),
+                                       (31, 1.7, 2), (33, 1.2, 1), (63, 1.5, 1), (100, 1.3, 2), (255, 1.8, 2),
+                                       (257, 1.5, 1)])
+def test_dense_step_parity(S, N, alpha, g):
+    kappa, tau = 1.0, 0.02
+    phi1 = WL.gaussian_bumps(N, 8, 5 + N)
+    phi2 = 0.2 * WL.gaussian(N, 10.0)
+    steps = 10
+    P = O.Problem(N, alpha, kappa, tau, -1.0, 1.0, g)
+    ref = O.run(P, phi1, phi2, steps, tier="fft" if N > 40 else "direct")
+    u = _run(S, N, alpha, kappa, tau, g, phi1, phi2, steps, S.SADI_PREC_FP32_DENSE)
+    assert O.rel_l2(u, ref) <= 1e-5, O.rel_l2(u, ref)
+
+
+def test_dense_full_size_1023(S):
+    w = WL.bumps_1023(1.8, steps=4)
+    P = O.Problem(w.N, w.alpha, w.kappa, w.tau, w.a, w.b, w.g)
+    ref = O.run(P, w.phi1, w.phi2, w.steps, tier="fft")
+    u = _run(S, w.N, w.alpha, w.kappa, w.tau, w.g, w.phi1, w.phi2, w.steps, S.SADI_PREC_FP32_DENSE)
+    assert O.rel_l2(u, ref) <= 1e-5, O.rel_l2(u, ref)
+
+
+@pytest.mark.parametrize("N,alpha,g,steps", [(2047, 1.4, 1, 5), (4095, 1.7, 1, 3)])
+def test_dense_large_n_against_fp64(S, N, alpha, g, steps):
+    # N' = 2048, 4096: the FFT part on the shared-memory engine, the sweeps as
+    # 8 x 16 and 16 x 32 tiles of 128 x 256
+    tau, kappa = 5e-4, 0.5
+    phi1 = WL.gaussian_bumps(N, 8, 2000 + N)
+    u64 = _run(S, N, alpha, kappa, tau, g, phi1, None, steps, S.SADI_PREC_FP64)
+    ud = _run(S, N, alpha, kappa, tau, g, phi1, None, steps, S.SADI_PREC_FP32_DENSE)
+    assert O.rel_l2(ud, u64) <= 1e-5, O.rel_l2(ud, u64)
+
+
+def test_dense_source_term_and_second_order(S):
+    N, alpha, kappa, tau, g = 31, 1.4, 0.8, 0.04, 2
+    F = WL.random_field(N, 77)
+    om, ph = 2.3, 0.4
+    phi1 = WL.gaussian_bumps(N, 3, 78)
+    phi2 = 0.2 * WL.random_field(N, 79)
+    P = O.Problem(N, alpha, kappa, tau, -1.0, 1.0, g)
+    ref = O.run(P, phi1, phi2, 7, tier="direct", forcing=lambda n: np.cos(om * n * tau + ph) * F)
+    u = _run(S, N, alpha, kappa, tau, g, phi1, phi2, 7, S.SADI_PREC_FP32_DENSE, F=F, om=om, ph=ph)
+    assert O.rel_l2(u, ref) <= 1e-5
+    # manufactured solution U = cos(t) phi (g = 0): O(tau^2) convergence
+    N, alpha, kappa = 63, 1.5, 1.0
+    phi = WL.gaussian(N, 8.0)
+    errs = []
+    for M in (8, 16, 32):
+        tau = 1.0 / M
+        P = O.Problem(N, alpha, kappa, tau)
+        Fm = kappa * O.lh_direct(P, phi) - phi
+        u = _run(S, N, alpha, kappa, tau, 0, phi, None, M, S.SADI_PREC_FP32_DENSE, F=Fm, om=1.0)
+        errs.append(np.abs(u - np.cos(1.0) * phi).max())
+    orders = [np.log2(errs[k] / errs[k + 1]) for k in range(2)]
+    assert all(1.9 < o < 2.15 for o in orders), (orders, errs)
+
+
+def test_dense_batch_matches_single_contexts(S):
+    # dense contexts of one FFT length (N' = 64) batch their FFT kernels and
+    # their GEMMs (different N: 1 x 1 tiles each); an FP32 context of the same
+    # N' and a dense N' = 512 context join the same call
+    specs = [(63, 1.5, 1.0, 0.02, 1, 2), (50, 1.2, 0.7, 0.03, 2, 2), (33, 1.8, 1.3, 0.01, 0, 2),
+             (40, 1.6, 1.0, 0.02, 1, 1), (300, 1.3, 1.0, 0.01, 2, 2)]
+
+    def make():
+        out = []
+        for k, (N, al, ka, ta, g, prec) in enumerate(specs):
+            s = S.Sadi(N, al, ka, ta)
+            s.set_options(g, prec)
+            s.set_initial(WL.gaussian_bumps(N, 4, 300 + k), 0.3 * WL.random_field(N, 400 + k))
+            out.append(s)
+        return out
+    single = make()
+    for s in single:
+        s.step(6)
+    ref = [s.get()[0] for s in single]
+    batch = make()
+    S.sadi_batch_step(batch, 6)
+    for s, r in zip(batch, ref):
+        u, n = s.get()
+        assert n == 6 and np.array_equal(u, r)
+    for s in single + batch:
+        s.close()
