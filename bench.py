@@ -7,8 +7,12 @@ Workload (one bench "step" = one S-ADI time step of every instance):
   phi1 = 8 seeded Gaussian bumps (centres U(-0.6, 0.6)^2, widths U(0.05, 0.2),
   amplitudes U(-1, 1)), phi2 = 0.  Synthetic, seeded.
 Metric: grid-point updates per second, N^2 * steps * instances / time, for the
-chosen form (FP32 FFTs and sweeps, FP64 setup), with the plain FP64 GS-FFT
-path on the same GPU and the relative L2 difference between the two stated.
+chosen form, with the plain FP64 GS-FFT path on the same GPU and each form's
+relative L2 difference to it stated.  Candidate forms: FP32 FFTs with
+Gohberg-Semencul FFT sweeps, and (N <= 4096) FP32 FFTs with both sweeps as
+split-BF16 dense-inverse GEMMs on the tensor cores; the chosen form is the
+fastest one within 1e-5 relative L2 of the FP64 path after the accuracy run
+(--acc-steps, default 1000 steps from the same data).
 
 Timing: W untimed warm-up steps, then K timed steps; each step is bracketed
 by CUDA events on the launching stream and an L2 flush (a 256 MiB write) runs
@@ -241,18 +245,22 @@ def aggregate(times, world_size, pts_per_step, steps_list, reduce_max=None):
             "ms32": ms32, "ms64": ms64, "e2e_s": e2e}
 
 
-def algorithmic(N, Np, es):
-    """Per-launch algorithmic work of each kernel (one instance), for the
-    roofline: (bytes, flops).  FFT flops are the nominal 5 L log2 L of a
-    complex FFT of length L."""
+def algorithmic(N, Np, es, dense=False):
+    """Per-launch algorithmic work of the four timed phases of one instance,
+    for the roofline: [(bytes, flops, bound)].  FFT flops are the nominal
+    5 L log2 L of a complex FFT of length L; a split-BF16 sweep GEMM counts
+    three BF16 products of 2 N^3 flops."""
     cs = 2 * es
     fft = 5.0 * Np * math.log2(Np)
-    return {
-        "k_rows_r2c": (N * N * es + N * Np * cs, N * fft),
-        "k_cols_conv": (2 * N * Np * cs + 2 * Np * Np * es, Np * 4 * fft),
-        "k_rows_solve": (N * Np * cs + 2 * N * N * es, N * 5 * fft),
-        "k_cols_solve": (4 * N * N * es, N * 4 * fft),
-    }
+    r2c = (N * N * es + N * Np * cs, N * fft, "alu")
+    conv = (2 * N * Np * cs + 2 * Np * Np * es, Np * 4 * fft, "alu")
+    if not dense:
+        return [r2c, conv, (N * Np * cs + 2 * N * N * es, N * 5 * fft, "alu"),
+                (4 * N * N * es, N * 4 * fft, "alu")]
+    gemm_bytes = 4 * N * N * 2 + 3 * N * N * es
+    # phase 2 is the B^n kernel followed by the x-sweep GEMM (one event pair)
+    return [r2c, conv, (N * Np * cs + 2 * N * N * es + 4 * N * N + gemm_bytes, N * fft + 6.0 * N ** 3, "mixed"),
+            (gemm_bytes + 4 * N * N * es, 6.0 * N ** 3, "tensor")]
 
 
 def main():
@@ -321,59 +329,104 @@ def main():
             phases = ([t / n for t in p], n)
         return ms, phases
 
-    # plain FP64 GS-FFT path
+    # plain FP64 GS-FFT path (the baseline of the metric)
     sampler = ClockSampler(local)
     sampler.start()
     has64 = N <= 4096                      # the FP64 step path supports N <= 4096
     c64 = make(S.SADI_PREC_FP64) if has64 else []
     K64 = max(1, min(a.steps, 20))
     ms64 = timed(c64, K64, a.warmup)[0] if has64 else float("nan")
-    # chosen form: FP32 FFTs and sweeps
-    c32 = make(S.SADI_PREC_FP32)
-    ms32, _ = timed(c32, a.steps, a.warmup)
+    # candidate forms: FP32 Gohberg-Semencul FFT sweeps, and (N <= 4096) the
+    # dense-inverse sweeps as split-BF16 tensor-core GEMMs
+    forms = [("fp32_gsfft", S.SADI_PREC_FP32)]
+    if N <= 4096:
+        forms.append(("fp32_dense", S.SADI_PREC_FP32_DENSE))
+    res = {}
+    for name, prec in forms:
+        ctxs = make(prec)
+        ms, _ = timed(ctxs, a.steps, a.warmup)
+        res[name] = {"ctxs": ctxs, "ms": ms, "prec": prec}
     clocks = sampler.stop()
-    # accuracy of the chosen form against the plain FP64 path after the same
-    # number of steps from the same data
+    # accuracy of each form against the plain FP64 path after the same number
+    # of steps from the same data
     extra = a.warmup + a.steps - (a.warmup + K64)
     if has64 and extra > 0:
         S.sadi_batch_step(c64, extra)
-    rels = []
-    nsteps_cmp = None
-    for s64, s32 in zip(c64, c32):
-        u64, n64 = s64.get()
-        u32, n32 = s32.get()
-        assert n64 == n32
-        rels.append(float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)))
-        nsteps_cmp = n32
+    ref64 = [s.get() for s in c64]
+    for name, r in res.items():
+        rels = []
+        for (u64, n64), s in zip(ref64, r["ctxs"]):
+            u, n = s.get()
+            assert n64 == n
+            rels.append(float(np.linalg.norm(u - u64) / np.linalg.norm(u64)))
+        r["rel_steps"] = (max(rels) if rels else None, a.warmup + a.steps)
+    # accuracy at the workload's full step count: every form from phi1
+    if a.acc_steps > 0 and has64:
+        allc = c64 + [s for r in res.values() for s in r["ctxs"]]
+        for s in allc:
+            s.set_initial(phi1, _phi2(phi1))
+        S.sadi_batch_step(allc, a.acc_steps)
+        ref = [s.get()[0] for s in c64]
+        for name, r in res.items():
+            per = [float(np.linalg.norm(s.get()[0] - u64) / np.linalg.norm(u64)) for s, u64 in zip(r["ctxs"], ref)]
+            r["rel_full"] = {"steps": a.acc_steps, "per_alpha": dict(zip([str(x) for x in ALPHAS], per)),
+                             "max": max(per)}
+    # the chosen form: the fastest one within the stated accuracy (1e-5
+    # relative L2 against the plain FP64 path)
+    TOL = 1e-5
+
+    def acc_of(r):
+        return r["rel_full"]["max"] if "rel_full" in r else r["rel_steps"][0]
+    ok = [n for n, r in res.items() if acc_of(r) is None or acc_of(r) <= TOL]
+    chosen = min(ok or list(res), key=lambda n: res[n]["ms"])
+    cc = res[chosen]["ctxs"]
+    dense = res[chosen]["prec"] == S.SADI_PREC_FP32_DENSE
     # per-kernel timing (separate profiled pass) for the roofline
+    for s in cc:
+        s.set_initial(phi1, _phi2(phi1))
     Kp = max(5, min(a.steps, 20))
-    _, (phase_ms, _) = timed(c32, Kp, 0, profile=True)
-    names = ["k_rows_r2c", "k_cols_conv", "k_rows_solve", "k_cols_solve"]
-    Np = c32[0].sadi_get_info()[0]
-    alg = {k: (b * len(ALPHAS), f * len(ALPHAS)) for k, (b, f) in algorithmic(N, Np, 4).items()}
-    dom = max(range(4), key=lambda k: phase_ms[k])
-    dname = names[dom]
-    dur_s = phase_ms[dom] / 1e3
+    _, (phase_ms, _) = timed(cc, Kp, 3, profile=True)
+    Np = cc[0].sadi_get_info()[0]
+    reg = Np <= 1024
+    pre = "kr_" if reg else "k_"
+    if dense:
+        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve<dense>+k_tc_gemm(x)", "k_tc_gemm(y)"]
+    else:
+        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve", pre + "cols_solve"]
+    alg = algorithmic(N, Np, 4, dense)
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except Exception:
         pass
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak_tflops = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
     hbm_peak = float(peaks.get("hbm_gbs", 6750.0))
-    b_alg, f_alg = alg[dname]
-    ach_tf = f_alg / dur_s / 1e12
-    ach_gbs = b_alg / dur_s / 1e9
-    roofline = {"kernel": dname, "bound": "alu", "achieved": ach_tf, "peak": fp32_peak_tflops,
-                "unit": "TFLOP/s", "frac": ach_tf / fp32_peak_tflops, "traffic": None,
-                "avg_launch_us": phase_ms[dom] * 1e3,
-                "peak_note": f"FP32 FMA peak of measured-max clock: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz",
-                "hbm_view": {"achieved_gbs": ach_gbs, "peak_gbs": hbm_peak, "frac": ach_gbs / hbm_peak},
-                "kernel_us": {n: phase_ms[k] * 1e3 for k, n in enumerate(names)},
-                "kernel_share": {n: phase_ms[k] / sum(phase_ms) for k, n in enumerate(names)}}
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1711.7))
+    ninst = len(ALPHAS)
+    per_kernel = {}
+    for k, nm in enumerate(names):
+        b_alg, f_alg, bound = alg[k]
+        dur = phase_ms[k] / 1e3
+        peak = bf16_peak if bound == "tensor" else fp32_peak
+        ach = f_alg * ninst / dur / 1e12
+        per_kernel[nm] = {"us": phase_ms[k] * 1e3, "share": phase_ms[k] / sum(phase_ms), "bound": bound,
+                          "achieved_tflops": ach, "frac": None if bound == "mixed" else ach / peak,
+                          "hbm_gbs": b_alg * ninst / dur / 1e9}
+    dom = max((k for k in range(4) if alg[k][2] != "mixed"), key=lambda k: phase_ms[k])
+    dname = names[dom]
+    dk = per_kernel[dname]
+    roofline = {"kernel": dname, "bound": "tensor" if dk["bound"] == "tensor" else "alu",
+                "achieved": dk["achieved_tflops"],
+                "peak": bf16_peak if dk["bound"] == "tensor" else fp32_peak, "unit": "TFLOP/s",
+                "frac": dk["frac"], "traffic": None, "avg_launch_us": dk["us"],
+                "peak_note": ("bf16 dense sustained of measured (MEASURED_PEAKS.json), split-BF16 counted "
+                              "as three BF16 products" if dk["bound"] == "tensor" else
+                              f"FP32 FMA peak at the measured max clock: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz"),
+                "hbm_view": {"achieved_gbs": dk["hbm_gbs"], "peak_gbs": hbm_peak, "frac": dk["hbm_gbs"] / hbm_peak},
+                "kernels": per_kernel}
     # e2e through the public API with host buffers: set_initial from pinned
-    # host arrays, then every step sadi_step(1) + sadi_get into pinned host.
+    # host arrays, then every step sadi_batch_step(1) + sadi_get into pinned host.
     pin_in = torch.from_numpy(phi1).pin_memory()
     p2h = _phi2(phi1)
     pin_in2 = None if p2h is None else torch.from_numpy(np.ascontiguousarray(p2h)).pin_memory()
@@ -384,30 +437,20 @@ def main():
     nll = ctypes.c_longlong()
     barrier()
     t0 = time.perf_counter()
-    for s in c32:
+    for s in cc:
         st = lib.sadi_set_initial(s.ctx, ctypes.c_void_p(pin_in.data_ptr()),
                                   None if pin_in2 is None else ctypes.c_void_p(pin_in2.data_ptr()))
         assert st == 0, s.sadi_last_error()
-    arr = (ctypes.c_void_p * len(c32))(*[s.ctx for s in c32])
+    arr = (ctypes.c_void_p * len(cc))(*[s.ctx for s in cc])
     for k in range(Ke):
-        assert lib.sadi_batch_step(arr, len(c32), 1) == 0
-        for i, s in enumerate(c32):
+        assert lib.sadi_batch_step(arr, len(cc), 1) == 0
+        for i, s in enumerate(cc):
             assert lib.sadi_get(s.ctx, ctypes.c_void_p(pin_out[i].data_ptr()), ctypes.byref(nll)) == 0
     dt_e2e = time.perf_counter() - t0
     barrier()
     h2d = len(ALPHAS) * N * N * 8 * (1 if pin_in2 is None else 2) / Ke
     d2h = len(ALPHAS) * N * N * 8
-    # accuracy at the workload's full step count: both forms from phi1
-    rel_full = None
-    if a.acc_steps > 0 and has64:
-        for s in c64 + c32:
-            s.set_initial(phi1, _phi2(phi1))
-        S.sadi_batch_step(c64 + c32, a.acc_steps)
-        rel_full = []
-        for s64, s32 in zip(c64, c32):
-            u64, _ = s64.get()
-            u32, _ = s32.get()
-            rel_full.append(float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64)))
+
     # aggregate over ranks (max time)
     def reduce_max(vals):
         tt = torch.tensor(vals, dtype=torch.float64, device=dev)
@@ -415,53 +458,58 @@ def main():
             torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
         return [float(x) for x in tt.tolist()]
     pts = N * N * len(ALPHAS)
-    agg = aggregate([ms32, ms64 if has64 else 1.0, dt_e2e], ws, pts, (a.steps, K64, Ke), reduce_max)
-    ms32m, ms64m = agg["ms32"], agg["ms64"]
+    others = [n for n in res if n != chosen]
+    agg = aggregate([res[chosen]["ms"], ms64 if has64 else 1.0, dt_e2e], ws, pts, (a.steps, K64, Ke), reduce_max)
+    agg_o = {n: aggregate([res[n]["ms"], 1.0, 1.0], ws, pts, (a.steps, 1, 1), reduce_max) for n in others}
     value, value64, e2e_val = agg["value"], agg["value64"], agg["e2e"]
     if rank == 0:
         cpu = None
         rel_oracle = None
-        rel_oracle32 = None
         if ws == 1 and not a.no_cpu_baseline and a.workload == "n1023":
             cpu, (u0, u1, uK) = cpu_baseline(N, phi1, alpha=ALPHAS[len(ALPHAS) // 2])
-            # FP64 GPU path vs the oracle after the same 1 + 3 steps (alpha=1.5)
-            with S.Sadi(N, ALPHAS[len(ALPHAS) // 2], KAPPA, TAU, (-1.0, 1.0)) as s:
-                s.set_options(GKIND, S.SADI_PREC_FP64)
-                s.set_initial(phi1, _phi2(phi1))
-                s.step(4)
-                ug, _ = s.get()
-                rel_oracle = float(np.linalg.norm(ug - uK) / np.linalg.norm(uK))
-            with S.Sadi(N, ALPHAS[len(ALPHAS) // 2], KAPPA, TAU, (-1.0, 1.0)) as s:
-                s.set_options(GKIND, S.SADI_PREC_FP32)
-                s.set_initial(phi1, _phi2(phi1))
-                s.step(4)
-                ug32, _ = s.get()
-                rel_oracle32 = float(np.linalg.norm(ug32 - uK) / np.linalg.norm(uK))
+            # each GPU form vs the oracle after the same 1 + 3 steps (middle alpha)
+            rel_oracle = {"alpha": ALPHAS[len(ALPHAS) // 2]}
+            for nm, prec in [("fp64", S.SADI_PREC_FP64)] + forms:
+                with S.Sadi(N, ALPHAS[len(ALPHAS) // 2], KAPPA, TAU, (-1.0, 1.0)) as s:
+                    s.set_options(GKIND, prec)
+                    s.set_initial(phi1, _phi2(phi1))
+                    s.step(4)
+                    ug, _ = s.get()
+                    rel_oracle[nm] = float(np.linalg.norm(ug - uK) / np.linalg.norm(uK))
+        form_desc = {"fp32_gsfft": "FP32 FFTs and Gohberg-Semencul FFT sweeps, double-float state, FP64 setup",
+                     "fp32_dense": "FP32 FFTs for L_h; both sweeps as split-BF16 dense-inverse tcgen05 GEMMs "
+                                   "(FP32 accumulate); double-float state; FP64 setup"}
+        forms_out = {}
+        for n, r in res.items():
+            v = value if n == chosen else agg_o[n]["value"]
+            forms_out[n] = {"value": v, "unit": UNIT, "ms_per_step": r["ms"] / a.steps,
+                            "rel_l2_vs_fp64": {"steps": r["rel_steps"][1], "max": r["rel_steps"][0]},
+                            "rel_l2_vs_fp64_full": r.get("rel_full"), "form": form_desc[n]}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
-            "warmup": a.warmup, "ms_per_step": ms32m / a.steps, "higher_is_better": True,
+            "warmup": a.warmup, "ms_per_step": agg["ms32"] / a.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": _config(N, {"form": "FP32 FFT/sweeps, FP64 setup", "parallelism": f"replicas x{ws}",
+            "config": _config(N, {"form": form_desc[chosen], "chosen_form": chosen,
+                                  "selection": f"fastest form within {TOL:g} relative L2 of the plain FP64 path "
+                                               f"after the accuracy run",
+                                  "parallelism": f"replicas x{ws}",
                                   "l2": "flushed between timed steps (256 MiB write outside the step events)"}),
-            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": ms64m / K64, "steps": K64}
+            "fp64_plain": {"value": value64, "unit": UNIT, "ms_per_step": agg["ms64"] / K64, "steps": K64}
             if has64 else None,
             "speedup_vs_fp64": value / value64 if has64 else None,
-            "rel_l2_fp32_vs_fp64": max(rels) if rels else None, "rel_l2_steps": nsteps_cmp,
-            "rel_l2_fp32_vs_fp64_full": None if rel_full is None else
-            {"steps": a.acc_steps, "per_alpha": dict(zip([str(x) for x in ALPHAS], rel_full)),
-             "max": max(rel_full)},
-            "rel_l2_vs_oracle_4steps": None if rel_oracle is None else
-            {"fp64": rel_oracle, "fp32": rel_oracle32, "alpha": ALPHAS[len(ALPHAS) // 2]},
-            "roofline": roofline, "batched": "one launch per kernel covers the three instances (sadi_batch_step)",
+            "forms": forms_out,
+            "rel_l2_vs_oracle_4steps": rel_oracle,
+            "roofline": roofline,
+            "batched": "one launch per kernel covers all instances (sadi_batch_step)",
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "how": "C ABI with pinned host buffers: sadi_set_initial once, then per step "
                            "sadi_batch_step(1) + sadi_get of u^{n+1} for each instance; wall clock"},
-            "gpu_launches": 4 * a.steps,
+            "gpu_launches": (5 if dense else 4) * a.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)
-    for s in c64 + c32:
+    for s in c64 + [s for r in res.values() for s in r["ctxs"]]:
         s.close()
     if ws > 1:
         torch.distributed.destroy_process_group()

@@ -54,7 +54,11 @@ typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2 } sadi_g
  * dense inverse) is always FP64.
  * SADI_PREC_FP64: FFTs, sweeps and state in double.
  * SADI_PREC_FP32: FFTs and Gohberg-Semencul sweeps in float; the state kept
- *   as a double-float pair with a compensated leapfrog (float storage).
+ *   as a double-float pair with a compensated leapfrog (float storage), and
+ *   the remainder -kappa tau^2 L_h u^n carried as a double-float pair that
+ *   each step advances by the FFT convolution of the increment u^n - u^{n-1}
+ *   (started from an FP64 evaluation of L_h phi1 when N' <= 4096; FP32 above).
+ *   FFT rounding then scales with the increment instead of u^n.
  * SADI_PREC_FP32_DENSE: as FP32, but both sweeps apply the precomputed dense
  *   inverse H^-1 = I + E to all rows / columns at once: W = B + B E and
  *   uhat = W + E W, each product a split-BF16 GEMM on the tensor cores

@@ -9,16 +9,18 @@
 // tiles.  Per-element representation error of a pair is <= 2^-16 relative, so
 // ACC carries about 2^-16 relative error on top of FP32 accumulation.
 //
-// One CTA computes one 128 x 256 output tile with 4 warps:
+// One CTA computes one 128 x 256 output tile with 8 warps:
 //   * thread 0 streams 64-wide K blocks of A_hi, A_lo (128 rows) and B_hi,
 //     B_lo (256 rows) with TMA (cp.async.bulk.tensor, 128-byte swizzle) into
 //     a 2-stage ring guarded by mbarriers;
 //   * thread 32 issues tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator
 //     of 128 lanes x 256 columns in tensor memory) and returns each stage to
 //     the producer with tcgen05.commit;
-//   * all 4 warps read their 32 accumulator lanes back (tcgen05.ld 32x32b)
-//     and run the epilogue of the launch (plain store, or the two fused sweep
-//     epilogues of the dense S-ADI step).
+//   * all 8 warps read the accumulator back (tcgen05.ld 32x32b; warp w takes
+//     lanes 32 (w % 4) .. +31 and column half w / 4), transpose 32 x 32
+//     blocks through shared memory and run the epilogue of the launch (plain
+//     store, or the two fused sweep epilogues of the dense S-ADI step) with
+//     coalesced global accesses.
 // A batch of independent problems of equal padded size runs as blockIdx.z.
 // Every mbarrier wait is bounded (about 1 s of %globaltimer); on expiry the
 // CTA sets *err, waits (bounded) for the copies it issued, frees its tensor
@@ -129,55 +131,95 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t* r) {
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
-// Epilogue of one accumulator row segment: row `row`, columns col0 .. col0+31.
-__device__ __forceinline__ void epilogue(const TcEpi& e, int row, int col0, const uint32_t* r) {
-  if (row >= e.m_valid) return;
-  const int ncol = min(32, e.n_valid - col0);
-  if (ncol <= 0) return;
+// Epilogue of one 32 x 32 accumulator block: rows rowbase .. rowbase+31 (one
+// per lane in r[], as tcgen05.ld delivers them), columns col0 .. col0+31.
+// The block is transposed through the warp's padded shared tile so that every
+// global access of the row-major arrays is a coalesced 128-byte row segment;
+// loads of 8 rows are issued before any store (memory-level parallelism).
+constexpr int EPI_LD = 33;
+__device__ __forceinline__ void epilogue_block(const TcEpi& e, int rowbase, int col0, const uint32_t* r, float* tile,
+                                               int lane) {
+#pragma unroll
+  for (int j = 0; j < 32; ++j) tile[lane * EPI_LD + j] = __uint_as_float(r[j]);
+  __syncwarp();
+  const int col = col0 + lane;
+  const bool cok = col < e.n_valid;
   if (e.mode == kTcStore) {
-    float* dst = e.C + (size_t)row * e.ldc + col0;
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-      if (j < ncol) dst[j] = __uint_as_float(r[j]);
+#pragma unroll 4
+    for (int rr = 0; rr < 32; ++rr) {
+      const int row = rowbase + rr;
+      if (row < e.m_valid && cok) e.C[(size_t)row * e.ldc + col] = tile[rr * EPI_LD + lane];
+    }
   } else if (e.mode == kTcSweepX) {
-    // W = B + B E (in place over B), and the transposed BF16 split of W
-    float* w = e.C + (size_t)row * e.ldc + col0;
+    // W = B + B E (in place over B)
+#pragma unroll 1
+    for (int g = 0; g < 32; g += 8) {
+      float wv[8];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j >= ncol) break;
-      const float v = w[j] + __uint_as_float(r[j]);
-      w[j] = v;
-      unsigned short hi, lo;
-      split_bf16(v, &hi, &lo);
-      const size_t t = (size_t)(col0 + j) * e.ldt + row;
-      e.t_hi[t] = hi;
-      e.t_lo[t] = lo;
+      for (int q = 0; q < 8; ++q) {
+        const int row = rowbase + g + q;
+        wv[q] = (row < e.m_valid && cok) ? e.C[(size_t)row * e.ldc + col] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int row = rowbase + g + q;
+        const float w = wv[q] + tile[(g + q) * EPI_LD + lane];
+        tile[(g + q) * EPI_LD + lane] = w;
+        if (row < e.m_valid && cok) e.C[(size_t)row * e.ldc + col] = w;
+      }
+    }
+    __syncwarp();
+    // the transposed BF16 split of W (the y-sweep GEMM's B operand): lane = row
+    const int row = rowbase + lane;
+    if (row < e.m_valid) {
+#pragma unroll 4
+      for (int j = 0; j < 32; ++j) {
+        if (col0 + j < e.n_valid) {
+          const size_t t = (size_t)(col0 + j) * e.ldt + row;
+          split_bf16(tile[lane * EPI_LD + j], e.t_hi + t, e.t_lo + t);
+        }
+      }
     }
   } else {
     // uhat = W + E W; compensated leapfrog d^{n+1} = d^n + uhat (d^1 = uhat),
     // u^{n+1} = u^n + d^{n+1} with u = u_hi + u_lo (two-sum), in place
-    const float* w = e.C + (size_t)row * e.ldc + col0;
-    const size_t base = (size_t)row * e.ldu + col0;
+#pragma unroll 1
+    for (int g = 0; g < 32; g += 8) {
+      float wv[8], dv[8], hv[8], lv[8];
 #pragma unroll
-    for (int j = 0; j < 32; ++j) {
-      if (j >= ncol) break;
-      const float uh = w[j] + __uint_as_float(r[j]);
-      const size_t idx = base + j;
-      const float d = e.first ? uh : e.u_d[idx] + uh;
-      const float hi = e.u_hi[idx], lo = e.u_lo[idx];
-      const float s = hi + d;
-      const float bb = s - hi;
-      const float err = (hi - (s - bb)) + (d - bb);
-      const float l2 = lo + err;
-      const float h2 = s + l2;
-      e.u_hi[idx] = h2;
-      e.u_lo[idx] = l2 - (h2 - s);
-      e.u_d[idx] = d;
+      for (int q = 0; q < 8; ++q) {
+        const int row = rowbase + g + q;
+        const bool ok = row < e.m_valid && cok;
+        const size_t idx = (size_t)row * e.ldu + col;
+        wv[q] = ok ? e.C[(size_t)row * e.ldc + col] : 0.f;
+        dv[q] = (ok && !e.first) ? e.u_d[idx] : 0.f;
+        hv[q] = ok ? e.u_hi[idx] : 0.f;
+        lv[q] = ok ? e.u_lo[idx] : 0.f;
+      }
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const int row = rowbase + g + q;
+        if (row < e.m_valid && cok) {
+          const float uh = wv[q] + tile[(g + q) * EPI_LD + lane];
+          const float d = dv[q] + uh;
+          const float hi = hv[q], lo = lv[q];
+          const float s = hi + d;
+          const float bb = s - hi;
+          const float err = (hi - (s - bb)) + (d - bb);
+          const float l2 = lo + err;
+          const float h2 = s + l2;
+          const size_t idx = (size_t)row * e.ldu + col;
+          e.u_hi[idx] = h2;
+          e.u_lo[idx] = l2 - (h2 - s);
+          e.u_d[idx] = d;
+        }
+      }
     }
   }
+  __syncwarp();
 }
 
-__global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int* err) {
+__global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   const TcInst& in = bt.in[blockIdx.z];
   if ((int)blockIdx.x >= in.tiles_n || (int)blockIdx.y >= in.tiles_m) return;   // beyond this problem
@@ -262,16 +304,20 @@ __global__ void __launch_bounds__(128, 1) k_tc_gemm(const __grid_constant__ TcBa
     mma_commit(tfull);
   }
   __syncwarp();
-  // ---- epilogue: tensor memory -> registers -> global ----
+  // ---- epilogue: tensor memory -> registers -> shared -> global ----
+  // warp w reads accumulator lanes 32 (w % 4) .. +31 (its tcgen05.ld lane
+  // quarter) and the column half w / 4; the pipeline buffers are free now
   const bool done = mbar_wait(tfull, 0);
   tc_fence_after();
   if (done && !*abort_flag) {
-    const int row = m0 + warp * 32 + lane;
+    float* tile = reinterpret_cast<float*>(base) + warp * 32 * EPI_LD;
+    const int quarter = warp & 3, half = warp >> 2;
 #pragma unroll 1
-    for (int c = 0; c < BN / 32; ++c) {
+    for (int c = 0; c < BN / 64; ++c) {
+      const int cc = half * (BN / 64) + c;
       uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32), r);
-      epilogue(in.e, row, n0 + c * 32, r);
+      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), r);
+      epilogue_block(in.e, m0 + quarter * 32, n0 + cc * 32, r, tile, lane);
     }
   } else if (lane == 0) {
     atomicExch(in.e.err ? in.e.err : err, 1);
@@ -357,7 +403,7 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
     attr = true;
   }
   const dim3 grid(tn, tm, b.count);
-  k_tc_gemm<<<grid, 128, SMEM_BYTES, st>>>(b, err);
+  k_tc_gemm<<<grid, 256, SMEM_BYTES, st>>>(b, err);
   return cudaGetLastError();
 }
 

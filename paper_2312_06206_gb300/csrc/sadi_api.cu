@@ -54,6 +54,10 @@ struct sadi_ctx {
   // (double-float state, updated in place; cur stays 0).
   void* ubuf[2] = {nullptr, nullptr};
   float* ulo = nullptr;
+  // FP32 forms: the remainder C = -kappa tau^2 L_h u^n as a double-float pair,
+  // advanced each step by the convolution of the increment d^n
+  float* Chi = nullptr;
+  float* Clo = nullptr;
   void* phi2 = nullptr;
   void* S = nullptr;         // N x Np complex
   void* W = nullptr;         // N x N
@@ -118,7 +122,7 @@ void free_all(sadi_ctx* c) {
                   c->ubuf[0], c->ubuf[1], c->ulo, c->F, c->phi2, c->S,      c->W,      c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr};
+  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->Chi, c->Clo};
   for (void* p : dense)
     if (p) cudaFree(p);
   for (auto& a : c->ev_pool)
@@ -166,15 +170,21 @@ sadi_status alloc_state(sadi_ctx* c) {
     c->ubuf[k] = nullptr;
     CK(cudaMalloc(&c->ubuf[k], nn * es), "cudaMalloc(state)");
   }
-  if (c->ulo) cudaFree(c->ulo);
-  c->ulo = nullptr;
-  if (c->prec != SADI_PREC_FP64) CK(cudaMalloc(&c->ulo, nn * sizeof(float)), "cudaMalloc(state lo)");
+  float** fbufs[] = {&c->ulo, &c->Chi, &c->Clo};
+  for (auto b : fbufs) {
+    if (*b) cudaFree(*b);
+    *b = nullptr;
+    if (c->prec != SADI_PREC_FP64) CK(cudaMalloc(b, nn * sizeof(float)), "cudaMalloc(state)");
+  }
   if (c->phi2) cudaFree(c->phi2);
   if (c->S) cudaFree(c->S);
   if (c->W) cudaFree(c->W);
   c->phi2 = c->S = c->W = nullptr;
   CK(cudaMalloc(&c->phi2, nn * es), "cudaMalloc(phi2)");
-  CK(cudaMalloc(&c->S, (size_t)c->g.N * c->g.Np * 2 * es), "cudaMalloc(spectrum)");
+  // the FP32 forms start their incremental remainder from an FP64 evaluation
+  // (N' <= 4096), which needs the spectrum scratch at double size
+  const size_t ses = (c->prec != SADI_PREC_FP64 && c->g.Np <= 4096) ? sizeof(double) : es;
+  CK(cudaMalloc(&c->S, (size_t)c->g.N * c->g.Np * 2 * ses), "cudaMalloc(spectrum)");
   CK(cudaMalloc(&c->W, nn * es), "cudaMalloc(sweep)");
   (void)e;
   return SADI_OK;
@@ -391,6 +401,18 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   } else {
     CK(launch_split_d2ff(c->stage, static_cast<float*>(c->ubuf[0]), c->ulo, nn, st), "phi1 split");
     CK(cudaMemsetAsync(c->ubuf[1], 0, nn * sizeof(float), st), "increment zero");
+    // starting remainder C^0 = -kappa tau^2 L_h phi1: FP64 where the FP64
+    // engine applies (N' <= 4096), else FP32 from the hi part
+    if (c->g.Np <= 4096) {
+      StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
+      CK(launch_remainder<double>(c->g, tb, default_tiles<double>(c->g.Np), c->stage, c->S, c->Chi, c->Clo, st),
+         "starting remainder");
+    } else {
+      StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+      CK(launch_remainder<float>(c->g, tb, default_tiles<float>(c->g.Np), static_cast<const float*>(c->ubuf[0]),
+                                 c->S, c->Chi, c->Clo, st),
+         "starting remainder");
+    }
   }
   if (phi2) {
     CK(cudaMemcpyAsync(c->stage, phi2, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy phi2");
@@ -449,6 +471,8 @@ RegInst reg_inst(const sadi_ctx* c) {
   r.first = c->n == 0 ? 1 : 0;
   r.F = static_cast<const float*>(c->F);
   r.fsc = c->F ? (float)std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.f;
+  r.C_hi = c->Chi;
+  r.C_lo = c->Clo;
   r.Bh = c->Bh;
   r.Bl = c->Bl;
   r.ldp = c->npad;
@@ -475,7 +499,8 @@ sadi_status step_smem(sadi_ctx* c, cudaEvent_t* ev, cudaStream_t st) {
     StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
     float* hi = static_cast<float*>(c->ubuf[0]);
     e = launch_step<float>(c->g, tb, c->tiles32, rp, hi, static_cast<float*>(c->ubuf[1]), hi, c->ulo,
-                           static_cast<const float*>(c->phi2), c->S, static_cast<float*>(c->W), st, ev);
+                           static_cast<const float*>(c->phi2), c->S, static_cast<float*>(c->W), st, ev, c->Chi,
+                           c->Clo);
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "step launch");
   if (c->prec == SADI_PREC_FP64) c->cur = 1 - c->cur;
@@ -530,8 +555,8 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
                  c->F ? std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.0};
     StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
     e = launch_dense_rows(c->g, tb, c->tiles32, rp, static_cast<const float*>(c->ubuf[0]),
-                          static_cast<const float*>(c->phi2), c->S, static_cast<float*>(c->W), c->Bh, c->Bl, c->npad,
-                          st_, ev);
+                          static_cast<const float*>(c->ubuf[1]), static_cast<const float*>(c->phi2), c->S,
+                          static_cast<float*>(c->W), c->Chi, c->Clo, c->Bh, c->Bl, c->npad, st_, ev);
   }
   // x sweeps of all members, then y sweeps (each in launches of <= kTcMaxBatch)
   static thread_local TcBatch tb;

@@ -96,6 +96,8 @@ struct RegInst {
   float2* S;            // N x N' spectrum scratch
   float* W;             // N x N sweep scratch
   const float* F;       // optional source field (N x N) or nullptr
+  float* C_hi;          // incremental remainder -kappa tau^2 L_h u^n (double-float)
+  float* C_lo;
   unsigned short* Bh;   // dense-inverse form: BF16 split of B^n (ld ldp, zero-padded)
   unsigned short* Bl;
   int ldp;
@@ -128,17 +130,27 @@ cudaError_t run_reg_tables(const Geom& g, const double* lnat, double scale, cons
 // of the four kernels.  u_lo == nullptr: plain leapfrog u_next = 2u_cur - u_prev
 // + uhat (u_next may alias u_prev).  u_lo != nullptr: compensated form, u_cur ==
 // u_next = hi part, u_lo = lo part, u_prev = increment d, all in place.
+// Ch, Cl (FP32 compensated form only, else nullptr): the incremental
+// remainder C = -kappa tau^2 L_h u^n as a double-float pair, advanced in place
+// by the convolution of the increment d = u_prev (the row FFT then reads d).
 template <typename T>
 cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
                         T* u_prev, T* u_next, T* u_lo, const T* phi2, void* S, T* W, cudaStream_t st,
-                        cudaEvent_t* ev = nullptr);
+                        cudaEvent_t* ev = nullptr, float* Ch = nullptr, float* Cl = nullptr);
+// C = -kappa tau^2 L_h u (N x N) into the double-float pair (Ch, Cl): the
+// starting value of the incremental remainder (T = double gives it to FP64
+// accuracy; needs the FP64 engine, N' <= 4096).
+template <typename T>
+cudaError_t launch_remainder(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const T* u, void* S, float* Ch,
+                             float* Cl, cudaStream_t st);
 
-// Dense-inverse form on the shared-memory engine (FP32): row FFT, column
-// convolution and B^n (events 0..2); B^n goes to W (N x N) and its BF16 split
-// to Bh / Bl (ld ldp).
+// Dense-inverse form on the shared-memory engine (FP32): row FFT of the
+// increment d, column convolution, incremental remainder and B^n (events
+// 0..2); B^n goes to W (N x N) and its BF16 split to Bh / Bl (ld ldp).
 cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const Tiles& tl, const RhsParams& rp,
-                              const float* u_cur, const float* phi2, void* S, float* W, unsigned short* Bh,
-                              unsigned short* Bl, int ldp, cudaStream_t st, cudaEvent_t* ev);
+                              const float* u_cur, const float* d, const float* phi2, void* S, float* W, float* Ch,
+                              float* Cl, unsigned short* Bh, unsigned short* Bl, int ldp, cudaStream_t st,
+                              cudaEvent_t* ev);
 // H^-1 - I of the N x N Toeplitz matrix H = I + s T(a_0 .. a_{N-1}) as a
 // zero-padded npad x npad BF16 pair (Eh, El), from the generator c = H^-1 e_1
 // (Durbin recursion) and the Gohberg-Semencul diagonal recurrence, in FP64.

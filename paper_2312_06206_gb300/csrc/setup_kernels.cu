@@ -210,9 +210,10 @@ __global__ void k_lambda_arrange(const double* __restrict__ lnat, Geom g, double
   int k2 = 2 * brev(p, logNp) + h;
   if (k2 > Np) k2 = P - k2;
   double val;
+  // slot 0 carries the k1 = 0 symbol, the extra slot Np the k1 = Np symbol
   if (slot >= 1 && slot < Np) val = lnat[(size_t)brev(slot, logNp) * (Np + 1) + k2];
-  else if (slot == 0) val = 0.5 * (lnat[k2] + lnat[(size_t)Np * (Np + 1) + k2]);
-  else val = 0.5 * (lnat[k2] - lnat[(size_t)Np * (Np + 1) + k2]);
+  else if (slot == 0) val = lnat[k2];
+  else val = lnat[(size_t)Np * (Np + 1) + k2];
   val *= scale;
   lpb64[idx] = val;
   lpb32[idx] = (float)val;

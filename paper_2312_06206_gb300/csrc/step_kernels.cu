@@ -61,6 +61,23 @@ __device__ __forceinline__ T real_view(const cx<T>* v, int k) {
   return f[k & 1];
 }
 
+// Incremental remainder of the FP32 forms: C = -kappa tau^2 L_h u^n is kept
+// as a double-float pair (Ch + Cl) and advanced by the convolution of the
+// increment d^n = u^n - u^{n-1} (two-sum); returns the new Ch.
+template <typename T>
+__device__ __forceinline__ T acc_remainder(float* Ch, float* Cl, size_t idx, T conv) {
+  const float hi = Ch[idx], lo = Cl[idx];
+  const float x = (float)conv;
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  const float l2 = lo + err;
+  const float h2 = s + l2;
+  Ch[idx] = h2;
+  Cl[idx] = l2 - (h2 - s);
+  return T(h2);
+}
+
 // ---------------------------------------------------------------------------
 // Gohberg-Semencul core, Algorithm 1 on the bordered matrix H':
 // input  buf[v] = Q v1 with v1 = (v' + i J v') (natural order),
@@ -168,9 +185,9 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
 // along y with the symbol: FFT of length P (N nonzero inputs) split into its
 // even and odd frequency halves (two FFTs of length Np), multiply by the
 // symbol, inverse, keep rows j < N.  Slot 0 holds two real columns (k1 = 0
-// and k1 = Np) packed as re + i im; their different symbols are applied with
-// the partner formula (L0 + LN)/2 Y[k] + (L0 - LN)/2 conj(Y[-k]).
-// In place on S.
+// and k1 = Np) packed as re + i im: they are separated with the partner
+// bin Y[-k] (Ev = (Y[k] + conj Y[-k]) / 2, Od = (Y[k] - conj Y[-k]) / 2) and
+// each multiplied by its own symbol, L0 Ev + LN Od.  In place on S.
 // ---------------------------------------------------------------------------
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
@@ -206,19 +223,26 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
     }
     if (s0 == 0) {
       // slot 0: pairs (p, partner) in each half, handled by one thread each.
+      const T half = T(0.5);
       for (int t = threadIdx.x; t < 2 * Np; t += blockDim.x) {
         const int h = t >> logNp, p = t & (Np - 1);
         const int pp = (h == 0) ? brev((Np - brev(p, logNp)) & (Np - 1), logNp) : (Np - 1 - p);
         if (pp < p) continue;
         cx<T>* e = buf + h * vs;
         const cx<T> Y = e[padi(p)], Yp = e[padi(pp)];
-        const T A = __ldg(&lpb[(size_t)h * Np + p]);
-        const T B = __ldg(&lpb[((size_t)Np * 2 + h) * Np + p]);
-        e[padi(p)] = cadd(cscale(Y, A), cscale(cconj(Yp), B));
+        // unpack the two real columns first: Ev = spectrum of the k1 = 0
+        // column, Od = i x spectrum of the k1 = Np column; each then takes its
+        // own symbol (no cancellation between the large k1 = Np symbol and
+        // the small low-frequency k1 = 0 symbol)
+        const cx<T> Ev = cscale(cadd(Y, cconj(Yp)), half);
+        const cx<T> Od = cscale(csub(Y, cconj(Yp)), half);
+        const T L0 = __ldg(&lpb[(size_t)h * Np + p]);
+        const T LN = __ldg(&lpb[((size_t)Np * 2 + h) * Np + p]);
+        e[padi(p)] = cadd(cscale(Ev, L0), cscale(Od, LN));
         if (pp != p) {
-          const T Ap = __ldg(&lpb[(size_t)h * Np + pp]);
-          const T Bp = __ldg(&lpb[((size_t)Np * 2 + h) * Np + pp]);
-          e[padi(pp)] = cadd(cscale(Yp, Ap), cscale(cconj(Y), Bp));
+          const T L0p = __ldg(&lpb[(size_t)h * Np + pp]);
+          const T LNp = __ldg(&lpb[((size_t)Np * 2 + h) * Np + pp]);
+          e[padi(pp)] = csub(cscale(cconj(Ev), L0p), cscale(cconj(Od), LNp));
         }
       }
     }
@@ -233,25 +257,15 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
   }
 }
 
-// ---------------------------------------------------------------------------
-// k_rows_solve: per row j: inverse real FFT of the convolved half spectrum
-// (gives -kappa tau^2 L_h u^n, the scale being folded into the symbol),
-// B^n epilogue with g(u^n) (and phi2 when n = 0), then the x sweep W_j = H^-1 B_j.
-// ---------------------------------------------------------------------------
-// DENSE: the dense-inverse form stops after B^n, which it writes to W and,
-// split into BF16 pairs, to Bh / Bl (ld ldp).
-template <typename T, bool DENSE = false>
-__global__ void __launch_bounds__(kThreads)
-k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ phi2, T* __restrict__ W,
-             Geom g, RhsParams rp, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
-             const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR,
-             unsigned short* Bh = nullptr, unsigned short* Bl = nullptr, int ldp = 0) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
-  const int N = g.N, Np = g.Np, logNp = g.logNp;
-  const int vs = vec_stride(Np);
-  const int row0 = blockIdx.x * NR;
-  const int nrows = min(NR, N - row0);
+// Rows row0 .. row0+nrows-1 of the convolved half spectrum S -> buf (real
+// view: the inverse real FFT of length 2Np, i.e. the convolution values at
+// x indices 0 .. 2Np-1): half spectrum X[k] (slots) -> Z[k] = E + iO, the
+// spectrum of z[n] = x[2n] + i x[2n+1], then an inverse complex FFT.
+template <typename T>
+__device__ __forceinline__ void rows_inverse(cx<T>* buf, const cx<T>* __restrict__ S, const Geom& g, int NR, int row0,
+                                             int nrows, int vs, const cx<T>* __restrict__ stw,
+                                             const cx<T>* __restrict__ tw) {
+  const int Np = g.Np, logNp = g.logNp;
   for (int t = threadIdx.x; t < (NR << logNp); t += blockDim.x) {
     const int v = t >> logNp, s = t & (Np - 1);
     cx<T> val = mkc(T(0), T(0));
@@ -259,8 +273,7 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
     buf[v * vs + padi(s)] = val;
   }
   __syncthreads();
-  // half spectrum X[k] (slots) -> Z[k] = E + iO, the spectrum of
-  // z[n] = x[2n] + i x[2n+1]; each thread owns a partner pair of slots.
+  // each thread owns a partner pair of slots
   const T half = T(0.5);
   for (int t = threadIdx.x; t < (NR << logNp); t += blockDim.x) {
     const int v = t >> logNp, s = t & (Np - 1);
@@ -288,6 +301,55 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
   }
   __syncthreads();
   fft_dit<T>(buf, logNp, NR, vs, stw);
+}
+
+// ---------------------------------------------------------------------------
+// k_rows_remainder: the convolution rows only, C = -kappa tau^2 L_h u (the
+// scale is in the symbol), written as a double-float pair of floats (the
+// starting value of the incremental remainder of the FP32 forms).
+// ---------------------------------------------------------------------------
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
+                 int NR, float* __restrict__ Ch, float* __restrict__ Cl) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int N = g.N;
+  const int vs = vec_stride(g.Np);
+  const int row0 = blockIdx.x * NR;
+  const int nrows = min(NR, N - row0);
+  rows_inverse<T>(buf, S, g, NR, row0, nrows, vs, stw, tw);
+  for (int t = threadIdx.x; t < nrows * N; t += blockDim.x) {
+    const int v = t / N, k = t % N;
+    const T c = real_view<T>(buf + v * vs, k);
+    const float hi = (float)c;
+    const size_t idx = (size_t)(row0 + v) * N + k;
+    Ch[idx] = hi;
+    Cl[idx] = (float)(c - (T)hi);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// k_rows_solve: per row j: inverse real FFT of the convolved half spectrum
+// (gives -kappa tau^2 L_h u^n, the scale being folded into the symbol),
+// B^n epilogue with g(u^n) (and phi2 when n = 0), then the x sweep W_j = H^-1 B_j.
+// ---------------------------------------------------------------------------
+// DENSE: the dense-inverse form stops after B^n, which it writes to W and,
+// split into BF16 pairs, to Bh / Bl (ld ldp).
+template <typename T, bool DENSE = false>
+__global__ void __launch_bounds__(kThreads)
+k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ phi2, T* __restrict__ W,
+             Geom g, RhsParams rp, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
+             const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR,
+             float* Ch, float* Cl, unsigned short* Bh = nullptr, unsigned short* Bl = nullptr, int ldp = 0) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int N = g.N, Np = g.Np;
+  const int vs = vec_stride(Np);
+  const int row0 = blockIdx.x * NR;
+  const int nrows = min(NR, N - row0);
+  rows_inverse<T>(buf, S, g, NR, row0, nrows, vs, stw, tw);
+  const T half = T(0.5);
   // B^n and v1 = Q (v' + i J v'), staged through registers (in place).
   const int halfNp = Np >> 1;
   const int npairs = NR * halfNp;
@@ -303,7 +365,8 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
         const int row = row0 + v;
         const cx<T>* e = buf + v * vs;
         if (k < N) {
-          const T conv = real_view<T>(e, k);
+          T conv = real_view<T>(e, k);
+          if (Ch) conv = acc_remainder<T>(Ch, Cl, (size_t)row * N + k, conv);
           const T uu = u[(size_t)row * N + k];
           T gsrc = g_of<T>(rp.g, uu);
           if (rp.F) gsrc += T(rp.fsc) * static_cast<const T*>(rp.F)[(size_t)row * N + k];
@@ -311,7 +374,8 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
           ra[it] = rp.first ? T(rp.tau) * phi2[(size_t)row * N + k] + half * (conv + gg) : conv + gg;
         }
         if (k2 < N) {
-          const T conv = real_view<T>(e, k2);
+          T conv = real_view<T>(e, k2);
+          if (Ch) conv = acc_remainder<T>(Ch, Cl, (size_t)row * N + k2, conv);
           const T uu = u[(size_t)row * N + k2];
           T gsrc = g_of<T>(rp.g, uu);
           if (rp.F) gsrc += T(rp.fsc) * static_cast<const T*>(rp.F)[(size_t)row * N + k2];
@@ -417,6 +481,7 @@ cudaError_t step_setup_attributes() {
   if ((e = cudaFuncSetAttribute(k_cols_conv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_rows_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_cols_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_remainder<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if constexpr (sizeof(T) == 4) {
     if ((e = cudaFuncSetAttribute(k_rows_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   }
@@ -454,7 +519,7 @@ bool tiles_valid(const Geom& g, const Tiles& t) {
 template <typename T>
 cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
                         T* u_prev, T* u_next, T* u_lo, const T* phi2, void* Sv, T* W, cudaStream_t st,
-                        cudaEvent_t* ev) {
+                        cudaEvent_t* ev, float* Ch, float* Cl) {
   const cx<T>* stw = reinterpret_cast<const cx<T>*>(tb.stw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
   const cx<T>* ls = reinterpret_cast<const cx<T>*>(tb.lam_s);
@@ -465,11 +530,13 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   const int NR = tl.rows, CTc = tl.conv_cols, CTs = tl.solve_cols;
   const int rblocks = (g.N + NR - 1) / NR;
   if (ev) cudaEventRecord(ev[0], st);
-  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, stw, tw, NR);
+  // incremental remainder (Ch != nullptr): transform the increment d = u_prev
+  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(Ch ? u_prev : u_cur, S, g, stw, tw, NR);
   if (ev) cudaEventRecord(ev[1], st);
   k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
   if (ev) cudaEventRecord(ev[2], st);
-  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR);
+  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch,
+                                                          Cl);
   if (ev) cudaEventRecord(ev[3], st);
   k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, u_lo, g, rp.first,
                                                                           stw, tw, ls, lc, tb.G, CTs);
@@ -485,14 +552,35 @@ template bool tiles_valid<float>(const Geom&, const Tiles&);
 template bool tiles_valid<double>(const Geom&, const Tiles&);
 template cudaError_t launch_step<float>(const Geom&, const StepTables<float>&, const Tiles&, const RhsParams&,
                                         const float*, float*, float*, float*, const float*, void*, float*,
-                                        cudaStream_t, cudaEvent_t*);
+                                        cudaStream_t, cudaEvent_t*, float*, float*);
 template cudaError_t launch_step<double>(const Geom&, const StepTables<double>&, const Tiles&, const RhsParams&,
                                          const double*, double*, double*, double*, const double*, void*, double*,
-                                         cudaStream_t, cudaEvent_t*);
+                                         cudaStream_t, cudaEvent_t*, float*, float*);
+
+template <typename T>
+cudaError_t launch_remainder(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const T* u, void* Sv, float* Ch,
+                             float* Cl, cudaStream_t st) {
+  const cx<T>* stw = reinterpret_cast<const cx<T>*>(tb.stw);
+  const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
+  cx<T>* S = reinterpret_cast<cx<T>*>(Sv);
+  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  if (!tiles_valid<T>(g, tl)) return cudaErrorInvalidConfiguration;
+  const int NR = tl.rows, CTc = tl.conv_cols;
+  const int rblocks = (g.N + NR - 1) / NR;
+  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u, S, g, stw, tw, NR);
+  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
+  k_rows_remainder<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, g, stw, tw, NR, Ch, Cl);
+  return cudaGetLastError();
+}
+template cudaError_t launch_remainder<float>(const Geom&, const StepTables<float>&, const Tiles&, const float*, void*,
+                                             float*, float*, cudaStream_t);
+template cudaError_t launch_remainder<double>(const Geom&, const StepTables<double>&, const Tiles&, const double*,
+                                              void*, float*, float*, cudaStream_t);
 
 cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const Tiles& tl, const RhsParams& rp,
-                              const float* u_cur, const float* phi2, void* Sv, float* W, unsigned short* Bh,
-                              unsigned short* Bl, int ldp, cudaStream_t st, cudaEvent_t* ev) {
+                              const float* u_cur, const float* d, const float* phi2, void* Sv, float* W,
+                              float* Ch, float* Cl, unsigned short* Bh, unsigned short* Bl, int ldp, cudaStream_t st,
+                              cudaEvent_t* ev) {
   using T = float;
   const cx<T>* stw = reinterpret_cast<const cx<T>*>(tb.stw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
@@ -504,12 +592,12 @@ cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const 
   const int NR = tl.rows, CTc = tl.conv_cols;
   const int rblocks = (g.N + NR - 1) / NR;
   if (ev) cudaEventRecord(ev[0], st);
-  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, stw, tw, NR);
+  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(d, S, g, stw, tw, NR);
   if (ev) cudaEventRecord(ev[1], st);
   k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
   if (ev) cudaEventRecord(ev[2], st);
   k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR,
-                                                                 Bh, Bl, ldp);
+                                                                 Ch, Cl, Bh, Bl, ldp);
   return cudaGetLastError();
 }
 

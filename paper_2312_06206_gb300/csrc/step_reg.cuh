@@ -1,9 +1,11 @@
 // step_reg.cuh -- the S-ADI step (Sec. 3, eq. "ADI scheme equivalent") for
 // FFT lengths N' <= 1024 with the register-resident two-level FFT of
 // regfft.cuh.  Same four kernels and the same mathematics as step_kernels.cu:
-//   kr_rows_r2c    rows of u^n -> half spectrum along x (natural slots)
+//   kr_rows_r2c    rows of the increment d^n = u^n - u^{n-1} -> half spectrum
+//                  along x (natural slots)
 //   kr_cols_conv   per x frequency: y FFT (even/odd halves) x symbol, inverse
-//   kr_rows_solve  inverse real FFT + B^n epilogue + x sweep (Algorithm 1)
+//   kr_rows_solve  inverse real FFT, remainder C += conv(d^n), B^n epilogue,
+//                  x sweep (Algorithm 1)
 //   kr_cols_solve  y sweep (Algorithm 1) + leapfrog
 // Spectra are in natural order here (slot k holds x-frequency k, slot 0 holds
 // X[0] + i X[N']); all spectral tables are natural-order copies of the FP64
@@ -28,6 +30,21 @@ __device__ __forceinline__ T g_of_r(int kind, T u) {
 }
 
 __host__ __device__ constexpr int pad32(int k) { return k + (k >> 5); }
+
+// Incremental remainder: C = -kappa tau^2 L_h u^n as a double-float pair
+// (Ch + Cl), advanced by the convolution of the increment d^n (two-sum);
+// returns the new Ch.
+__device__ __forceinline__ float acc_rem(float* Ch, float* Cl, size_t idx, float x) {
+  const float hi = Ch[idx], lo = Cl[idx];
+  const float s = hi + x;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (x - bb);
+  const float l2 = lo + err;
+  const float h2 = s + l2;
+  Ch[idx] = h2;
+  Cl[idx] = l2 - (h2 - s);
+  return h2;
+}
 
 // elements of one vector's shared buffer, rounded so that buffers of
 // consecutive vectors start on staggered banks (8-byte elements, 16 per 128 B)
@@ -157,7 +174,9 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ 
   const int row = blockIdx.x * C::VB + v;
   const bool valid = row < N;
   float2* sm = reinterpret_cast<float2*>(smem_raw) + v * C::SMV;
-  const float* ur = I.u_hi + (size_t)(valid ? row : 0) * N;
+  // the increment d^n = u^n - u^{n-1} (zero before the first step): the
+  // remainder is advanced incrementally
+  const float* ur = I.u_d + (size_t)(valid ? row : 0) * N;
   float2 x[F::E];
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
@@ -318,16 +337,18 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
     const float2 cv = sm[pad32(n)];
     float b0 = 0.f, b1 = 0.f;
     if (valid && 2 * n < N) {
+      const float c = acc_rem(I.C_hi, I.C_lo, (size_t)row * N + 2 * n, cv.x);
       float gs = g_of_r<float>(I.gkind, us[2 * n]);
       if (I.F) gs += I.fsc * I.F[(size_t)row * N + 2 * n];
       const float gg = tau2 * gs;
-      b0 = I.first ? tau * ps[2 * n] + 0.5f * (cv.x + gg) : cv.x + gg;
+      b0 = I.first ? tau * ps[2 * n] + 0.5f * (c + gg) : c + gg;
     }
     if (valid && 2 * n + 1 < N) {
+      const float c = acc_rem(I.C_hi, I.C_lo, (size_t)row * N + 2 * n + 1, cv.y);
       float gs = g_of_r<float>(I.gkind, us[2 * n + 1]);
       if (I.F) gs += I.fsc * I.F[(size_t)row * N + 2 * n + 1];
       const float gg = tau2 * gs;
-      b1 = I.first ? tau * ps[2 * n + 1] + 0.5f * (cv.y + gg) : cv.y + gg;
+      b1 = I.first ? tau * ps[2 * n + 1] + 0.5f * (c + gg) : c + gg;
     }
     sm[pad32(n)] = make_float2(b0, b1);
   }

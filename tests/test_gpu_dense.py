@@ -147,3 +147,19 @@ def test_dense_batch_matches_single_contexts(S):
         assert n == 6 and np.array_equal(u, r)
     for s in single + batch:
         s.close()
+
+
+@pytest.mark.parametrize("N", [1023, 2047])
+def test_long_run_fp32_forms_track_fp64(S, N):
+    # 250 steps of the N=4095 precision workload's parameters (alpha 1.7,
+    # kappa 0.5, tau 5e-4, g = -u^3): both FP32 forms stay within 1e-6 of the
+    # FP64 path.  N = 1023 runs the register FFT path, N = 2047 the
+    # shared-memory engine, whose packed k1 = 0 / k1 = N' column must keep
+    # the small low-frequency symbol free of cancellation (before that was
+    # fixed the drift here was about 4e-6).
+    alpha, kappa, tau, g, steps = 1.7, 0.5, 5e-4, 1, 250
+    phi1 = WL.gaussian_bumps(N, 8, WL.SEED_BASE + 3)
+    u64 = _run(S, N, alpha, kappa, tau, g, phi1, None, steps, S.SADI_PREC_FP64)
+    for prec in (S.SADI_PREC_FP32, S.SADI_PREC_FP32_DENSE):
+        u = _run(S, N, alpha, kappa, tau, g, phi1, None, steps, prec)
+        assert O.rel_l2(u, u64) <= 1e-6, (prec, O.rel_l2(u, u64))
