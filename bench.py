@@ -245,6 +245,13 @@ def aggregate(times, world_size, pts_per_step, steps_list, reduce_max=None):
             "ms32": ms32, "ms64": ms64, "e2e_s": e2e}
 
 
+# DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
+# kernel in a workload, from the ncu captures summarised under profiles/
+# (kr_cols_conv_n1023.md, k_tc_gemm_n4095.md); absent = no capture of the
+# current kernel, reported as null.
+NCU_TRAFFIC = {("n1023", "kr_cols_conv"): 50.55e6, ("n4095", "k_tc_gemm(y)"): 792.5e6}
+
+
 def algorithmic(N, Np, es, dense=False):
     """Per-launch algorithmic work of the four timed phases of one instance,
     for the roofline: [(bytes, flops, bound)].  FFT flops are the nominal
@@ -412,14 +419,17 @@ def main():
         ach = f_alg * ninst / dur / 1e12
         per_kernel[nm] = {"us": phase_ms[k] * 1e3, "share": phase_ms[k] / sum(phase_ms), "bound": bound,
                           "achieved_tflops": ach, "frac": None if bound == "mixed" else ach / peak,
-                          "hbm_gbs": b_alg * ninst / dur / 1e9}
+                          "hbm_gbs": b_alg * ninst / dur / 1e9, "alg_bytes": b_alg * ninst,
+                          "alg_flops": f_alg * ninst,
+                          "traffic": NCU_TRAFFIC.get((a.workload if a.N == PRESETS[a.workload]["N"] else None, nm))}
     dom = max((k for k in range(4) if alg[k][2] != "mixed"), key=lambda k: phase_ms[k])
     dname = names[dom]
     dk = per_kernel[dname]
     roofline = {"kernel": dname, "bound": "tensor" if dk["bound"] == "tensor" else "alu",
                 "achieved": dk["achieved_tflops"],
                 "peak": bf16_peak if dk["bound"] == "tensor" else fp32_peak, "unit": "TFLOP/s",
-                "frac": dk["frac"], "traffic": None, "avg_launch_us": dk["us"],
+                "frac": dk["frac"], "traffic": dk["traffic"], "avg_launch_us": dk["us"],
+                "traffic_note": "ncu dram bytes per launch from profiles/ (null if no capture of this kernel)",
                 "peak_note": ("bf16 dense sustained of measured (MEASURED_PEAKS.json), split-BF16 counted "
                               "as three BF16 products" if dk["bound"] == "tensor" else
                               f"FP32 FMA peak at the measured max clock: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz"),
