@@ -49,6 +49,10 @@ PRESETS = {
     "n4095": dict(N=4095, alphas=(1.7,), kappa=0.5, tau=5e-4, g=1, bumps=8, phi2=0.0, seed=3, total_steps=2000),
     "n8191": dict(N=8191, alphas=(1.6,), kappa=1.0, tau=2.5e-4, g=2, bumps=32, phi2=0.1, seed=5,
                   total_steps=500),
+    # 256 independent instances of uneven size: N from {127, 255, 511, 1023, 2047},
+    # alpha ~ U(1.1, 1.9), kappa ~ U(0.5, 2), tau = h/2 = 1/(N+1), g = -u^3, 8 bumps
+    "batch256": dict(N=None, count=256, sizes=(127, 255, 511, 1023, 2047), alphas=(1.1, 1.9), kappa=(0.5, 2.0),
+                     g=1, bumps=8, phi2=0.0, seed=4, total_steps=500),
 }
 CFG = PRESETS["n1023"]
 N_DEFAULT = CFG["N"]
@@ -88,7 +92,37 @@ def _select(a):
     if a.N is not None:
         CFG["N"] = a.N
     a.N = CFG["N"]
-    ALPHAS, KAPPA, TAU, GKIND = CFG["alphas"], CFG["kappa"], CFG["tau"], CFG["g"]
+    ALPHAS, KAPPA, TAU, GKIND = CFG["alphas"], CFG["kappa"], CFG.get("tau"), CFG["g"]
+
+
+def batch_instances(cfg):
+    """The batch workload's instances: (N, alpha, kappa, tau, seed) per
+    instance k, parameters drawn in order from default_rng(SEED_BASE + seed),
+    the bumps of instance k from seed SEED_BASE + seed + k."""
+    import numpy as np
+    from paper_2312_06206_gb300 import workloads as WL
+    rng = np.random.default_rng(WL.SEED_BASE + cfg["seed"])
+    out = []
+    for k in range(cfg["count"]):
+        N = int(rng.choice(cfg["sizes"]))
+        al = float(rng.uniform(*cfg["alphas"]))
+        ka = float(rng.uniform(*cfg["kappa"]))
+        out.append((N, al, ka, 1.0 / (N + 1), WL.SEED_BASE + cfg["seed"] + k))
+    return out
+
+
+def lpt_partition(costs, world):
+    """Longest-processing-time-first assignment of items to world bins:
+    items in decreasing cost, each to the least loaded bin (ties: lowest
+    rank).  Returns the item indices of every bin."""
+    order = sorted(range(len(costs)), key=lambda i: (-costs[i], i))
+    load = [0.0] * world
+    bins = [[] for _ in range(world)]
+    for i in order:
+        r = min(range(world), key=lambda b: (load[b], b))
+        bins[r].append(i)
+        load[r] += costs[i]
+    return [sorted(b) for b in bins]
 
 
 def _workload(N):
@@ -188,11 +222,56 @@ def cpu_baseline(N, phi1, nsteps=3, alpha=1.5):
 
 # --------------------------------------------------------- reference arm -----
 
+def run_reference_batch(a):
+    """Reference arm of the batch workload: the FP64 oracle (FFT tier) on the
+    host cores, each step one S-ADI step of one instance, cycling through the
+    first eight instances of the batch."""
+    import numpy as np
+    from oracle import sadi as O
+    from paper_2312_06206_gb300 import workloads as WL
+    sample = batch_instances(CFG)[:8]
+    probs, states = [], []
+    for (N, al, ka, ta, sd) in sample:
+        P = O.Problem(N, al, ka, ta, -1.0, 1.0, CFG["g"])
+        u0 = WL.gaussian_bumps(N, CFG["bumps"], sd)
+        probs.append(P)
+        states.append([u0, O.step(P, None, u0, True, np.zeros_like(u0), tier="fft")])
+
+    def one(k):
+        i = k % len(probs)
+        up, uc = states[i]
+        states[i] = [uc, O.step(probs[i], up, uc, False, tier="fft")]
+        return probs[i].N ** 2
+    for k in range(a.warmup):
+        one(k)
+    pts = 0
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        pts += one(a.warmup + k)
+    dt = time.perf_counter() - t0
+    val = pts / dt
+    sizes = [x[0] for x in sample]
+    line = {"metric": METRIC, "value": val, "unit": UNIT, "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": dt / a.steps * 1e3, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+            "config": {"workload": "sadi-batch 256 instances N~U{127,255,511,1023,2047} alpha~U(1.1,1.9) "
+                                   "kappa~U(0.5,2) tau=h/2 g=-u^3 phi1=8 gaussian bumps phi2=0",
+                       "reference": "FP64 CPU oracle (FFT tier); one step = one S-ADI step of one instance, "
+                                    f"cycling the first 8 instances (N = {sizes})"},
+            "cpu_baseline": {"value": val, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"{a.steps} single-instance S-ADI steps over instances of N = {sizes}"},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def run_reference(a):
     _select(a)
     ws, rank, _ = _dist()
     if rank != 0:
         return 0
+    if a.workload == "batch256":
+        return run_reference_batch(a)
     import numpy as np
     from oracle import sadi as O
     N = a.N
@@ -270,11 +349,261 @@ def algorithmic(N, Np, es, dense=False):
             (gemm_bytes + 4 * N * N * es, 6.0 * N ** 3, "tensor")]
 
 
+def roofline_of(phase_ms, N, Np, dense, ninst, workload):
+    """Roofline entry of the dominant kernel from the per-phase times (ms per
+    step, one launch per phase covering ninst instances of size N)."""
+    reg = Np <= 1024
+    pre = "kr_" if reg else "k_"
+    if dense:
+        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve<dense>+k_tc_gemm(x)", "k_tc_gemm(y)"]
+    else:
+        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve", pre + "cols_solve"]
+    alg = algorithmic(N, Np, 4, dense)
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
+    hbm_peak = float(peaks.get("hbm_gbs", 6750.0))
+    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1711.7))
+    per_kernel = {}
+    for k, nm in enumerate(names):
+        b_alg, f_alg, bound = alg[k]
+        dur = phase_ms[k] / 1e3
+        peak = bf16_peak if bound == "tensor" else fp32_peak
+        ach = f_alg * ninst / dur / 1e12
+        per_kernel[nm] = {"us": phase_ms[k] * 1e3, "share": phase_ms[k] / sum(phase_ms), "bound": bound,
+                          "achieved_tflops": ach, "frac": None if bound == "mixed" else ach / peak,
+                          "hbm_gbs": b_alg * ninst / dur / 1e9, "alg_bytes": b_alg * ninst,
+                          "alg_flops": f_alg * ninst, "traffic": NCU_TRAFFIC.get((workload, nm))}
+    dom = max((k for k in range(4) if alg[k][2] != "mixed"), key=lambda k: phase_ms[k])
+    dname = names[dom]
+    dk = per_kernel[dname]
+    return {"kernel": dname, "bound": "tensor" if dk["bound"] == "tensor" else "alu",
+            "achieved": dk["achieved_tflops"],
+            "peak": bf16_peak if dk["bound"] == "tensor" else fp32_peak, "unit": "TFLOP/s",
+            "frac": dk["frac"], "traffic": dk["traffic"], "avg_launch_us": dk["us"],
+            "traffic_note": "ncu dram bytes per launch from profiles/ (null if no capture of this kernel)",
+            "peak_note": ("bf16 dense sustained of measured (MEASURED_PEAKS.json), split-BF16 counted "
+                          "as three BF16 products" if dk["bound"] == "tensor" else
+                          f"FP32 FMA peak at the measured max clock: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz"),
+            "hbm_view": {"achieved_gbs": dk["hbm_gbs"], "peak_gbs": hbm_peak, "frac": dk["hbm_gbs"] / hbm_peak},
+            "kernels": per_kernel}
+
+
+def run_batch(a):
+    """The batch workload: every rank builds its LPT share of the 256
+    instances, the autotuner picks each size's form, and one CUDA graph
+    launch per step advances all of them (total work fixed: strong scaling)."""
+    ws, rank, local = _dist()
+    import numpy as np
+    import torch
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+    from paper_2312_06206_gb300 import build
+    build.build()
+    from paper_2312_06206_gb300 import sadi as S
+    from paper_2312_06206_gb300 import workloads as WL
+    inst = batch_instances(CFG)
+    costs = [N * N * math.log2(N + 1) for (N, _, _, _, _) in inst]
+    mine = lpt_partition(costs, ws)[rank]
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
+
+    def barrier():
+        torch.cuda.synchronize(dev)
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    t0 = time.perf_counter()
+    ctxs = []
+    for i in mine:
+        N, al, ka, ta, _ = inst[i]
+        s = S.Sadi(N, al, ka, ta, (-1.0, 1.0))
+        s.set_stream(stream.cuda_stream)
+        ctxs.append(s)
+    t_setup = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    S.sadi_autotune(ctxs, CFG["g"])
+    t_tune = time.perf_counter() - t0
+    tuning = sorted(set(s.sadi_tuning_log() for s in ctxs))
+    phis = {}
+    for i, s in zip(mine, ctxs):
+        N = inst[i][0]
+        phis[i] = WL.gaussian_bumps(N, CFG["bumps"], inst[i][4])
+        s.set_initial(phis[i])
+    S.sadi_batch_step(ctxs, 1)                  # the n = 0 step (not replayed)
+    graph = S.SadiGraph(ctxs, 1)
+    kernels_per_step = graph.sadi_graph_kernels()
+    graph.launch(max(a.warmup, 3))
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
+    for k in range(a.steps):
+        evs[k][0].record(stream)
+        graph.launch(1)
+        evs[k][1].record(stream)
+    barrier()
+    ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
+    clocks = sampler.stop()
+    graph.close()
+    # per-kernel phases of the largest instance of this rank (the dominant
+    # group: the largest N carries most of the points), for the roofline
+    big = max(range(len(ctxs)), key=lambda j: inst[mine[j]][0])
+    cb = ctxs[big]
+    cb.sadi_profile(True)
+    S.sadi_batch_step([cb], 10)
+    phase, nph = cb.sadi_get_phase_times()
+    cb.sadi_profile(False)
+    phase_ms = [t / max(nph, 1) for t in phase]
+    Nb = inst[mine[big]][0]
+    Npb = cb.sadi_get_info()[0]
+    gb, pb = cb.sadi_get_options()
+    roof = roofline_of(phase_ms, Nb, Npb, pb == S.SADI_PREC_FP32_DENSE, 1, None)
+    roof["scope"] = f"one N={Nb} instance of the batch stepped alone"
+    # e2e through the public API: set_initial from pinned host arrays, the
+    # n = 0 step, then per step one graph launch + sadi_get of every instance
+    import ctypes
+    lib = S.lib()
+    pins = {i: torch.from_numpy(phis[i]).pin_memory() for i in mine}
+    outs = {i: torch.empty(phis[i].shape, dtype=torch.float64).pin_memory() for i in mine}
+    nll = ctypes.c_longlong()
+    Ke = 2
+    barrier()
+    t0 = time.perf_counter()
+    for i, s in zip(mine, ctxs):
+        assert lib.sadi_set_initial(s.ctx, ctypes.c_void_p(pins[i].data_ptr()), None) == 0
+    S.sadi_batch_step(ctxs, 1)
+    g2 = S.SadiGraph(ctxs, 1)
+    for k in range(Ke):
+        g2.launch(1)
+        for i, s in zip(mine, ctxs):
+            assert lib.sadi_get(s.ctx, ctypes.c_void_p(outs[i].data_ptr()), ctypes.byref(nll)) == 0
+    dt_e2e = time.perf_counter() - t0
+    g2.close()
+    barrier()
+    h2d = sum(phis[i].size * 8 for i in mine) / (Ke + 1)
+    d2h = sum(phis[i].size * 8 for i in mine)
+
+    def reduce_max(vals):
+        tt = torch.tensor(vals, dtype=torch.float64, device=dev)
+        if ws > 1:
+            torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        return [float(x) for x in tt.tolist()]
+    ms_max, e2e_max = reduce_max([ms, dt_e2e])
+    pts_all = sum(N * N for (N, _, _, _, _) in inst)
+    value = pts_all * a.steps / (ms_max / 1e3)
+    # e2e counts the n = 0 step and Ke graph steps of every instance
+    e2e_val = pts_all * (Ke + 1) / e2e_max
+    if rank == 0:
+        # accuracy over the full step count: one instance per size against the
+        # FP64 path from the same data, in the form the autotuner chose
+        firsts = {}
+        for i, (N, _, _, _, _) in enumerate(inst):
+            firsts.setdefault(N, i)
+        acc = {}
+        pairs = []
+        for N, i in sorted(firsts.items()):
+            _, al, ka, ta, sd = inst[i]
+            phi = WL.gaussian_bumps(N, CFG["bumps"], sd)
+            prec = None
+            for j, s in zip(mine, ctxs):
+                if inst[j][0] == N:
+                    prec = s.sadi_get_options()[1]
+                    break
+            if prec is None:
+                prec = S.SADI_PREC_FP32
+            c64 = S.Sadi(N, al, ka, ta)
+            c64.set_options(CFG["g"], S.SADI_PREC_FP64)
+            c64.set_initial(phi)
+            c32 = S.Sadi(N, al, ka, ta)
+            c32.set_options(CFG["g"], prec)
+            c32.set_initial(phi)
+            pairs.append((N, i, prec, c64, c32))
+        acc_steps = CFG["total_steps"] if a.acc_steps > 0 else 0
+        if acc_steps:
+            S.sadi_batch_step([p[3] for p in pairs] + [p[4] for p in pairs], acc_steps)
+        for N, i, prec, c64, c32 in pairs:
+            if acc_steps:
+                u64, _ = c64.get()
+                u32, _ = c32.get()
+                acc[str(N)] = {"instance": i, "form": {1: "fp32_gsfft", 2: "fp32_dense"}.get(prec, prec),
+                               "rel_l2": float(np.linalg.norm(u32 - u64) / np.linalg.norm(u64))}
+            c64.close()
+            c32.close()
+        cpu = None
+        if ws == 1 and not a.no_cpu_baseline:
+            cpu = batch_cpu_baseline(inst)
+        nsz = {str(n): sum(1 for x in inst if x[0] == n) for n in CFG["sizes"]}
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+            "scaling": "strong", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "sadi-batch 256 instances N~U{127,255,511,1023,2047} alpha~U(1.1,1.9) "
+                                   "kappa~U(0.5,2) tau=h/2 g=-u^3 phi1=8 gaussian bumps phi2=0",
+                       "instances": len(inst), "instances_per_size": nsz, "points_per_step": pts_all,
+                       "parallelism": f"LPT-partitioned instances over {ws} rank(s), no collective",
+                       "launch": "one CUDA graph launch per step covering every instance of the rank",
+                       "l2": "working set of all instances far above L2 (no flush needed)",
+                       "autotune": tuning, "setup_s": t_setup, "autotune_s": t_tune},
+            "rel_l2_vs_fp64_full": {"steps": acc_steps, "per_size": acc} if acc_steps else None,
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                    "how": "C ABI with pinned host buffers: sadi_set_initial of every instance, the n = 0 "
+                           "batch step, then per step one graph launch + sadi_get of every instance; wall clock"},
+            "gpu_launches": kernels_per_step * a.steps,
+            "clocks": clocks,
+        }
+        print(json.dumps(line), flush=True)
+    for s in ctxs:
+        s.close()
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def batch_cpu_baseline(inst, budget_s=10.0):
+    """The FP64 oracle (FFT tier) stepping instances of the batch in order,
+    two n >= 1 steps each, until about budget_s seconds of work."""
+    import numpy as np
+    from oracle import sadi as O
+    from paper_2312_06206_gb300 import workloads as WL
+    pts = 0
+    spent = 0.0
+    used = 0
+    for (N, al, ka, ta, sd) in inst:
+        P = O.Problem(N, al, ka, ta, -1.0, 1.0, CFG["g"])
+        u0 = WL.gaussian_bumps(N, CFG["bumps"], sd)
+        u1 = O.step(P, None, u0, True, np.zeros_like(u0), tier="fft")
+        t0 = time.perf_counter()
+        up, uc = u0, u1
+        for _ in range(2):
+            up, uc = uc, O.step(P, up, uc, False, tier="fft")
+        spent += time.perf_counter() - t0
+        pts += 2 * N * N
+        used += 1
+        if spent >= budget_s:
+            break
+    return {"value": pts / spent, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": f"the first {used} instances of the batch, 2 S-ADI steps (n>=1) each, oracle FFT tier "
+                      "(FP64), default BLAS threading", "seconds": spent}
+
+
 def main():
     a = _args()
     if a.impl == "reference":
         return run_reference(a)
     _select(a)
+    if a.workload == "batch256":
+        return run_batch(a)
     ws, rank, local = _dist()
     import numpy as np
     import torch
@@ -394,47 +723,7 @@ def main():
     Kp = max(5, min(a.steps, 20))
     _, (phase_ms, _) = timed(cc, Kp, 3, profile=True)
     Np = cc[0].sadi_get_info()[0]
-    reg = Np <= 1024
-    pre = "kr_" if reg else "k_"
-    if dense:
-        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve<dense>+k_tc_gemm(x)", "k_tc_gemm(y)"]
-    else:
-        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve", pre + "cols_solve"]
-    alg = algorithmic(N, Np, 4, dense)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    hbm_peak = float(peaks.get("hbm_gbs", 6750.0))
-    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1711.7))
-    ninst = len(ALPHAS)
-    per_kernel = {}
-    for k, nm in enumerate(names):
-        b_alg, f_alg, bound = alg[k]
-        dur = phase_ms[k] / 1e3
-        peak = bf16_peak if bound == "tensor" else fp32_peak
-        ach = f_alg * ninst / dur / 1e12
-        per_kernel[nm] = {"us": phase_ms[k] * 1e3, "share": phase_ms[k] / sum(phase_ms), "bound": bound,
-                          "achieved_tflops": ach, "frac": None if bound == "mixed" else ach / peak,
-                          "hbm_gbs": b_alg * ninst / dur / 1e9, "alg_bytes": b_alg * ninst,
-                          "alg_flops": f_alg * ninst,
-                          "traffic": NCU_TRAFFIC.get((a.workload if a.N == PRESETS[a.workload]["N"] else None, nm))}
-    dom = max((k for k in range(4) if alg[k][2] != "mixed"), key=lambda k: phase_ms[k])
-    dname = names[dom]
-    dk = per_kernel[dname]
-    roofline = {"kernel": dname, "bound": "tensor" if dk["bound"] == "tensor" else "alu",
-                "achieved": dk["achieved_tflops"],
-                "peak": bf16_peak if dk["bound"] == "tensor" else fp32_peak, "unit": "TFLOP/s",
-                "frac": dk["frac"], "traffic": dk["traffic"], "avg_launch_us": dk["us"],
-                "traffic_note": "ncu dram bytes per launch from profiles/ (null if no capture of this kernel)",
-                "peak_note": ("bf16 dense sustained of measured (MEASURED_PEAKS.json), split-BF16 counted "
-                              "as three BF16 products" if dk["bound"] == "tensor" else
-                              f"FP32 FMA peak at the measured max clock: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz"),
-                "hbm_view": {"achieved_gbs": dk["hbm_gbs"], "peak_gbs": hbm_peak, "frac": dk["hbm_gbs"] / hbm_peak},
-                "kernels": per_kernel}
+    roofline = roofline_of(phase_ms, N, Np, dense, len(ALPHAS), a.workload if a.N == PRESETS[a.workload]["N"] else None)
     # e2e through the public API with host buffers: set_initial from pinned
     # host arrays, then every step sadi_batch_step(1) + sadi_get into pinned host.
     pin_in = torch.from_numpy(phi1).pin_memory()

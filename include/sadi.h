@@ -86,6 +86,9 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau,
  * (SADI_ESTATE otherwise). */
 sadi_status sadi_set_options(sadi_ctx *ctx, int g, int prec);
 
+/* Current g and precision of ctx (either pointer may be NULL). */
+sadi_status sadi_get_options(const sadi_ctx *ctx, int *g, int *prec);
+
 /* Optional source term (an extension beyond the paper's problem statement,
  * used for manufactured-solution checks): the equation becomes
  * u_tt = -kappa (-Delta)^{alpha/2} u + g(u) + f with
@@ -124,6 +127,45 @@ sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
  * queued on the other contexts' streams and before their later work (event
  * waits).  Results are identical to stepping each context alone. */
 sadi_status sadi_batch_step(sadi_ctx **ctxs, int count, int nsteps);
+
+/* CUDA-graph replay of batched steps (no paper counterpart; it removes the
+ * per-step host launch cost when many small instances advance together).
+ * sadi_graph_create captures nsteps >= 1 steps of the count contexts, issued
+ * exactly as sadi_batch_step(ctxs, count, nsteps) would issue them, into a
+ * CUDA graph on the first context's stream; nothing runs at capture time and
+ * the contexts' step counters are unchanged.  Requirements (SADI_ESTATE /
+ * SADI_EINVAL / SADI_EUNSUPPORTED otherwise): every context initialised and
+ * past its n = 0 step (n >= 1), FP32 or FP32_DENSE precision (their state is
+ * updated in place, so one captured step fits every later step), no source
+ * term, profiling off, all contexts on one stream, distinct.
+ * sadi_graph_launch replays the graph reps >= 0 times (asynchronous) and
+ * advances every context's n by nsteps * reps; it re-checks the requirements
+ * first.  The graph holds the contexts' device pointers: destroy it before
+ * any of its contexts, and re-create it after sadi_set_options on any of
+ * them.  sadi_graph_destroy waits for the stream and frees the graph (NULL
+ * is a no-op). */
+typedef struct sadi_graph sadi_graph;
+sadi_status sadi_graph_create(sadi_ctx **ctxs, int count, int nsteps, sadi_graph **out);
+sadi_status sadi_graph_launch(sadi_graph *graph, int reps);
+/* Number of kernel launches one replay of graph performs (*kernels). */
+sadi_status sadi_graph_kernels(const sadi_graph *graph, int *kernels);
+void sadi_graph_destroy(sadi_graph *graph);
+
+/* Autotuner (no paper counterpart): for the count contexts, grouped by N,
+ * time the candidate step forms on zero data with the group stepped as
+ * sadi_batch_step steps it (up to 32 contexts per group) -- SADI_PREC_FP32
+ * (Gohberg-Semencul FFT sweeps) and, for N <= 4096 unless flags bit 0 is
+ * set, SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, on
+ * the shared-memory FFT engine (N' > 1024), the work decomposition of
+ * sadi_set_tiles by coordinate descent.  Each context is left with g, the
+ * fastest precision and tiles of its group, uninitialised (call
+ * sadi_set_initial next).  Must precede sadi_set_initial and
+ * sadi_set_source.  The choice and the timings are readable with
+ * sadi_tuning_log.  Synchronous. */
+sadi_status sadi_autotune(sadi_ctx **ctxs, int count, int g, int flags);
+
+/* Text record of the last sadi_autotune choice for ctx ("" if none). */
+const char *sadi_tuning_log(const sadi_ctx *ctx);
 
 /* Copy u^n to the host (N*N doubles) after the stream's pending work; *n_out
  * (may be NULL) receives n.  Synchronous.  Returns SADI_ETIMEOUT (and the

@@ -12,82 +12,14 @@
 
 #include "../../include/sadi.h"
 #include "fft.cuh"
+#include "sadi_ctx.h"
 #include "sadi_internal.h"
 
 using namespace sadi;
 
-struct sadi_ctx {
-  Geom g{};
-  double alpha = 0, kappa = 0, tau = 0, a = 0, b = 0, h = 0, s = 0;
-  int gkind = SADI_G_ZERO;
-  int prec = SADI_PREC_FP64;
-  int device = 0;
-  cudaStream_t own_stream = nullptr;
-  cudaStream_t stream = nullptr;
-  // FP64 setup products
-  double* a1 = nullptr;      // Np
-  double* a2d = nullptr;     // N x N
-  double* cgen = nullptr;    // Np
-  double* lnat = nullptr;    // (Np+1)^2
-  double2* tw64 = nullptr;   // P
-  float2* tw32 = nullptr;    // P
-  double2* stw64 = nullptr;  // per-stage FFT twiddles
-  float2* stw32 = nullptr;
-  Tiles tiles64{}, tiles32{};
-  // FP32 register-FFT path tables (N' <= 1024)
-  float2* rtw1 = nullptr;
-  float* rlreg = nullptr;
-  float2* rlamc = nullptr;
-  float2* rlams = nullptr;
-  bool reg_path = false;
-  double* lpb64 = nullptr;   // (Np+1) 2 Np
-  float* lpb32 = nullptr;
-  double2* lamc64 = nullptr;
-  double2* lams64 = nullptr;
-  float2* lamc32 = nullptr;
-  float2* lams32 = nullptr;
-  double* G64 = nullptr;     // N x r
-  float* G32 = nullptr;
-  // state (element type per prec)
-  // FP64: ubuf[cur] = u^n, ubuf[1-cur] = u^{n-1} (ping-pong).
-  // FP32: ubuf[0] = hi part of u^n, ubuf[1] = d = u^n - u^{n-1}, ulo = lo part
-  // (double-float state, updated in place; cur stays 0).
-  void* ubuf[2] = {nullptr, nullptr};
-  float* ulo = nullptr;
-  // FP32 forms: the remainder C = -kappa tau^2 L_h u^n as a double-float pair,
-  // advanced each step by the convolution of the increment d^n
-  float* Chi = nullptr;
-  float* Clo = nullptr;
-  void* phi2 = nullptr;
-  void* S = nullptr;         // N x Np complex
-  void* W = nullptr;         // N x N
-  double* stage = nullptr;   // N x N doubles (host <-> device staging)
-  int cur = 0;
-  long long n = 0;
-  bool initialized = false;
-  bool broken = false;
-  std::string err;
-  // per-kernel timing (sadi_profile)
-  bool profiling = false;
-  std::vector<std::array<cudaEvent_t, 5>> ev_pool;   // recorded, not yet folded
-  std::vector<std::array<cudaEvent_t, 5>> ev_free;
-  double phase_ms[4] = {0, 0, 0, 0};
-  long long phase_steps = 0;
-  cudaEvent_t order_ev = nullptr;   // cross-stream ordering in sadi_batch_step
-  // optional source term f^n = cos(omega t_n + phase) F(x)
-  void* F = nullptr;                // T, N x N
-  double f_omega = 0.0, f_phase = 0.0;
-  // dense-inverse form (SADI_PREC_FP32_DENSE): BF16 pairs, npad x npad,
-  // zero-padded: E = H^-1 - I, B^n rows, W^T rows; tensor maps of the two GEMMs
-  int npad = 0;
-  unsigned short *Eh = nullptr, *El = nullptr, *Bh = nullptr, *Bl = nullptr, *WTh = nullptr, *WTl = nullptr;
-  int* tcerr = nullptr;             // device flag: a bounded wait in a GEMM ran out
-  std::unique_ptr<TcInst> tc_x, tc_y;
-};
-
 static thread_local std::string g_create_err;
 
-namespace {
+namespace sadi_api {
 
 sadi_status fail(sadi_ctx* c, sadi_status st, const std::string& msg) {
   if (c) c->err = msg;
@@ -218,7 +150,9 @@ sadi_status setup_dense(sadi_ctx* c) {
   return SADI_OK;
 }
 
-}  // namespace
+}  // namespace sadi_api
+
+using namespace sadi_api;
 
 extern "C" {
 
@@ -356,6 +290,13 @@ sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
   return SADI_OK;
 }
 
+sadi_status sadi_get_options(const sadi_ctx* c, int* g, int* prec) {
+  if (!c) return SADI_EINVAL;
+  if (g) *g = c->gkind;
+  if (prec) *prec = c->prec;
+  return SADI_OK;
+}
+
 sadi_status sadi_set_source(sadi_ctx* c, const double* F, double omega, double phase) {
   if (!c) return SADI_EINVAL;
   if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
@@ -431,7 +372,7 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
 
 }  // extern "C"
 
-namespace {
+namespace sadi_api {
 
 // Profiling events for one step of ctx (nullptr when not profiling).
 sadi_status next_events(sadi_ctx* c, cudaEvent_t** out) {
@@ -605,7 +546,7 @@ sadi_status check_steppable(sadi_ctx* c) {
   return SADI_OK;
 }
 
-}  // namespace
+}  // namespace sadi_api
 
 extern "C" {
 
@@ -629,15 +570,11 @@ sadi_status sadi_step(sadi_ctx* c, int nsteps) {
   return SADI_OK;
 }
 
-sadi_status sadi_batch_step(sadi_ctx** ctxs, int count, int nsteps) {
-  if (!ctxs || count < 1 || nsteps < 0) return SADI_EINVAL;
-  for (int k = 0; k < count; ++k) {
-    if (!ctxs[k]) return SADI_EINVAL;
-    for (int j = 0; j < k; ++j)
-      if (ctxs[j] == ctxs[k]) return fail(ctxs[k], SADI_EINVAL, "a context appears twice in the batch");
-    sadi_status st = check_steppable(ctxs[k]);
-    if (st != SADI_OK) return st;
-  }
+}  // extern "C"
+
+namespace sadi_api {
+
+sadi_status batch_issue(sadi_ctx** ctxs, int count, int nsteps) {
   // group register-path contexts by FFT length (insertion order kept)
   // (dense-form contexts on the register path form their own groups)
   std::vector<std::vector<sadi_ctx*>> groups;
@@ -697,6 +634,38 @@ sadi_status sadi_batch_step(sadi_ctx** ctxs, int count, int nsteps) {
       if (ctxs[k]->stream != s0) CK(cudaStreamWaitEvent(ctxs[k]->stream, c0->order_ev, 0), "cudaStreamWaitEvent");
   }
   return SADI_OK;
+}
+
+sadi_status zero_initial(sadi_ctx* c) {
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  const size_t es = esize(c->prec);
+  cudaStream_t st = c->stream;
+  void* bufs[] = {c->ubuf[0], c->ubuf[1], c->phi2};
+  for (void* b : bufs)
+    if (b) CK(cudaMemsetAsync(b, 0, nn * es, st), "zero state");
+  float* fb[] = {c->ulo, c->Chi, c->Clo};
+  for (float* b : fb)
+    if (b) CK(cudaMemsetAsync(b, 0, nn * sizeof(float), st), "zero state");
+  c->cur = 0;
+  c->n = 0;
+  c->initialized = true;
+  return SADI_OK;
+}
+
+}  // namespace sadi_api
+
+extern "C" {
+
+sadi_status sadi_batch_step(sadi_ctx** ctxs, int count, int nsteps) {
+  if (!ctxs || count < 1 || nsteps < 0) return SADI_EINVAL;
+  for (int k = 0; k < count; ++k) {
+    if (!ctxs[k]) return SADI_EINVAL;
+    for (int j = 0; j < k; ++j)
+      if (ctxs[j] == ctxs[k]) return fail(ctxs[k], SADI_EINVAL, "a context appears twice in the batch");
+    sadi_status st = check_steppable(ctxs[k]);
+    if (st != SADI_OK) return st;
+  }
+  return batch_issue(ctxs, count, nsteps);
 }
 
 sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {

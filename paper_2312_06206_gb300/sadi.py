@@ -26,6 +26,7 @@ _SIGS = {
     "sadi_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
                               C.POINTER(C.c_void_p)]),
     "sadi_set_options": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
+    "sadi_get_options": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sadi_set_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
     "sadi_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
     "sadi_set_initial": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p]),
@@ -43,6 +44,12 @@ _SIGS = {
     "sadi_destroy": (None, [C.c_void_p]),
     "sadi_gemm_split_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                         C.c_void_p]),
+    "sadi_graph_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "sadi_graph_launch": (C.c_int, [C.c_void_p, C.c_int]),
+    "sadi_graph_destroy": (None, [C.c_void_p]),
+    "sadi_graph_kernels": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "sadi_autotune": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int]),
+    "sadi_tuning_log": (C.c_char_p, [C.c_void_p]),
     "sadi_step_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong]),
 }
 
@@ -96,6 +103,60 @@ def sadi_gemm_split_bf16(A_ptr: int, B_ptr: int, C_ptr: int, M: int, N: int, K: 
         raise SadiError(st, "sadi_gemm_split_bf16 failed")
 
 
+def _batch_error(st, instances, what):
+    msgs = [s.sadi_last_error() for s in instances]
+    raise SadiError(st, "; ".join(m for m in msgs if m) or what)
+
+
+class SadiGraph:
+    """A captured batched step (sadi_graph_create); launch() replays it."""
+
+    def __init__(self, instances, nsteps: int = 1):
+        self.instances = list(instances)
+        arr = (C.c_void_p * len(self.instances))(*[s.ctx for s in self.instances])
+        out = C.c_void_p()
+        st = lib().sadi_graph_create(arr, len(self.instances), int(nsteps), C.byref(out))
+        if st != SADI_OK:
+            _batch_error(st, self.instances, "sadi_graph_create failed")
+        self.handle = out.value
+        self.nsteps = int(nsteps)
+
+    def sadi_graph_launch(self, reps: int = 1):
+        st = lib().sadi_graph_launch(self.handle, int(reps))
+        if st != SADI_OK:
+            _batch_error(st, self.instances, "sadi_graph_launch failed")
+
+    launch = sadi_graph_launch
+
+    def sadi_graph_kernels(self) -> int:
+        k = C.c_int()
+        st = lib().sadi_graph_kernels(self.handle, C.byref(k))
+        if st != SADI_OK:
+            _batch_error(st, self.instances, "sadi_graph_kernels failed")
+        return k.value
+
+    def sadi_graph_destroy(self):
+        if getattr(self, "handle", None):
+            lib().sadi_graph_destroy(self.handle)
+            self.handle = None
+
+    close = sadi_graph_destroy
+
+    def __del__(self):
+        try:
+            self.sadi_graph_destroy()
+        except Exception:
+            pass
+
+
+def sadi_autotune(instances, g: int, flags: int = 0):
+    """Pick the step form and tiles per N for these (uninitialised) instances."""
+    arr = (C.c_void_p * len(instances))(*[s.ctx for s in instances])
+    st = lib().sadi_autotune(arr, len(instances), int(g), int(flags))
+    if st != SADI_OK:
+        _batch_error(st, instances, "sadi_autotune failed")
+
+
 def sadi_batch_step(instances, nsteps: int = 1):
     """Advance several Sadi instances together (same stream); see sadi.h."""
     arr = (C.c_void_p * len(instances))(*[s.ctx for s in instances])
@@ -119,6 +180,11 @@ class Sadi:
     # -- C ABI calls, same names -------------------------------------------
     def sadi_set_options(self, g: int = SADI_G_ZERO, prec: int = SADI_PREC_FP64):
         _check(lib().sadi_set_options(self.ctx, int(g), int(prec)), self.ctx)
+
+    def sadi_get_options(self):
+        g, p = C.c_int(), C.c_int()
+        _check(lib().sadi_get_options(self.ctx, C.byref(g), C.byref(p)), self.ctx)
+        return g.value, p.value
 
     def sadi_set_source(self, F=None, omega: float = 0.0, phase: float = 0.0):
         f = None if F is None else _f64(F, self.N)
@@ -183,6 +249,9 @@ class Sadi:
         """One step on caller-owned device buffers (N*N doubles each); no allocation."""
         _check(lib().sadi_step_noalloc(self.ctx, C.c_void_p(u_prev_ptr), C.c_void_p(u_cur_ptr),
                                        C.c_void_p(u_next_ptr), int(n)), self.ctx)
+
+    def sadi_tuning_log(self) -> str:
+        return lib().sadi_tuning_log(self.ctx).decode()
 
     def sadi_last_error(self) -> str:
         return lib().sadi_last_error(self.ctx).decode()

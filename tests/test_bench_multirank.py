@@ -43,3 +43,47 @@ def test_two_rank_aggregate_uses_slowest_rank():
         assert agg["value"] == pytest.approx(2 * 1000 * 50 / 0.020)
         assert agg["value64"] == pytest.approx(2 * 1000 * 20 / 0.200)
         assert agg["e2e"] == pytest.approx(2 * 1000 * 20 / 1.0)
+
+
+def _lpt_worker(rank, world, port, q):
+    os.environ["MASTER_ADDR"] = "127.0.0.1"
+    os.environ["MASTER_PORT"] = str(port)
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    cfg = dict(bench.PRESETS["batch256"])
+    inst = bench.batch_instances(cfg)
+    costs = [N * N * __import__("math").log2(N + 1) for (N, _, _, _, _) in inst]
+    mine = bench.lpt_partition(costs, world)[rank]
+    got = [None] * world
+    dist.all_gather_object(got, mine)
+    q.put((rank, got, costs))
+    dist.destroy_process_group()
+
+
+def test_two_rank_lpt_partition_of_the_batch_workload():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    procs = [ctx.Process(target=_lpt_worker, args=(r, 2, 29613, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    out = dict((r, (g, c)) for r, g, c in (q.get(timeout=120) for _ in range(2)))
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (g0, costs), (g1, _) = out[0], out[1]
+    assert g0 == g1                                   # every rank computes the same split
+    a, b = g0
+    assert sorted(a + b) == list(range(256)) and not set(a) & set(b)
+    la, lb = sum(costs[i] for i in a), sum(costs[i] for i in b)
+    assert abs(la - lb) <= max(costs)                 # LPT bound: within one item
+
+
+def test_batch_instances_follow_the_recipe():
+    import bench
+    inst = bench.batch_instances(bench.PRESETS["batch256"])
+    assert len(inst) == 256
+    for N, al, ka, ta, sd in inst:
+        assert N in (127, 255, 511, 1023, 2047)
+        assert 1.1 <= al <= 1.9 and 0.5 <= ka <= 2.0 and ta == 1.0 / (N + 1)
+    assert len({x[0] for x in inst}) == 5
+    assert inst == bench.batch_instances(bench.PRESETS["batch256"])   # seeded

@@ -1,0 +1,72 @@
+"""Full-size checks through the C ABI where no FP64 reference run exists
+(N = 8191, FFT length 8192, FP32 only) and at the dense form's largest size:
+properties that hold at any N.
+
+1. alpha = 2: L_h is the 5-point stencil, the remainder vanishes and a
+   Dirichlet sine mode (k, l) is an eigenvector of everything; u^n = c_n mode
+   with the closed scalar recursion of the scheme (Sec. 3 factored form):
+   (1 + tau^2 kappa mu_k / 2)(1 + tau^2 kappa mu_l / 2)(c_{n+1} - 2c_n + c_{n-1})
+       = -tau^2 kappa (mu_k + mu_l) c_n,  mu_k = (4/h^2) sin^2(k pi / (2(N+1))),
+   with the n = 0 start step (c_1 - c_0) x (...) = tau d_0 - tau^2/2 kappa (mu_k + mu_l) c_0.
+2. Fractional alpha: data symmetric under x <-> y stays symmetric (the x and
+   y sweeps and the 2D symbol are applied consistently)."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2312_06206_gb300 import workloads as WL
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def S():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2312_06206_gb300 import build
+    build.build()
+    from paper_2312_06206_gb300 import sadi
+    return sadi
+
+
+def _mode_run(S, N, prec, k, l, kappa, tau, steps, c0=0.7, d0=-0.4):
+    X, Y = WL.coords(N, -1.0, 1.0)
+    mode = np.sin(k * np.pi * (X + 1) / 2) * np.sin(l * np.pi * (Y + 1) / 2)
+    with S.Sadi(N, 2.0, kappa, tau) as s:
+        s.set_options(0, prec)
+        s.set_initial(c0 * mode, d0 * mode)
+        s.step(steps)
+        u, _ = s.get()
+    h = 2.0 / (N + 1)
+    mu = lambda m: 4 / h ** 2 * math.sin(m * math.pi / (2 * (N + 1))) ** 2
+    fac = (1 + tau ** 2 * kappa * mu(k) / 2) * (1 + tau ** 2 * kappa * mu(l) / 2)
+    lam = mu(k) + mu(l)
+    c = [c0, c0 + (tau * d0 - 0.5 * tau ** 2 * kappa * lam * c0) / fac]
+    for n in range(1, steps):
+        c.append(2 * c[n] - c[n - 1] - tau ** 2 * kappa * lam * c[n] / fac)
+    ref = c[steps] * mode
+    return float(np.linalg.norm(u - ref) / np.linalg.norm(ref))
+
+
+@pytest.mark.parametrize("N,prec_name,k,l", [(8191, "SADI_PREC_FP32", 3, 5), (8191, "SADI_PREC_FP32", 40, 7),
+                                             (4095, "SADI_PREC_FP32_DENSE", 3, 5),
+                                             (4095, "SADI_PREC_FP64", 11, 2)])
+def test_alpha2_sine_mode_at_full_size(S, N, prec_name, k, l):
+    tol = 1e-10 if prec_name == "SADI_PREC_FP64" else 1e-5
+    err = _mode_run(S, N, getattr(S, prec_name), k, l, kappa=1.0, tau=2.5e-4, steps=20)
+    assert err <= tol, err
+
+
+def test_symmetric_data_stays_symmetric_at_n8191(S):
+    N = 8191
+    X, Y = WL.coords(N, -1.0, 1.0)
+    phi1 = np.exp(-30 * (X ** 2 + Y ** 2)) + 0.5 * np.exp(-60 * ((X - 0.3) ** 2 + (Y - 0.3) ** 2))
+    with S.Sadi(N, 1.6, 1.0, 2.5e-4) as s:
+        s.set_options(2, S.SADI_PREC_FP32)
+        s.set_initial(phi1, 0.1 * phi1)
+        s.step(10)
+        u, _ = s.get()
+    assert np.isfinite(u).all()
+    assert np.abs(u - u.T).max() <= 1e-5 * np.abs(u).max()
