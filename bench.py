@@ -9,7 +9,7 @@ Workload (one bench "step" = one S-ADI time step of every instance):
 Metric: grid-point updates per second, N^2 * steps * instances / time, for the
 chosen form, with the plain FP64 GS-FFT path on the same GPU and each form's
 relative L2 difference to it stated.  Candidate forms: FP32 FFTs with
-Gohberg-Semencul FFT sweeps, and (N <= 4096) FP32 FFTs with both sweeps as
+Gohberg-Semencul FFT sweeps, and FP32 FFTs with both sweeps as
 split-BF16 dense-inverse GEMMs on the tensor cores; the chosen form is the
 fastest one within 1e-5 relative L2 of the FP64 path after the accuracy run
 (--acc-steps, default 1000 steps from the same data).
@@ -675,7 +675,7 @@ def main():
     # candidate forms: FP32 Gohberg-Semencul FFT sweeps, and (N <= 4096) the
     # dense-inverse sweeps as split-BF16 tensor-core GEMMs
     forms = [("fp32_gsfft", S.SADI_PREC_FP32)]
-    if N <= 4096:
+    if N <= 8192:
         forms.append(("fp32_dense", S.SADI_PREC_FP32_DENSE))
     res = {}
     for name, prec in forms:

@@ -64,7 +64,8 @@ typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2 } sadi_g
  *   uhat = W + E W, each product a split-BF16 GEMM on the tensor cores
  *   (E and the right-hand side split into BF16 hi + lo pairs, three products,
  *   FP32 accumulation).  E comes from the FP64 generator of the N x N matrix.
- *   N <= 4096 (SADI_EUNSUPPORTED otherwise). */
+ *   Any N up to 8192 (E and the operands take 12 N_p^2 bytes, N_p = N rounded
+ *   up to 256). */
 typedef enum { SADI_PREC_FP64 = 0, SADI_PREC_FP32 = 1, SADI_PREC_FP32_DENSE = 2 } sadi_prec;
 
 /* Create a context for N interior points per direction, fractional order
@@ -154,8 +155,8 @@ void sadi_graph_destroy(sadi_graph *graph);
 /* Autotuner (no paper counterpart): for the count contexts, grouped by N,
  * time the candidate step forms on zero data with the group stepped as
  * sadi_batch_step steps it (up to 32 contexts per group) -- SADI_PREC_FP32
- * (Gohberg-Semencul FFT sweeps) and, for N <= 4096 unless flags bit 0 is
- * set, SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, on
+ * (Gohberg-Semencul FFT sweeps) and, unless flags bit 0 is set,
+ * SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, on
  * the shared-memory FFT engine (N' > 1024), the work decomposition of
  * sadi_set_tiles by coordinate descent.  Each context is left with g, the
  * fastest precision and tiles of its group, uninitialised (call

@@ -212,7 +212,7 @@ sadi_status sadi_autotune(sadi_ctx** ctxs, int count, int g, int flags) {
     std::vector<sadi_ctx*> grp(all.begin(), all.begin() + std::min(all.size(), cap));
     const int N = kv.first, Np = grp[0]->g.Np;
     std::vector<int> precs{SADI_PREC_FP32};
-    if (N <= 4096 && !(flags & 1)) precs.push_back(SADI_PREC_FP32_DENSE);
+    if (!(flags & 1)) precs.push_back(SADI_PREC_FP32_DENSE);
     std::string log = fmt("N=%.0f N'=%.0f batch=%.0f:", N, Np, (double)grp.size());
     Cand best{SADI_PREC_FP32, Tiles{0, 0, 0}};
     double best_ms = 1e30;

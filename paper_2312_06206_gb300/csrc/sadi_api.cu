@@ -274,8 +274,8 @@ sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
     return fail(c, SADI_EINVAL, "prec must be 0, 1 or 2");
   if (prec == SADI_PREC_FP64 && c->g.N > 4096)
     return fail(c, SADI_EUNSUPPORTED, "the FP64 step path supports N <= 4096");
-  if (prec == SADI_PREC_FP32_DENSE && c->g.N > 4096)
-    return fail(c, SADI_EUNSUPPORTED, "the dense-inverse form supports N <= 4096");
+  if (prec == SADI_PREC_FP32_DENSE && c->g.N > 8192)
+    return fail(c, SADI_EUNSUPPORTED, "the dense-inverse form supports N <= 8192");
   if (prec != c->prec && c->F) return fail(c, SADI_ESTATE, "set the precision before sadi_set_source");
   if (prec == SADI_PREC_FP32_DENSE) {
     const sadi_status ds = setup_dense(c);

@@ -31,20 +31,6 @@ __device__ __forceinline__ T g_of_r(int kind, T u) {
 
 __host__ __device__ constexpr int pad32(int k) { return k + (k >> 5); }
 
-// Incremental remainder: C = -kappa tau^2 L_h u^n as a double-float pair
-// (Ch + Cl), advanced by the convolution of the increment d^n (two-sum);
-// returns the new Ch.
-__device__ __forceinline__ float acc_rem(float* Ch, float* Cl, size_t idx, float x) {
-  const float hi = Ch[idx], lo = Cl[idx];
-  const float s = hi + x;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (x - bb);
-  const float l2 = lo + err;
-  const float h2 = s + l2;
-  Ch[idx] = h2;
-  Cl[idx] = l2 - (h2 - s);
-  return h2;
-}
 
 // elements of one vector's shared buffer, rounded so that buffers of
 // consecutive vectors start on staggered banks (8-byte elements, 16 per 128 B)
@@ -329,28 +315,47 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
   F::inv(x, sm, t, I.tw1);
   store_nat<LOGL>(x, sm, t);
   __syncthreads();
-  // B^n in place: sm[n] holds the convolution at 2n, 2n+1 (real view)
+  // B^n in place: sm[n] holds the convolution at 2n, 2n+1 (real view).  The
+  // remainder pairs of four q are loaded before any of them is stored (the
+  // loads overlap instead of waiting one after another).
   const float tau = I.tau, tau2 = I.tau2;
+  const size_t rbase = (size_t)rrow * N;
 #pragma unroll 1
-  for (int q = 0; q < F::E; ++q) {
-    const int n = t + F::TT * q;
-    const float2 cv = sm[pad32(n)];
-    float b0 = 0.f, b1 = 0.f;
-    if (valid && 2 * n < N) {
-      const float c = acc_rem(I.C_hi, I.C_lo, (size_t)row * N + 2 * n, cv.x);
-      float gs = g_of_r<float>(I.gkind, us[2 * n]);
-      if (I.F) gs += I.fsc * I.F[(size_t)row * N + 2 * n];
-      const float gg = tau2 * gs;
-      b0 = I.first ? tau * ps[2 * n] + 0.5f * (c + gg) : c + gg;
+  for (int q0 = 0; q0 < F::E; q0 += 4) {
+    float ch[8], cl[8];
+#pragma unroll
+    for (int j = 0; j < 8; ++j) {
+      const int x = 2 * (t + F::TT * (q0 + (j >> 1))) + (j & 1);
+      const bool ok = valid && x < N;
+      ch[j] = ok ? I.C_hi[rbase + x] : 0.f;
+      cl[j] = ok ? I.C_lo[rbase + x] : 0.f;
     }
-    if (valid && 2 * n + 1 < N) {
-      const float c = acc_rem(I.C_hi, I.C_lo, (size_t)row * N + 2 * n + 1, cv.y);
-      float gs = g_of_r<float>(I.gkind, us[2 * n + 1]);
-      if (I.F) gs += I.fsc * I.F[(size_t)row * N + 2 * n + 1];
-      const float gg = tau2 * gs;
-      b1 = I.first ? tau * ps[2 * n + 1] + 0.5f * (c + gg) : c + gg;
+#pragma unroll
+    for (int j2 = 0; j2 < 4; ++j2) {
+      const int n = t + F::TT * (q0 + j2);
+      const float2 cv = sm[pad32(n)];
+      float b[2] = {0.f, 0.f};
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int x = 2 * n + e;
+        if (valid && x < N) {
+          // C <- C + conv (two-sum into the double-float pair)
+          const float hi = ch[2 * j2 + e], lo = cl[2 * j2 + e], cx = e ? cv.y : cv.x;
+          const float s = hi + cx;
+          const float bb = s - hi;
+          const float err = (hi - (s - bb)) + (cx - bb);
+          const float l2 = lo + err;
+          const float c = s + l2;
+          I.C_hi[rbase + x] = c;
+          I.C_lo[rbase + x] = l2 - (c - s);
+          float gs = g_of_r<float>(I.gkind, us[x]);
+          if (I.F) gs += I.fsc * I.F[rbase + x];
+          const float gg = tau2 * gs;
+          b[e] = I.first ? tau * ps[x] + 0.5f * (c + gg) : c + gg;
+        }
+      }
+      sm[pad32(n)] = make_float2(b[0], b[1]);
     }
-    sm[pad32(n)] = make_float2(b0, b1);
   }
   __syncthreads();
   if constexpr (DENSE) {

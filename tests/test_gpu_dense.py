@@ -58,10 +58,10 @@ def test_dense_setup_requires_the_dense_form(S):
         with pytest.raises(S.SadiError) as ei:
             s.sadi_get_setup(4)
         assert ei.value.status == S.SADI_ESTATE
-    with S.Sadi(4097, 1.5, 1.0, 1e-3) as s:
+    with S.Sadi(15, 1.5, 1.0, 0.1) as s:
         with pytest.raises(S.SadiError) as ei:
-            s.set_options(0, S.SADI_PREC_FP32_DENSE)
-        assert ei.value.status == S.SADI_EUNSUPPORTED
+            s.set_options(0, 7)
+        assert ei.value.status == S.SADI_EINVAL
 
 
 @pytest.mark.parametrize("N,alpha,g", [(1, 1.5, 1), (2, 1.3, 2), (5, 1.9, 0), (8, 1.6, 1), (9, 1.4, 2),

@@ -51,6 +51,7 @@ def _mode_run(S, N, prec, k, l, kappa, tau, steps, c0=0.7, d0=-0.4):
 
 
 @pytest.mark.parametrize("N,prec_name,k,l", [(8191, "SADI_PREC_FP32", 3, 5), (8191, "SADI_PREC_FP32", 40, 7),
+                                             (8191, "SADI_PREC_FP32_DENSE", 5, 3),
                                              (4095, "SADI_PREC_FP32_DENSE", 3, 5),
                                              (4095, "SADI_PREC_FP64", 11, 2)])
 def test_alpha2_sine_mode_at_full_size(S, N, prec_name, k, l):
