@@ -9,22 +9,24 @@
 // tiles.  Per-element representation error of a pair is <= 2^-16 relative, so
 // ACC carries about 2^-16 relative error on top of FP32 accumulation.
 //
-// One CTA computes one 128 x 256 output tile with 8 warps:
+// Persistent: one CTA per SM (at most one per tile) walks the 128 x 256
+// output tiles of all problems of the launch, 10 warps:
 //   * thread 0 streams 64-wide K blocks of A_hi, A_lo (128 rows) and B_hi,
 //     B_lo (256 rows) with TMA (cp.async.bulk.tensor, 128-byte swizzle) into
-//     a 2-stage ring guarded by mbarriers;
+//     a 2-stage ring guarded by mbarriers, continuing across tiles;
 //   * thread 32 issues tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator
-//     of 128 lanes x 256 columns in tensor memory) and returns each stage to
-//     the producer with tcgen05.commit;
-//   * all 8 warps read the accumulator back (tcgen05.ld 32x32b; warp w takes
-//     lanes 32 (w % 4) .. +31 and column half w / 4), transpose 32 x 32
-//     blocks through shared memory and run the epilogue of the launch (plain
-//     store, or the two fused sweep epilogues of the dense S-ADI step) with
-//     coalesced global accesses.
-// A batch of independent problems of equal padded size runs as blockIdx.z.
+//     of 128 lanes x 256 columns in tensor memory) into one of two
+//     accumulators (the 512 TMEM columns), returns each stage to the producer
+//     with tcgen05.commit and signals the finished accumulator;
+//   * 8 epilogue warps drain the other accumulator meanwhile (tcgen05.ld
+//     32x32b; a warp takes the lane quarter 32 (w % 4) .. +31 and one column
+//     half), transpose 32 x 32 blocks through shared memory and run the
+//     epilogue of the launch (plain store, or the two fused sweep epilogues of
+//     the dense S-ADI step) with coalesced global accesses.
 // Every mbarrier wait is bounded (about 1 s of %globaltimer); on expiry the
-// CTA sets *err, waits (bounded) for the copies it issued, frees its tensor
-// memory and returns.
+// CTA sets *err, the other roles stop at their next wait, the producer waits
+// (bounded) for the copies it issued, all MMAs are waited for, and the
+// tensor memory is freed before the CTA returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -45,7 +47,6 @@ constexpr int A_TILE = BM * BK * 2;                    // 16 KB
 constexpr int B_TILE = BN * BK * 2;                    // 32 KB
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // 96 KB
 constexpr int TMEM_COLS = 256;
-constexpr size_t SMEM_BYTES = (size_t)STAGES * STAGE_BYTES + 1024 + 128;
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -219,31 +220,84 @@ __device__ __forceinline__ void epilogue_block(const TcEpi& e, int rowbase, int 
   __syncwarp();
 }
 
-__global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int* err) {
+// Wait for a phase like mbar_wait, but give up at once when another role of
+// the CTA has aborted, and abort the CTA when the time limit runs out.
+__device__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtimer();
+  while (!mbar_try(bar, parity)) {
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > WAIT_LIMIT_NS) {
+      *abort_flag = 1;
+      return false;
+    }
+  }
+  return true;
+}
+
+// Tile t of the launch -> problem z and tile origin (m0, n0).  Tiles are
+// numbered problem by problem; inside a problem in groups of kGroupM tile
+// rows, column-major within a group, so that the tiles in flight at one time
+// share A and B panels in L2.
+constexpr int kGroupM = 8;
+__device__ __forceinline__ void tile_coords(const TcBatch& bt, int t, int* z, int* m0, int* n0) {
+  int k = 0;
+  for (; k < bt.count - 1; ++k) {
+    const int nt = bt.in[k].tiles_m * bt.in[k].tiles_n;
+    if (t < nt) break;
+    t -= nt;
+  }
+  const int tm = bt.in[k].tiles_m, tn = bt.in[k].tiles_n;
+  const int per_group = kGroupM * tn;
+  const int first_m = (t / per_group) * kGroupM;
+  const int gsz = min(tm - first_m, kGroupM);
+  const int local = t % per_group;
+  *z = k;
+  *m0 = (first_m + local % gsz) * BM;
+  *n0 = (local / gsz) * BN;
+}
+
+// Persistent kernel: one CTA per SM walks the tiles t = blockIdx.x,
+// blockIdx.x + gridDim.x, ...  Warp 0 (one thread) streams operand blocks by
+// TMA through the stage ring, warp 1 (one thread) issues the MMAs into one
+// of two TMEM accumulators (columns 0-255 and 256-511) and signals tmem_full;
+// warps 2-9 run the epilogue of the other accumulator meanwhile (two warps
+// per TMEM lane quarter, one per column half) and free it through tmem_empty.  The ring and the accumulator pair carry over from
+// tile to tile.
+constexpr int EPI_WARPS = 8;
+constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
+constexpr size_t EPI_BYTES = (size_t)EPI_WARPS * 32 * EPI_LD * sizeof(float);
+constexpr size_t PSMEM_BYTES = (size_t)STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 128;
+
+__global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int total, int* err) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  const TcInst& in = bt.in[blockIdx.z];
-  if ((int)blockIdx.x >= in.tiles_n || (int)blockIdx.y >= in.tiles_m) return;   // beyond this problem
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
-  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES);
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  float* epi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
+  uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES + EPI_BYTES);
+  // bars: full[STAGES], empty[STAGES], tmem_full[2], tmem_empty[2], mma_done
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
-  const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES), tfull = su32(bars + 2 * STAGES);
+  const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
+  const uint32_t tfull0 = su32(bars + 2 * STAGES), tempty0 = su32(bars + 2 * STAGES + 2);
+  const uint32_t mdone = su32(bars + 2 * STAGES + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
-  const int nk = in.K / BK;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(full0 + 8 * s, 1);
       mbar_init(empty0 + 8 * s, 1);
     }
-    mbar_init(tfull, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(tfull0 + 8 * b, 1);
+      mbar_init(tempty0 + 8 * b, EPI_WARPS);
+    }
+    mbar_init(mdone, 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(tmem_slot)),
-                 "r"(TMEM_COLS)
+                 "r"(2 * TMEM_COLS)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -252,80 +306,111 @@ __global__ void __launch_bounds__(256, 1) k_tc_gemm(const __grid_constant__ TcBa
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  if (warp == 0 && lane == 0) {
-    // ---- TMA producer ----
-    int issued = 0;
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      const uint32_t use = (uint32_t)(kb / STAGES);
-      if (kb >= STAGES && !mbar_wait(empty0 + 8 * s, (use - 1) & 1u)) {
-        *abort_flag = 1;
-        break;
-      }
-      if (*abort_flag) break;
-      uint8_t* st = base + s * STAGE_BYTES;
-      mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
-      tma_load_2d(su32(st), &in.a_hi, kb * BK, m0, full0 + 8 * s);
-      tma_load_2d(su32(st + A_TILE), &in.a_lo, kb * BK, m0, full0 + 8 * s);
-      tma_load_2d(su32(st + 2 * A_TILE), &in.b_hi, kb * BK, n0, full0 + 8 * s);
-      tma_load_2d(su32(st + 2 * A_TILE + B_TILE), &in.b_lo, kb * BK, n0, full0 + 8 * s);
-      issued = kb + 1;
-    }
-    if (*abort_flag) {
-      // the copies already issued must land before the CTA may exit
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        (void)mbar_wait(full0 + 8 * (kb % STAGES), (uint32_t)(kb / STAGES) & 1u);
-    }
-  } else if (warp == 1 && lane == 0) {
-    // ---- MMA issuer ----
-    constexpr uint32_t idesc = idesc_bf16(BM, BN);
-    for (int kb = 0; kb < nk; ++kb) {
-      const int s = kb % STAGES;
-      if (!mbar_wait(full0 + 8 * s, (uint32_t)(kb / STAGES) & 1u) || *abort_flag) {
-        *abort_flag = 1;
-        break;
-      }
-      tc_fence_after();
-      const uint32_t st = su32(base + s * STAGE_BYTES);
-      const uint64_t a_hi = sw128_desc(st), a_lo = sw128_desc(st + A_TILE);
-      const uint64_t b_hi = sw128_desc(st + 2 * A_TILE), b_lo = sw128_desc(st + 2 * A_TILE + B_TILE);
-#pragma unroll
-      for (int p = 0; p < 3; ++p) {
-        const uint64_t a = (p < 2) ? a_hi : a_lo;
-        const uint64_t b = (p == 1) ? b_lo : b_hi;
-#pragma unroll
-        for (int k = 0; k < BK / 16; ++k) {
-          // K step of 16 BF16 = 32 bytes inside the 128-byte swizzled row
-          mma_bf16(tmem, a + (uint64_t)(2 * k), b + (uint64_t)(2 * k), idesc, (kb | p | k) != 0 ? 1u : 0u);
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---- TMA producer ----
+      int it = 0;
+      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+        int z, m0, n0;
+        tile_coords(bt, t, &z, &m0, &n0);
+        const TcInst& in = bt.in[z];
+        const int nk = in.K / BK;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          const uint32_t use = (uint32_t)(it / STAGES);
+          if (it >= STAGES && !wait_or_abort(empty0 + 8 * s, (use - 1) & 1u, abort_flag)) break;
+          uint8_t* st = base + s * STAGE_BYTES;
+          mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
+          tma_load_2d(su32(st), &in.a_hi, kb * BK, m0, full0 + 8 * s);
+          tma_load_2d(su32(st + A_TILE), &in.a_lo, kb * BK, m0, full0 + 8 * s);
+          tma_load_2d(su32(st + 2 * A_TILE), &in.b_hi, kb * BK, n0, full0 + 8 * s);
+          tma_load_2d(su32(st + 2 * A_TILE + B_TILE), &in.b_lo, kb * BK, n0, full0 + 8 * s);
         }
       }
-      mma_commit(empty0 + 8 * s);
+      if (*abort_flag) {
+        // the copies issued last must land before the CTA may exit
+        for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
+          (void)mbar_wait(full0 + 8 * (j % STAGES), (uint32_t)(j / STAGES) & 1u);
+      }
     }
-    mma_commit(tfull);
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---- MMA issuer ----
+      constexpr uint32_t idesc = idesc_bf16(BM, BN);
+      int it = 0, tl = 0;
+      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++tl) {
+        int z, m0, n0;
+        tile_coords(bt, t, &z, &m0, &n0);
+        const int nk = bt.in[z].K / BK;
+        const int b = tl & 1;
+        const uint32_t ub = (uint32_t)(tl >> 1);
+        if (tl >= 2 && !wait_or_abort(tempty0 + 8 * b, (ub - 1) & 1u, abort_flag)) break;
+        tc_fence_after();
+        const uint32_t acc = tmem + (uint32_t)(b * TMEM_COLS);
+        bool ok = true;
+        for (int kb = 0; kb < nk; ++kb, ++it) {
+          const int s = it % STAGES;
+          if (!wait_or_abort(full0 + 8 * s, (uint32_t)(it / STAGES) & 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t st = su32(base + s * STAGE_BYTES);
+          const uint64_t a_hi = sw128_desc(st), a_lo = sw128_desc(st + A_TILE);
+          const uint64_t b_hi = sw128_desc(st + 2 * A_TILE), b_lo = sw128_desc(st + 2 * A_TILE + B_TILE);
+#pragma unroll
+          for (int p = 0; p < 3; ++p) {
+            const uint64_t a = (p < 2) ? a_hi : a_lo;
+            const uint64_t bb = (p == 1) ? b_lo : b_hi;
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+              mma_bf16(acc, a + (uint64_t)(2 * k), bb + (uint64_t)(2 * k), idesc, (kb | p | k) != 0 ? 1u : 0u);
+          }
+          mma_commit(empty0 + 8 * s);
+        }
+        mma_commit(tfull0 + 8 * b);
+        if (!ok) break;
+      }
+      // every MMA issued must have finished before the tensor memory is freed
+      mma_commit(mdone);
+      (void)mbar_wait(mdone, 0);
+    }
+  } else {
+    // ---- epilogue warps: TMEM lane quarter = warp % 4, column half ----
+    const int quarter = warp & 3, half = (warp - 2) >> 2;
+    float* tile = epi + (warp - 2) * 32 * EPI_LD;
+    int tl = 0;
+    for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+      int z, m0, n0;
+      tile_coords(bt, t, &z, &m0, &n0);
+      const int b = tl & 1;
+      const uint32_t ub = (uint32_t)(tl >> 1);
+      if (!wait_or_abort(tfull0 + 8 * b, ub & 1u, abort_flag) || *abort_flag) break;
+      tc_fence_after();
+      const TcInst& in = bt.in[z];
+      const uint32_t acc = tmem + (uint32_t)(b * TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);
+#pragma unroll 1
+      for (int c = 0; c < BN / 64; ++c) {
+        const int cc = half * (BN / 64) + c;
+        uint32_t r[32];
+        tmem_ld32(acc + (uint32_t)(cc * 32), r);
+        epilogue_block(in.e, m0 + quarter * 32, n0 + cc * 32, r, tile, lane);
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(tempty0 + 8 * b) : "memory");
+    }
   }
   __syncwarp();
-  // ---- epilogue: tensor memory -> registers -> shared -> global ----
-  // warp w reads accumulator lanes 32 (w % 4) .. +31 (its tcgen05.ld lane
-  // quarter) and the column half w / 4; the pipeline buffers are free now
-  const bool done = mbar_wait(tfull, 0);
-  tc_fence_after();
-  if (done && !*abort_flag) {
-    float* tile = reinterpret_cast<float*>(base) + warp * 32 * EPI_LD;
-    const int quarter = warp & 3, half = warp >> 2;
-#pragma unroll 1
-    for (int c = 0; c < BN / 64; ++c) {
-      const int cc = half * (BN / 64) + c;
-      uint32_t r[32];
-      tmem_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(cc * 32), r);
-      epilogue_block(in.e, m0 + quarter * 32, n0 + cc * 32, r, tile, lane);
-    }
-  } else if (lane == 0) {
-    atomicExch(in.e.err ? in.e.err : err, 1);
+  if (*abort_flag && threadIdx.x == 64) {
+    int z, m0, n0;
+    tile_coords(bt, blockIdx.x, &z, &m0, &n0);
+    atomicExch(bt.in[z].e.err ? bt.in[z].e.err : err, 1);
   }
   tc_fence_before();
   __syncthreads();
   if (warp == 0) {
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS) : "memory");
   }
 }
 
@@ -389,21 +474,26 @@ cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, cons
 
 cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
   if (b.count < 1 || b.count > kTcMaxBatch) return cudaErrorInvalidValue;
-  int tm = 0, tn = 0;
+  int total = 0;
   for (int k = 0; k < b.count; ++k) {
     const TcInst& in = b.in[k];
     if (in.K <= 0 || in.K % BK || in.tiles_m < 1 || in.tiles_n < 1) return cudaErrorInvalidValue;
-    tm = in.tiles_m > tm ? in.tiles_m : tm;
-    tn = in.tiles_n > tn ? in.tiles_n : tn;
+    total += in.tiles_m * in.tiles_n;
   }
-  static bool attr = false;
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM_BYTES);
-    if (e != cudaSuccess) return e;
-    attr = true;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PSMEM_BYTES);
+    if (e != cudaSuccess) {
+      sms = 0;
+      return e;
+    }
   }
-  const dim3 grid(tn, tm, b.count);
-  k_tc_gemm<<<grid, 256, SMEM_BYTES, st>>>(b, err);
+  const int grid = total < sms ? total : sms;
+  k_tc_gemm<<<grid, GEMM_THREADS, PSMEM_BYTES, st>>>(b, total, err);
   return cudaGetLastError();
 }
 
