@@ -65,7 +65,10 @@ typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2 } sadi_g
  *   (E and the right-hand side split into BF16 hi + lo pairs, three products,
  *   FP32 accumulation).  E comes from the FP64 generator of the N x N matrix.
  *   Any N up to 8192 (E and the operands take 12 N_p^2 bytes, N_p = N rounded
- *   up to 256). */
+ *   up to 256).  Its error is relative to E, whose size grows with
+ *   s = kappa tau^2 / (2 h^alpha): near-FP32 while s a_0 is small (a_0 the
+ *   first 1D weight), visibly coarser once E is O(1) (s a_0 of order 1 or
+ *   more); prefer SADI_PREC_FP32 there. */
 typedef enum { SADI_PREC_FP64 = 0, SADI_PREC_FP32 = 1, SADI_PREC_FP32_DENSE = 2 } sadi_prec;
 
 /* Create a context for N interior points per direction, fractional order
@@ -129,6 +132,21 @@ sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
  * waits).  Results are identical to stepping each context alone. */
 sadi_status sadi_batch_step(sadi_ctx **ctxs, int count, int nsteps);
 
+/* Checkpoint and resume (no paper counterpart).  sadi_save_state writes the
+ * step state of an initialised context into buf (host memory of *bytes
+ * bytes, owned by the caller): a header (N, precision, g, alpha, kappa, tau,
+ * domain, step counter n) followed by the device arrays the next step reads
+ * (FP64: u^n, u^{n-1}, phi2; FP32 forms: u_hi, u_lo, the increment, the
+ * remainder pair, phi2).  With buf NULL it only stores the size needed in
+ * *bytes; a buffer that is too small returns SADI_EINVAL with the size in
+ * *bytes.  sadi_load_state restores such a blob into a context created with
+ * the same N, alpha, kappa, tau and domain and set to the same g and
+ * precision (SADI_EINVAL otherwise); the context continues exactly as the
+ * saved one would (bitwise).  Both are synchronous on the context's stream.
+ * The blob is tied to this build's layout; it is not an interchange format. */
+sadi_status sadi_save_state(sadi_ctx *ctx, void *buf, size_t *bytes);
+sadi_status sadi_load_state(sadi_ctx *ctx, const void *buf, size_t bytes);
+
 /* CUDA-graph replay of batched steps (no paper counterpart; it removes the
  * per-step host launch cost when many small instances advance together).
  * sadi_graph_create captures nsteps >= 1 steps of the count contexts, issued
@@ -155,9 +173,10 @@ void sadi_graph_destroy(sadi_graph *graph);
 /* Autotuner (no paper counterpart): for the count contexts, grouped by N,
  * time the candidate step forms on zero data with the group stepped as
  * sadi_batch_step steps it (up to 32 contexts per group) -- SADI_PREC_FP32
- * (Gohberg-Semencul FFT sweeps) and, unless flags bit 0 is set,
- * SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, on
- * the shared-memory FFT engine (N' > 1024), the work decomposition of
+ * (Gohberg-Semencul FFT sweeps) and, unless flags bit 0 is set or
+ * s a_0 > 0.2 (the dense form's accuracy limit above),
+ * SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, on the
+ * shared-memory FFT engine (N' > 1024), the work decomposition of
  * sadi_set_tiles by coordinate descent.  Each context is left with g, the
  * fastest precision and tiles of its group, uninitialised (call
  * sadi_set_initial next).  Must precede sadi_set_initial and

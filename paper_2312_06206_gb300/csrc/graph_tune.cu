@@ -139,6 +139,9 @@ struct Cand {
   Tiles t;
 };
 
+// largest s a_0 for which the autotuner offers the dense form
+constexpr double kDenseMaxSA0 = 0.2;
+
 // ms per batched step of the group in its current configuration (zero data:
 // the step's cost does not depend on the values)
 sadi_status time_group(std::vector<sadi_ctx*>& grp, int reps, double* ms) {
@@ -212,8 +215,14 @@ sadi_status sadi_autotune(sadi_ctx** ctxs, int count, int g, int flags) {
     std::vector<sadi_ctx*> grp(all.begin(), all.begin() + std::min(all.size(), cap));
     const int N = kv.first, Np = grp[0]->g.Np;
     std::vector<int> precs{SADI_PREC_FP32};
-    if (!(flags & 1)) precs.push_back(SADI_PREC_FP32_DENSE);
-    std::string log = fmt("N=%.0f N'=%.0f batch=%.0f:", N, Np, (double)grp.size());
+    // the dense form's split-BF16 error scales with E = H^-1 - I, i.e. with
+    // s a_0 (s = kappa tau^2 / (2 h^alpha)); it is offered only while E is small
+    double a0 = 0.0;
+    if (cudaMemcpy(&a0, grp[0]->a1, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_fail(grp[0], cudaErrorUnknown, "reading a_0");
+    const bool dense_ok = grp[0]->s * a0 <= kDenseMaxSA0;
+    if (!(flags & 1) && dense_ok) precs.push_back(SADI_PREC_FP32_DENSE);
+    std::string log = fmt("N=%.0f N'=%.0f batch=%.0f s*a0=%.3g:", N, Np, (double)grp.size(), grp[0]->s * a0);
     Cand best{SADI_PREC_FP32, Tiles{0, 0, 0}};
     double best_ms = 1e30;
     for (int prec : precs) {

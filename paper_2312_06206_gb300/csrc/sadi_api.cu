@@ -885,3 +885,107 @@ extern "C" sadi_status sadi_step_noalloc(sadi_ctx* c, const double* u_prev, cons
      "step launch");
   return SADI_OK;
 }
+
+// ---- checkpoint / resume -----------------------------------------------------
+
+namespace {
+
+struct StateHeader {
+  char magic[8];          // "SADIST01"
+  int N, Np, prec, gkind, cur, initialized;
+  long long n;
+  double alpha, kappa, tau, a, b;
+  int narrays;            // arrays of N*N elements that follow
+  int esz;                // bytes per element of the state arrays
+};
+
+// device arrays that make up the step state of c, in blob order
+int state_arrays(sadi_ctx* c, void** out) {
+  int k = 0;
+  if (c->prec == SADI_PREC_FP64) {
+    out[k++] = c->ubuf[c->cur];        // u^n
+    out[k++] = c->ubuf[1 - c->cur];    // u^{n-1}
+    out[k++] = c->phi2;
+  } else {
+    out[k++] = c->ubuf[0];             // u_hi
+    out[k++] = c->ulo;                 // u_lo
+    out[k++] = c->ubuf[1];             // d = u^n - u^{n-1}
+    out[k++] = c->Chi;                 // remainder pair
+    out[k++] = c->Clo;
+    out[k++] = c->phi2;
+  }
+  return k;
+}
+
+}  // namespace
+
+extern "C" sadi_status sadi_save_state(sadi_ctx* c, void* buf, size_t* bytes) {
+  if (!c || !bytes) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_save_state before sadi_set_initial");
+  void* arr[8];
+  const int na = state_arrays(c, arr);
+  const size_t es = c->prec == SADI_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  const size_t need = sizeof(StateHeader) + (size_t)na * nn * es;
+  if (!buf) {
+    *bytes = need;
+    return SADI_OK;
+  }
+  if (*bytes < need) {
+    *bytes = need;
+    return fail(c, SADI_EINVAL, "sadi_save_state: buffer too small (size returned in *bytes)");
+  }
+  StateHeader h{};
+  std::memcpy(h.magic, "SADIST01", 8);
+  h.N = c->g.N;
+  h.Np = c->g.Np;
+  h.prec = c->prec;
+  h.gkind = c->gkind;
+  h.cur = 0;
+  h.initialized = 1;
+  h.n = c->n;
+  h.alpha = c->alpha;
+  h.kappa = c->kappa;
+  h.tau = c->tau;
+  h.a = c->a;
+  h.b = c->b;
+  h.narrays = na;
+  h.esz = (int)es;
+  std::memcpy(buf, &h, sizeof h);
+  char* p = static_cast<char*>(buf) + sizeof h;
+  for (int k = 0; k < na; ++k, p += nn * es)
+    CK(cudaMemcpyAsync(p, arr[k], nn * es, cudaMemcpyDeviceToHost, c->stream), "copy state");
+  CK(cudaStreamSynchronize(c->stream), "sadi_save_state");
+  *bytes = need;
+  return SADI_OK;
+}
+
+extern "C" sadi_status sadi_load_state(sadi_ctx* c, const void* buf, size_t bytes) {
+  if (!c || !buf) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  StateHeader h;
+  if (bytes < sizeof h) return fail(c, SADI_EINVAL, "sadi_load_state: blob too small");
+  std::memcpy(&h, buf, sizeof h);
+  if (std::memcmp(h.magic, "SADIST01", 8) != 0) return fail(c, SADI_EINVAL, "sadi_load_state: not a state blob");
+  if (h.N != c->g.N || h.prec != c->prec || h.gkind != c->gkind || h.alpha != c->alpha || h.kappa != c->kappa ||
+      h.tau != c->tau || h.a != c->a || h.b != c->b)
+    return fail(c, SADI_EINVAL,
+                "sadi_load_state: the blob was saved by a context with another N, alpha, kappa, tau, domain, g or "
+                "precision");
+  void* arr[8];
+  const int na = state_arrays(c, arr);
+  const size_t es = c->prec == SADI_PREC_FP64 ? sizeof(double) : sizeof(float);
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  if (h.narrays != na || h.esz != (int)es || bytes < sizeof h + (size_t)na * nn * es || h.n < 0)
+    return fail(c, SADI_EINVAL, "sadi_load_state: blob size or layout does not match");
+  c->cur = 0;   // saved in canonical order: arr[0] = u^n
+  state_arrays(c, arr);
+  const char* p = static_cast<const char*>(buf) + sizeof h;
+  for (int k = 0; k < na; ++k, p += nn * es)
+    CK(cudaMemcpyAsync(arr[k], p, nn * es, cudaMemcpyHostToDevice, c->stream), "copy state");
+  CK(cudaStreamSynchronize(c->stream), "sadi_load_state");
+  c->n = h.n;
+  c->initialized = true;
+  return SADI_OK;
+}

@@ -44,6 +44,8 @@ _SIGS = {
     "sadi_destroy": (None, [C.c_void_p]),
     "sadi_gemm_split_bf16": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
                                         C.c_void_p]),
+    "sadi_save_state": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_size_t)]),
+    "sadi_load_state": (C.c_int, [C.c_void_p, C.c_void_p, C.c_size_t]),
     "sadi_graph_create": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
     "sadi_graph_launch": (C.c_int, [C.c_void_p, C.c_int]),
     "sadi_graph_destroy": (None, [C.c_void_p]),
@@ -249,6 +251,17 @@ class Sadi:
         """One step on caller-owned device buffers (N*N doubles each); no allocation."""
         _check(lib().sadi_step_noalloc(self.ctx, C.c_void_p(u_prev_ptr), C.c_void_p(u_cur_ptr),
                                        C.c_void_p(u_next_ptr), int(n)), self.ctx)
+
+    def sadi_save_state(self) -> bytes:
+        n = C.c_size_t(0)
+        _check(lib().sadi_save_state(self.ctx, None, C.byref(n)), self.ctx)
+        buf = C.create_string_buffer(n.value)
+        _check(lib().sadi_save_state(self.ctx, buf, C.byref(n)), self.ctx)
+        return buf.raw[:n.value]
+
+    def sadi_load_state(self, blob: bytes):
+        buf = C.create_string_buffer(bytes(blob), len(blob))
+        _check(lib().sadi_load_state(self.ctx, buf, len(blob)), self.ctx)
 
     def sadi_tuning_log(self) -> str:
         return lib().sadi_tuning_log(self.ctx).decode()
