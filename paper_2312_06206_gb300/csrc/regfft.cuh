@@ -152,12 +152,13 @@ struct RegFFT {
   }
 
   // Forward transform; ends with the buffer free (after a __syncthreads()).
+  // tw1 may point to global or shared memory.
   __device__ static __forceinline__ void fwd(cx<T>* x, cx<T>* sm, int t, const cx<T>* __restrict__ tw1) {
     dft_fwd<T, E>(x);
     static_for<0, E>([&](auto pc) {
       constexpr int p = decltype(pc)::value;
       constexpr int k1 = cbrev(p, LOGE);
-      sm[k1 * ROW + t] = cmul(x[p], __ldg(&tw1[k1 * TT + t]));
+      sm[k1 * ROW + t] = cmul(x[p], tw1[k1 * TT + t]);
     });
     __syncthreads();
     static_for<0, KPT>([&](auto jc) {
@@ -185,7 +186,7 @@ struct RegFFT {
     static_for<0, E>([&](auto pc) {
       constexpr int p = decltype(pc)::value;
       constexpr int k1 = cbrev(p, LOGE);
-      x[p] = cmulc(sm[k1 * ROW + t], __ldg(&tw1[k1 * TT + t]));
+      x[p] = cmulc(sm[k1 * ROW + t], tw1[k1 * TT + t]);
     });
     __syncthreads();
     dft_inv<T, E>(x);

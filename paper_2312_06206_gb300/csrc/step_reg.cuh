@@ -47,9 +47,10 @@ struct RowCfg {
   using F = rf::RegFFT<float, LOGL>;
   static constexpr int VB = BLOCK / F::TT;                    // vectors (rows) per block
   static constexpr int SMV = vec_smem<LOGL>(F::TT & 15);      // transform buffer (float2)
-  static constexpr int STG = F::L;                            // staged u / phi2 row (floats)
-  static constexpr size_t bytes_r2c = (size_t)VB * SMV * sizeof(float2);
-  static constexpr size_t bytes_solve = (size_t)VB * (SMV * sizeof(float2) + 2 * STG * sizeof(float));
+  static constexpr int STG = F::L;                            // staged u row (floats)
+  static constexpr size_t tw_bytes = 2 * (size_t)F::L * sizeof(float2);   // tw1 and tw[0 .. L) staged
+  static constexpr size_t bytes_r2c = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
+  static constexpr size_t bytes_solve = (size_t)VB * (SMV * sizeof(float2) + STG * sizeof(float)) + tw_bytes;
 };
 template <int LOGL, int BLOCK>
 struct ColCfg {
@@ -60,8 +61,12 @@ struct ColCfg {
   // bank pairs of a half-warp distinct
   static constexpr int SMV = vec_smem<LOGL>(CT >= 16 ? 1 : 16 / CT);
   static constexpr int STG = F::L;                            // staged state column (floats)
-  static constexpr size_t bytes_conv = (size_t)CT * SMV * sizeof(float2) + (size_t)BLOCK * F::E * sizeof(float);
-  static constexpr size_t bytes_solve = (size_t)CT * (SMV * sizeof(float2) + 3 * STG * sizeof(float));
+  // FFT buffers, the parked symbol values, and the twiddle tables tw1 and
+  // tw[0 .. L) staged once per block
+  static constexpr size_t bytes_conv =
+      (size_t)CT * SMV * sizeof(float2) + (size_t)BLOCK * F::E * sizeof(float) + 2 * (size_t)F::L * sizeof(float2);
+  static constexpr size_t bytes_solve =
+      (size_t)CT * (SMV * sizeof(float2) + 3 * STG * sizeof(float)) + 2 * (size_t)F::L * sizeof(float2);
 };
 
 // Asynchronous global -> shared copies (Ampere+ cp.async); a false predicate
@@ -79,8 +84,21 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred)
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// The twiddle tables tw1 (two-level FFT) and tw[0 .. L) staged into shared
+// memory (one cp.async group): the transforms read them in their inner
+// stages, where global (L1) loads would stall the few resident warps.
+template <int LOGL, int BLOCK>
+__device__ __forceinline__ void stage_twiddles(const RegInst& I, float2* s_tw1, float2* s_tw) {
+  constexpr int L = 1 << LOGL;
+  for (int e = threadIdx.x; e < L; e += BLOCK) {
+    cp_async8(&s_tw1[e], I.tw1 + e, true);
+    cp_async8(&s_tw[e], I.tw + e, true);
+  }
+}
+
 // Gohberg-Semencul core (Algorithm 1 on the bordered matrix): x natural
-// (x[q] = Q v1 at t + TT q) -> x natural (vhat).  lam tables natural order.
+// (x[q] = Q v1 at t + TT q) -> x natural (vhat).  lam tables natural order
+// (global memory); tw1 and tw may be in global or shared memory.
 template <int LOGL>
 __device__ __forceinline__ void gs_reg(float2* x, float2* sm, int t, const float2* __restrict__ tw1,
                                        const float2* __restrict__ tw, const float2* __restrict__ lam_s,
@@ -100,7 +118,7 @@ __device__ __forceinline__ void gs_reg(float2* x, float2* sm, int t, const float
     if (round == 0) {
       static_for<0, F::E>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
-        x[q] = cmulc(x[q], __ldg(&tw[t + F::TT * q]));       // Q^H
+        x[q] = cmulc(x[q], tw[t + F::TT * q]);       // Q^H
       });
     }
   }
@@ -160,6 +178,10 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ 
   const int row = blockIdx.x * C::VB + v;
   const bool valid = row < N;
   float2* sm = reinterpret_cast<float2*>(smem_raw) + v * C::SMV;
+  float2* s_tw1 = reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV;
+  float2* s_tw = s_tw1 + F::L;
+  stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
+  cp_async_commit();
   // the increment d^n = u^n - u^{n-1} (zero before the first step): the
   // remainder is advanced incrementally
   const float* ur = I.u_d + (size_t)(valid ? row : 0) * N;
@@ -171,7 +193,9 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ 
     const float b = (valid && 2 * n + 1 < N) ? ur[2 * n + 1] : 0.f;
     x[q] = make_float2(a, b);
   });
-  F::fwd(x, sm, t, I.tw1);
+  cp_async_wait_all();
+  __syncthreads();
+  F::fwd(x, sm, t, s_tw1);
   store_freq<LOGL>(x, sm, t);
   __syncthreads();
   if (!valid) return;
@@ -183,7 +207,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ 
     const float2 Zc = cconj(sm[pad32((F::L - k) & (F::L - 1))]);
     const float2 Ev = cscale(cadd(Z, Zc), 0.5f);
     const float2 Ov = cscale(cmul_mi(csub(Z, Zc)), 0.5f);
-    srow[k] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(__ldg(&I.tw[k]), Ov));
+    srow[k] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(s_tw[k], Ov));
   }
 }
 
@@ -206,6 +230,15 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__
   const int slot = (item <= 1 || !valid) ? 0 : item - 1;
   float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
   float* ls = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::CT * C::SMV);
+  // twiddles from shared memory: the transforms read them in their inner
+  // stages, where global (L1) loads would stall the few resident warps
+  float2* s_tw1 = reinterpret_cast<float2*>(ls + BLOCK * F::E);
+  float2* s_tw = s_tw1 + F::L;
+  for (int e = threadIdx.x; e < F::L; e += BLOCK) {
+    cp_async8(&s_tw1[e], I.tw1 + e, true);
+    cp_async8(&s_tw[e], I.tw + e, true);
+  }
+  cp_async_commit();
   // the column and this thread's symbol values (frequency layout) are loaded
   // together (all loads in flight), the symbol values parked in shared memory
   const float* lrow = I.lreg + ((size_t)(valid ? k1 : 0) * 2 + h) * Np;
@@ -223,16 +256,23 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__
     float2 val = x[q];
     if (item == 0) val.y = 0.f;
     else if (item == 1) val = make_float2(val.y, 0.f);
-    if (h) val = cmul(val, __ldg(&I.tw[j]));
     x[q] = val;
     ls[q * BLOCK + threadIdx.x] = lv[q];
   });
-  F::fwd(x, sm, t, I.tw1);
+  cp_async_wait_all();
+  __syncthreads();
+  if (h) {
+    static_for<0, F::E>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      x[q] = cmul(x[q], s_tw[t + F::TT * q]);
+    });
+  }
+  F::fwd(x, sm, t, s_tw1);
   static_for<0, F::E>([&](auto rc) {
     constexpr int r = decltype(rc)::value;
     x[r] = cscale(x[r], ls[r * BLOCK + threadIdx.x]);
   });
-  F::inv(x, sm, t, I.tw1);
+  F::inv(x, sm, t, s_tw1);
   store_nat<LOGL>(x, sm, t);
   __syncthreads();
   if (!valid || h != 0 || item == 1) return;
@@ -241,7 +281,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__
   for (int q = 0; q < F::E; ++q) {
     const int j = t + F::TT * q;
     if (j < N) {
-      const float2 w = __ldg(&I.tw[j]);
+      const float2 w = s_tw[j];
       const float2 y = cadd(sm[pad32(j)], cmulc(smo[pad32(j)], w));
       if (item == 0) {
         // the x-frequency N' result lives in the next item's two vectors
@@ -270,18 +310,20 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
   const bool valid = row < N;
   const int rrow = valid ? row : 0;
   float2* sm = reinterpret_cast<float2*>(smem_raw) + v * C::SMV;
-  float* us = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV) + v * 2 * C::STG;
-  float* ps = us + C::STG;
-  // stage the spectrum row, u^n row and (first step) phi2 row
+  float* us = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV) + v * C::STG;
+  float2* s_tw1 = reinterpret_cast<float2*>(
+      reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV) + C::VB * C::STG);
+  float2* s_tw = s_tw1 + F::L;
+  stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
+  // stage the spectrum row and the u^n row (the first step reads phi2 from
+  // global memory)
   const float2* srow = I.S + (size_t)rrow * Np;
   const float* ur = I.u_hi + (size_t)rrow * N;
-  const float* pr = I.phi2 + (size_t)rrow * N;
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int k = t + F::TT * q;
     cp_async8(&sm[pad32(k)], srow + k, valid);
     cp_async4(&us[k], ur + (k < N ? k : 0), valid && k < N);
-    if (I.first) cp_async4(&ps[k], pr + (k < N ? k : 0), valid && k < N);
   });
   cp_async_commit();
   cp_async_wait_all();
@@ -300,11 +342,11 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
     const int kp = Np - k;
     const float2 X = sm[pad32(k)], Xq = sm[pad32(kp)];
     const float2 Ev = cscale(cadd(X, cconj(Xq)), 0.5f);
-    const float2 Ov = cscale(cmulc(csub(X, cconj(Xq)), __ldg(&I.tw[k])), 0.5f);
+    const float2 Ov = cscale(cmulc(csub(X, cconj(Xq)), s_tw[k]), 0.5f);
     sm[pad32(k)] = cadd(Ev, cmul_pi(Ov));
     if (kp != k) {
       const float2 Eq = cscale(cadd(Xq, cconj(X)), 0.5f);
-      const float2 Oq = cscale(cmulc(csub(Xq, cconj(X)), __ldg(&I.tw[kp])), 0.5f);
+      const float2 Oq = cscale(cmulc(csub(Xq, cconj(X)), s_tw[kp]), 0.5f);
       sm[pad32(kp)] = cadd(Eq, cmul_pi(Oq));
     }
   }
@@ -312,7 +354,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
   float2 x[F::E];
   load_freq<LOGL>(x, sm, t);
   __syncthreads();
-  F::inv(x, sm, t, I.tw1);
+  F::inv(x, sm, t, s_tw1);
   store_nat<LOGL>(x, sm, t);
   __syncthreads();
   // B^n in place: sm[n] holds the convolution at 2n, 2n+1 (real view).  The
@@ -351,7 +393,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
           float gs = g_of_r<float>(I.gkind, us[x]);
           if (I.F) gs += I.fsc * I.F[rbase + x];
           const float gg = tau2 * gs;
-          b[e] = I.first ? tau * ps[x] + 0.5f * (c + gg) : c + gg;
+          b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
         }
       }
       sm[pad32(n)] = make_float2(b[0], b[1]);
@@ -378,10 +420,10 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int k = t + F::TT * q;
-    x[q] = cmul(make_float2(real_at(sm, k), real_at(sm, Np - 1 - k)), __ldg(&I.tw[k]));
+    x[q] = cmul(make_float2(real_at(sm, k), real_at(sm, Np - 1 - k)), s_tw[k]);
   });
   __syncthreads();
-  gs_reg<LOGL>(x, sm, t, I.tw1, I.tw, I.lam_s, I.lam_c);
+  gs_reg<LOGL>(x, sm, t, s_tw1, s_tw, I.lam_s, I.lam_c);
   store_nat<LOGL>(x, sm, t);
   __syncthreads();
   if (!valid) return;
@@ -421,6 +463,10 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
   float* s_hi = st;
   float* s_lo = st + C::CT * C::STG;
   float* s_d = st + 2 * C::CT * C::STG;
+  float2* s_tw1 = reinterpret_cast<float2*>(st + 3 * C::CT * C::STG);
+  float2* s_tw = s_tw1 + F::L;
+  stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
+  cp_async_commit();
   // the state column (needed at the end) is staged asynchronously; the W
   // column (needed now) is loaded straight into registers, all loads in flight
   static_for<0, F::E>([&](auto qc) {
@@ -441,12 +487,15 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
     const float b = (valid && k2 < N) ? I.W[(size_t)k2 * N + ii] : 0.f;
     x[q] = make_float2(a, b);
   });
+  // the twiddle group (committed first) has landed once at most the state
+  // group is still pending
+  asm volatile("cp.async.wait_group 1;\n" ::: "memory");
+  __syncthreads();
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
-    x[q] = cmul(x[q], __ldg(&I.tw[t + F::TT * q]));
+    x[q] = cmul(x[q], s_tw[t + F::TT * q]);
   });
-  __syncthreads();
-  gs_reg<LOGL>(x, sm, t, I.tw1, I.tw, I.lam_s, I.lam_c);
+  gs_reg<LOGL>(x, sm, t, s_tw1, s_tw, I.lam_s, I.lam_c);
   store_nat<LOGL>(x, sm, t);
   cp_async_wait_all();
   __syncthreads();
