@@ -15,7 +15,8 @@ fastest one within 1e-5 relative L2 of the FP64 path after the accuracy run
 (--acc-steps, default 1000 steps from the same data).
 
 Timing: W untimed warm-up steps, then K timed steps; each step is bracketed
-by CUDA events on the launching stream and an L2 flush (a 256 MiB write) runs
+by CUDA events on the launching stream (the FP32 forms replay a captured
+CUDA graph of one batched step) and an L2 flush (a 256 MiB write) runs
 between timed steps, outside the events (the working set, ~30 MB per
 instance, is smaller than L2).  Multi-GPU: every rank advances its own copy
 of the three instances (independent problems, no collective); value = all
@@ -646,14 +647,24 @@ def main():
             step_all(ctxs)
         if profile:
             ctxs[0].sadi_profile(True)
+        # the FP32 forms replay one captured step per launch (sadi_graph_*);
+        # the FP64 path (ping-pong state) and profiled passes launch directly
+        graph = None
+        if not profile and W > 0 and ctxs[0].sadi_get_options()[1] != S.SADI_PREC_FP64:
+            graph = S.SadiGraph(ctxs, 1)
         barrier()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
         for k in range(K):
             flush.zero_()
             evs[k][0].record(stream)
-            step_all(ctxs)
+            if graph is not None:
+                graph.launch(1)
+            else:
+                step_all(ctxs)
             evs[k][1].record(stream)
         barrier()
+        if graph is not None:
+            graph.close()
         ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
         phases = None
         if profile:
