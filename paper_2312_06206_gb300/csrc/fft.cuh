@@ -30,10 +30,17 @@
 // consecutive addresses.  A separate table tw[k] = exp(-2 pi i k / P), P = 2L,
 // provides the exp(-i pi k / L) twist of Algorithm 1 and the packing factors.
 //
-// Shared-memory layout: element i of a vector lives at i + (i >> 3) (one pad
-// slot per 8 elements), which spreads the stride-8 accesses of the span-8
-// stages over all banks.  A buffer of nvec vectors uses nvec * vec_stride(L)
-// elements.
+// Shared-memory layout (sidx, vstride): a half-warp of 16 threads reads 16
+// elements per access, at stride 1 (spans >= 128 and all staging loops), in
+// two blocks of 8 (span 64) or at stride 8 (span 8).
+//   * FP32 (8-byte elements, 16 per 128-byte bank row): element i lives at
+//     i ^ h(i >> 4) with h(x) = (x & 7) | ((x & 4) << 1), an XOR of its low
+//     four bits: every aligned run of 16 stays a permutation of itself, the two
+//     8-runs 64 apart land in different halves, and the stride-8 set spreads
+//     over all 16 positions, so none of these accesses conflicts; no padding.
+//   * FP64 (16-byte elements, accessed per quarter-warp of 8): element i lives
+//     at i + (i >> 3), one pad slot per 8 elements.
+// A buffer of nvec vectors uses nvec * vstride<T>(L) elements.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -73,6 +80,18 @@ __device__ __forceinline__ double2 cmulany(double2 a, double2 b) { return cmul(a
 
 __host__ __device__ __forceinline__ int padi(int i) { return i + (i >> 3); }
 __host__ __device__ __forceinline__ int vec_stride(int L) { return L + (L >> 3) + 2; }
+
+// Shared-memory position of element i (see the layout note above).
+template <typename T> __host__ __device__ __forceinline__ int sidx(int i);
+template <> __host__ __device__ __forceinline__ int sidx<double>(int i) { return padi(i); }
+template <> __host__ __device__ __forceinline__ int sidx<float>(int i) {
+  const int x = i >> 4;
+  return i ^ ((x & 7) | ((x & 4) << 1));
+}
+// Elements per vector buffer.
+template <typename T> __host__ __device__ __forceinline__ int vstride(int L);
+template <> __host__ __device__ __forceinline__ int vstride<double>(int L) { return vec_stride(L); }
+template <> __host__ __device__ __forceinline__ int vstride<float>(int L) { return L + 2; }
 
 __device__ __forceinline__ int brev(int p, int logL) {
   return (int)(__brev((unsigned)p) >> (32 - logL));
@@ -250,7 +269,7 @@ __device__ __forceinline__ void fft_stage(cx<T>* __restrict__ buf, int logL, int
     cx<T>* p = buf + v * vstride;
     cx<T> x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = p[padi(base + (q << logm))];
+    for (int q = 0; q < R; ++q) x[q] = p[sidx<T>(base + (q << logm))];
     if (!FWD && j != 0) {
 #pragma unroll
       for (int q = 1; q < R; ++q) x[q] = cmulc(x[q], __ldg(&stw[((q - 1) << logm) + j]));
@@ -261,7 +280,7 @@ __device__ __forceinline__ void fft_stage(cx<T>* __restrict__ buf, int logL, int
       for (int q = 1; q < R; ++q) x[q] = cmul(x[q], __ldg(&stw[((q - 1) << logm) + j]));
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q) p[padi(base + (q << logm))] = x[q];
+    for (int q = 0; q < R; ++q) p[sidx<T>(base + (q << logm))] = x[q];
   }
 }
 
@@ -308,17 +327,17 @@ __device__ void fused8(cx<T>* __restrict__ buf, int logL, int nvec, int vs, cons
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
     const int v = t >> lognb;
     const int base = (t & ((1 << lognb) - 1)) << 3;
-    cx<T>* p = buf + v * vs + padi(base);     // 8 consecutive elements share one pad group
+    cx<T>* p = buf + v * vs;
     const M* mm = mult + (size_t)v * mstride + base;
     cx<T> x[8];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = p[q];
+    for (int q = 0; q < 8; ++q) x[q] = p[sidx<T>(base + q)];
     bfly8<T, true>(x);
 #pragma unroll
     for (int q = 0; q < 8; ++q) x[q] = cmulany(x[q], __ldg(&mm[q]));
     bfly8<T, false>(x);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) p[q] = x[q];
+    for (int q = 0; q < 8; ++q) p[sidx<T>(base + q)] = x[q];
   }
   __syncthreads();
 }
@@ -341,7 +360,7 @@ __device__ void fusedL_impl(cx<T>* __restrict__ buf, int logL, int nvec, int vs,
     cx<T>* p = buf + v * vs;
     cx<T> x[R];
 #pragma unroll
-    for (int q = 0; q < R; ++q) x[q] = p[padi(j + (q << logm))];
+    for (int q = 0; q < R; ++q) x[q] = p[sidx<T>(j + (q << logm))];
     cx<T> w[R];
     w[0] = mkc(T(1), T(0));
 #pragma unroll
@@ -359,7 +378,7 @@ __device__ void fusedL_impl(cx<T>* __restrict__ buf, int logL, int nvec, int vs,
       for (int q = 1; q < R; ++q) x[q] = cmul(x[q], w[q]);
     }
 #pragma unroll
-    for (int q = 0; q < R; ++q) p[padi(j + (q << logm))] = x[q];
+    for (int q = 0; q < R; ++q) p[sidx<T>(j + (q << logm))] = x[q];
   }
   __syncthreads();
 }

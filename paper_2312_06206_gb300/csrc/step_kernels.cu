@@ -57,7 +57,7 @@ __device__ __forceinline__ void leapfrog_comp(T hi, T uh, int first, size_t idx,
 
 template <typename T>
 __device__ __forceinline__ T real_view(const cx<T>* v, int k) {
-  const T* f = reinterpret_cast<const T*>(v + padi(k >> 1));
+  const T* f = reinterpret_cast<const T*>(v + sidx<T>(k >> 1));
   return f[k & 1];
 }
 
@@ -103,21 +103,21 @@ __device__ void gs_core(cx<T>* buf, int nvec, int vs, const Geom& g, const cx<T>
   fft_dif<T>(buf, logNp, nvec, vs, stw);
   for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
     const int v = t >> logNp, p = t & (Np - 1);
-    cx<T>* e = buf + v * vs + padi(p);
+    cx<T>* e = buf + v * vs + sidx<T>(p);
     *e = cmul(*e, __ldg(&lam_s[p]));
   }
   __syncthreads();
   fft_dit<T>(buf, logNp, nvec, vs, stw);
   for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
     const int v = t >> logNp, k = t & (Np - 1);
-    cx<T>* e = buf + v * vs + padi(k);
+    cx<T>* e = buf + v * vs + sidx<T>(k);
     *e = cmulc(*e, __ldg(&tw[k]));       // Q^H
   }
   __syncthreads();
   fft_dif<T>(buf, logNp, nvec, vs, stw);
   for (int t = threadIdx.x; t < (nvec << logNp); t += blockDim.x) {
     const int v = t >> logNp, p = t & (Np - 1);
-    cx<T>* e = buf + v * vs + padi(p);
+    cx<T>* e = buf + v * vs + sidx<T>(p);
     *e = cmul(*e, __ldg(&lam_c[p]));
   }
   __syncthreads();
@@ -128,10 +128,10 @@ __device__ void gs_core(cx<T>* buf, int nvec, int vs, const Geom& g, const cx<T>
 // border correction sum_q G[k, q] ybot[q], ybot[q] = (H'^-1 v')[N + q].
 template <typename T>
 __device__ __forceinline__ T gs_out(const cx<T>* vh, int k, const Geom& g, const T* __restrict__ G) {
-  T y = vh[padi(k)].x + vh[padi(g.Np - 1 - k)].y;
+  T y = vh[sidx<T>(k)].x + vh[sidx<T>(g.Np - 1 - k)].y;
   for (int q = 0; q < g.r; ++q) {
     const int kb = g.N + q;
-    const T yb = vh[padi(kb)].x + vh[padi(g.Np - 1 - kb)].y;
+    const T yb = vh[sidx<T>(kb)].x + vh[sidx<T>(g.Np - 1 - kb)].y;
     y += __ldg(&G[(size_t)k * g.r + q]) * yb;
   }
   return y;
@@ -149,7 +149,7 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
-  const int vs = vec_stride(Np);
+  const int vs = vstride<T>(Np);
   const int row0 = blockIdx.x * NR;
   const int nrows = min(NR, N - row0);
   for (int t = threadIdx.x; t < (NR << logNp); t += blockDim.x) {
@@ -160,7 +160,7 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
       if (2 * n < N) a = row[2 * n];
       if (2 * n + 1 < N) b = row[2 * n + 1];
     }
-    buf[v * vs + padi(n)] = mkc(a, b);
+    buf[v * vs + sidx<T>(n)] = mkc(a, b);
   }
   __syncthreads();
   fft_dif<T>(buf, logNp, NR, vs, stw);
@@ -169,8 +169,8 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
     const int v = t >> logNp, s = t & (Np - 1);
     const int k = brev(s, logNp);
     const int sp = brev((Np - k) & (Np - 1), logNp);
-    const cx<T> Z = buf[v * vs + padi(s)];
-    const cx<T> Zc = cconj(buf[v * vs + padi(sp)]);
+    const cx<T> Z = buf[v * vs + sidx<T>(s)];
+    const cx<T> Zc = cconj(buf[v * vs + sidx<T>(sp)]);
     const cx<T> E = cscale(cadd(Z, Zc), half);
     const cx<T> O = cscale(cmul_mi(csub(Z, Zc)), half);   // (Z - Zc) / (2i)
     cx<T> X;
@@ -196,14 +196,14 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
-  const int vs = vec_stride(Np);
+  const int vs = vstride<T>(Np);
   const int s0 = blockIdx.x * CT;
   for (int t = threadIdx.x; t < CT * Np; t += blockDim.x) {
     const int c = t % CT, j = t / CT;
     cx<T> val = mkc(T(0), T(0));
     if (j < N) val = S[(size_t)j * Np + s0 + c];
-    buf[(2 * c) * vs + padi(j)] = val;
-    buf[(2 * c + 1) * vs + padi(j)] = cmul(val, __ldg(&tw[j]));
+    buf[(2 * c) * vs + sidx<T>(j)] = val;
+    buf[(2 * c + 1) * vs + sidx<T>(j)] = cmul(val, __ldg(&tw[j]));
   }
   __syncthreads();
   const int ns = plan_stages(logNp);
@@ -218,7 +218,7 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
       const int vec = t >> logNp, p = t & (Np - 1);
       const int slot = s0 + (vec >> 1), h = vec & 1;
       if (slot == 0) continue;
-      cx<T>* e = buf + vec * vs + padi(p);
+      cx<T>* e = buf + vec * vs + sidx<T>(p);
       *e = cscale(*e, __ldg(&lpb[((size_t)slot * 2 + h) * Np + p]));
     }
     if (s0 == 0) {
@@ -229,7 +229,7 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
         const int pp = (h == 0) ? brev((Np - brev(p, logNp)) & (Np - 1), logNp) : (Np - 1 - p);
         if (pp < p) continue;
         cx<T>* e = buf + h * vs;
-        const cx<T> Y = e[padi(p)], Yp = e[padi(pp)];
+        const cx<T> Y = e[sidx<T>(p)], Yp = e[sidx<T>(pp)];
         // unpack the two real columns first: Ev = spectrum of the k1 = 0
         // column, Od = i x spectrum of the k1 = Np column; each then takes its
         // own symbol (no cancellation between the large k1 = Np symbol and
@@ -238,11 +238,11 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
         const cx<T> Od = cscale(csub(Y, cconj(Yp)), half);
         const T L0 = __ldg(&lpb[(size_t)h * Np + p]);
         const T LN = __ldg(&lpb[((size_t)Np * 2 + h) * Np + p]);
-        e[padi(p)] = cadd(cscale(Ev, L0), cscale(Od, LN));
+        e[sidx<T>(p)] = cadd(cscale(Ev, L0), cscale(Od, LN));
         if (pp != p) {
           const T L0p = __ldg(&lpb[(size_t)h * Np + pp]);
           const T LNp = __ldg(&lpb[((size_t)Np * 2 + h) * Np + pp]);
-          e[padi(pp)] = csub(cscale(cconj(Ev), L0p), cscale(cconj(Od), LNp));
+          e[sidx<T>(pp)] = csub(cscale(cconj(Ev), L0p), cscale(cconj(Od), LNp));
         }
       }
     }
@@ -251,8 +251,8 @@ k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const 
   }
   for (int t = threadIdx.x; t < CT * N; t += blockDim.x) {
     const int c = t % CT, j = t / CT;
-    const cx<T> ye = buf[(2 * c) * vs + padi(j)];
-    const cx<T> yo = buf[(2 * c + 1) * vs + padi(j)];
+    const cx<T> ye = buf[(2 * c) * vs + sidx<T>(j)];
+    const cx<T> yo = buf[(2 * c + 1) * vs + sidx<T>(j)];
     S[(size_t)j * Np + s0 + c] = cadd(ye, cmulc(yo, __ldg(&tw[j])));
   }
 }
@@ -270,7 +270,7 @@ __device__ __forceinline__ void rows_inverse(cx<T>* buf, const cx<T>* __restrict
     const int v = t >> logNp, s = t & (Np - 1);
     cx<T> val = mkc(T(0), T(0));
     if (v < nrows) val = S[(size_t)(row0 + v) * Np + s];
-    buf[v * vs + padi(s)] = val;
+    buf[v * vs + sidx<T>(s)] = val;
   }
   __syncthreads();
   // each thread owns a partner pair of slots
@@ -282,21 +282,21 @@ __device__ __forceinline__ void rows_inverse(cx<T>* buf, const cx<T>* __restrict
     const int sp = brev(kp, logNp);
     if (sp < s) continue;
     cx<T>* e = buf + v * vs;
-    const cx<T> X = e[padi(s)];
+    const cx<T> X = e[sidx<T>(s)];
     if (s == 0) {
-      e[padi(0)] = mkc((X.x + X.y) * half, (X.x - X.y) * half);
+      e[sidx<T>(0)] = mkc((X.x + X.y) * half, (X.x - X.y) * half);
       continue;
     }
-    const cx<T> Xp = e[padi(sp)];
+    const cx<T> Xp = e[sidx<T>(sp)];
     {
       const cx<T> E = cscale(cadd(X, cconj(Xp)), half);
       const cx<T> O = cscale(cmulc(csub(X, cconj(Xp)), __ldg(&tw[k])), half);
-      e[padi(s)] = cadd(E, cmul_pi(O));
+      e[sidx<T>(s)] = cadd(E, cmul_pi(O));
     }
     if (sp != s) {
       const cx<T> E = cscale(cadd(Xp, cconj(X)), half);
       const cx<T> O = cscale(cmulc(csub(Xp, cconj(X)), __ldg(&tw[kp])), half);
-      e[padi(sp)] = cadd(E, cmul_pi(O));
+      e[sidx<T>(sp)] = cadd(E, cmul_pi(O));
     }
   }
   __syncthreads();
@@ -315,7 +315,7 @@ k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ 
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N;
-  const int vs = vec_stride(g.Np);
+  const int vs = vstride<T>(g.Np);
   const int row0 = blockIdx.x * NR;
   const int nrows = min(NR, N - row0);
   rows_inverse<T>(buf, S, g, NR, row0, nrows, vs, stw, tw);
@@ -345,7 +345,7 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np;
-  const int vs = vec_stride(Np);
+  const int vs = vstride<T>(Np);
   const int row0 = blockIdx.x * NR;
   const int nrows = min(NR, N - row0);
   rows_inverse<T>(buf, S, g, NR, row0, nrows, vs, stw, tw);
@@ -413,8 +413,8 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
     if (t < npairs) {
       const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
       cx<T>* e = buf + v * vs;
-      e[padi(k)] = cmul(mkc(ra[it], rb[it]), __ldg(&tw[k]));
-      e[padi(k2)] = cmul(mkc(rb[it], ra[it]), __ldg(&tw[k2]));
+      e[sidx<T>(k)] = cmul(mkc(ra[it], rb[it]), __ldg(&tw[k]));
+      e[sidx<T>(k2)] = cmul(mkc(rb[it], ra[it]), __ldg(&tw[k2]));
     }
   }
   __syncthreads();
@@ -442,7 +442,7 @@ k_cols_solve(const T* __restrict__ W, const T* u_cur, T* u_prev, T* u_next, T* u
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np;
-  const int vs = vec_stride(Np);
+  const int vs = vstride<T>(Np);
   const int i0 = blockIdx.x * CT;
   for (int t = threadIdx.x; t < CT * Np; t += blockDim.x) {
     const int c = t % CT, k = t / CT;
@@ -452,7 +452,7 @@ k_cols_solve(const T* __restrict__ W, const T* u_cur, T* u_prev, T* u_next, T* u
       if (k < N) a = W[(size_t)k * N + i];
       if (k2 < N) b = W[(size_t)k2 * N + i];
     }
-    buf[c * vs + padi(k)] = cmul(mkc(a, b), __ldg(&tw[k]));
+    buf[c * vs + sidx<T>(k)] = cmul(mkc(a, b), __ldg(&tw[k]));
   }
   __syncthreads();
   gs_core<T>(buf, CT, vs, g, stw, tw, lam_s, lam_c);
@@ -507,7 +507,7 @@ Tiles default_tiles(int Np) {
 
 template <typename T>
 bool tiles_valid(const Geom& g, const Tiles& t) {
-  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
   const size_t lim = 227 * 1024;
   if (t.rows < 1 || t.conv_cols < 1 || t.solve_cols < 1) return false;
   if (g.Np % t.conv_cols != 0) return false;
@@ -525,7 +525,7 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   const cx<T>* ls = reinterpret_cast<const cx<T>*>(tb.lam_s);
   const cx<T>* lc = reinterpret_cast<const cx<T>*>(tb.lam_c);
   cx<T>* S = reinterpret_cast<cx<T>*>(Sv);
-  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
   if (!tiles_valid<T>(g, tl)) return cudaErrorInvalidConfiguration;
   const int NR = tl.rows, CTc = tl.conv_cols, CTs = tl.solve_cols;
   const int rblocks = (g.N + NR - 1) / NR;
@@ -563,7 +563,7 @@ cudaError_t launch_remainder(const Geom& g, const StepTables<T>& tb, const Tiles
   const cx<T>* stw = reinterpret_cast<const cx<T>*>(tb.stw);
   const cx<T>* tw = reinterpret_cast<const cx<T>*>(tb.tw);
   cx<T>* S = reinterpret_cast<cx<T>*>(Sv);
-  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
   if (!tiles_valid<T>(g, tl)) return cudaErrorInvalidConfiguration;
   const int NR = tl.rows, CTc = tl.conv_cols;
   const int rblocks = (g.N + NR - 1) / NR;
@@ -587,7 +587,7 @@ cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const 
   const cx<T>* ls = reinterpret_cast<const cx<T>*>(tb.lam_s);
   const cx<T>* lc = reinterpret_cast<const cx<T>*>(tb.lam_c);
   cx<T>* S = reinterpret_cast<cx<T>*>(Sv);
-  const size_t vbytes = (size_t)vec_stride(g.Np) * sizeof(cx<T>);
+  const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
   if (!tiles_valid<T>(g, tl)) return cudaErrorInvalidConfiguration;
   const int NR = tl.rows, CTc = tl.conv_cols;
   const int rblocks = (g.N + NR - 1) / NR;
