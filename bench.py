@@ -636,8 +636,12 @@ def main():
             s = S.Sadi(N, al, KAPPA, TAU, (-1.0, 1.0))
             s.set_options(GKIND, prec)
             s.set_stream(stream.cuda_stream)
-            s.set_initial(phi1, _phi2(phi1))
             ctxs.append(s)
+        if prec != S.SADI_PREC_FP64:
+            # tiles of the shared-memory FFT engine tuned for this form
+            S.sadi_autotune(ctxs, GKIND, 2)
+        for s in ctxs:
+            s.set_initial(phi1, _phi2(phi1))
         return ctxs
 
     def step_all(ctxs):

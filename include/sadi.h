@@ -125,8 +125,9 @@ sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
  * N' <= 1024 are grouped by precision and N' (at most 32 per group) and each
  * group runs one launch per kernel for all its members (independent problems
  * of possibly different N, alpha, kappa, tau and g; the dense sweeps in GEMM
- * launches of up to 16 problems); the other contexts step one after another.  All contexts must be
- * initialised and distinct (SADI_EINVAL / SADI_ESTATE otherwise).  The work
+ * launches of up to 16 problems); the other contexts step one after another.
+ * All contexts must be initialised and distinct (SADI_EINVAL / SADI_ESTATE
+ * otherwise).  The work
  * is issued on the first context's stream, ordered after the work already
  * queued on the other contexts' streams and before their later work (event
  * waits).  Results are identical to stepping each context alone. */
@@ -177,9 +178,10 @@ void sadi_graph_destroy(sadi_graph *graph);
  * s a_0 > 0.2 (the dense form's accuracy limit above),
  * SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, on the
  * shared-memory FFT engine (N' > 1024), the work decomposition of
- * sadi_set_tiles by coordinate descent.  Each context is left with g, the
- * fastest precision and tiles of its group, uninitialised (call
- * sadi_set_initial next).  Must precede sadi_set_initial and
+ * sadi_set_tiles by coordinate descent.  flags bit 1 keeps the precision the
+ * contexts already have (FP32 or FP32_DENSE, equal within each N) and tunes
+ * only the tiles.  Each context is left with g, the fastest precision and
+ * tiles of its group, uninitialised (call sadi_set_initial next).  Must precede sadi_set_initial and
  * sadi_set_source.  The choice and the timings are readable with
  * sadi_tuning_log.  Synchronous. */
 sadi_status sadi_autotune(sadi_ctx **ctxs, int count, int g, int flags);
@@ -222,8 +224,10 @@ sadi_status sadi_get_info(const sadi_ctx *ctx, int *fft_len, int *border_rank);
  * of the column convolution (a divisor of N'), grid columns per block of the
  * y sweep.  All zero restores the defaults.  Invalid combinations (shared
  * memory above 227 KB per block, or more rows than the row kernel stages)
- * return SADI_EINVAL and leave the setting unchanged.  Results do not depend
- * on the tiles (bitwise). Call after sadi_set_options. */
+ * return SADI_EINVAL and leave the setting unchanged.  The tiles change the
+ * order of some rounding steps (the column convolution multiplies the symbol
+ * fused into its transforms or in a separate pass), so results of different
+ * tiles agree to rounding, not bitwise.  Call after sadi_set_options. */
 sadi_status sadi_set_tiles(sadi_ctx *ctx, int rows, int conv_cols, int solve_cols);
 
 /* Current tiles of the selected precision: tiles[0..2] = rows, conv_cols,

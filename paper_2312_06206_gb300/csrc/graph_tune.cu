@@ -222,6 +222,14 @@ sadi_status sadi_autotune(sadi_ctx** ctxs, int count, int g, int flags) {
       return cuda_fail(grp[0], cudaErrorUnknown, "reading a_0");
     const bool dense_ok = grp[0]->s * a0 <= kDenseMaxSA0;
     if (!(flags & 1) && dense_ok) precs.push_back(SADI_PREC_FP32_DENSE);
+    if (flags & 2) {
+      // keep the precision the group was created with; tune its tiles only
+      const int p0 = grp[0]->prec;
+      for (sadi_ctx* c : all)
+        if (c->prec != p0) return fail(c, SADI_EINVAL, "flags bit 1: contexts of one N differ in precision");
+      if (p0 == SADI_PREC_FP64) return fail(grp[0], SADI_EUNSUPPORTED, "flags bit 1 tunes the FP32 forms only");
+      precs.assign(1, p0);
+    }
     std::string log = fmt("N=%.0f N'=%.0f batch=%.0f s*a0=%.3g:", N, Np, (double)grp.size(), grp[0]->s * a0);
     Cand best{SADI_PREC_FP32, Tiles{0, 0, 0}};
     double best_ms = 1e30;

@@ -112,3 +112,19 @@ def test_autotune_picks_a_form_per_n_and_keeps_parity(S):
                 ref, _ = r.get()
         assert O.rel_l2(u, ref) <= 1e-5
         s.close()
+
+
+def test_autotune_can_keep_the_precision(S):
+    # flags bit 1: tiles only, the precision each context was given stays
+    ctxs = [S.Sadi(1100, 1.5, 1.0, 0.01) for _ in range(2)]
+    ctxs[0].set_options(1, S.SADI_PREC_FP32_DENSE)
+    ctxs[1].set_options(1, S.SADI_PREC_FP32_DENSE)
+    S.sadi_autotune(ctxs, 1, 2)
+    assert all(s.sadi_get_options() == (1, S.SADI_PREC_FP32_DENSE) for s in ctxs)
+    assert "fp32-gsfft" not in ctxs[0].sadi_tuning_log() and "tiles" in ctxs[0].sadi_tuning_log()
+    f64 = S.Sadi(63, 1.5, 1.0, 0.01)
+    with pytest.raises(S.SadiError) as ei:
+        S.sadi_autotune([f64], 1, 2)
+    assert ei.value.status == S.SADI_EUNSUPPORTED
+    for s in ctxs + [f64]:
+        s.close()
