@@ -9,14 +9,16 @@
 // tiles.  Per-element representation error of a pair is <= 2^-16 relative, so
 // ACC carries about 2^-16 relative error on top of FP32 accumulation.
 //
-// Persistent: one CTA per SM (at most one per tile) walks the 128 x 256
-// output tiles of all problems of the launch, 10 warps:
+// Persistent: one CTA per SM (at most one per tile) walks the output tiles
+// of all problems of the launch, 128 x 256 when there are enough of them to
+// give every SM one, else 128 x 128 (BN below), 10 warps:
 //   * thread 0 streams 64-wide K blocks of A_hi, A_lo (128 rows) and B_hi,
-//     B_lo (256 rows) with TMA (cp.async.bulk.tensor, 128-byte swizzle) into
-//     a 2-stage ring guarded by mbarriers, continuing across tiles;
+//     B_lo (BN rows, in 128-row boxes) with TMA (cp.async.bulk.tensor,
+//     128-byte swizzle) into a ring of 2 (BN = 256) or 3 (BN = 128) stages
+//     guarded by mbarriers, continuing across tiles;
 //   * thread 32 issues tcgen05.mma (kind::f16, BF16 inputs, FP32 accumulator
-//     of 128 lanes x 256 columns in tensor memory) into one of two
-//     accumulators (the 512 TMEM columns), returns each stage to the producer
+//     of 128 lanes x BN columns in tensor memory) into one of two
+//     accumulators (2 BN TMEM columns), returns each stage to the producer
 //     with tcgen05.commit and signals the finished accumulator;
 //   * 8 epilogue warps drain the other accumulator meanwhile (tcgen05.ld
 //     32x32b; a warp takes the lane quarter 32 (w % 4) .. +31 and one column
@@ -41,12 +43,23 @@
 namespace sadi {
 namespace {
 
-constexpr int BM = kTcTileM, BN = kTcTileN, BK = kTcTileK;
-constexpr int STAGES = 2;
-constexpr int A_TILE = BM * BK * 2;                    // 16 KB
-constexpr int B_TILE = BN * BK * 2;                    // 32 KB
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;   // 96 KB
-constexpr int TMEM_COLS = 256;
+constexpr int BM = kTcTileM, BK = kTcTileK;
+constexpr int BOX = kTcBox;             // rows of every TMA box, A and B alike
+constexpr int A_TILE = BM * BK * 2;     // 16 KB
+constexpr int BOX_BYTES = BOX * BK * 2; // 16 KB
+
+// What depends on the tile width BN (256 or 128 output columns): the B block of
+// one stage, the stage bytes, the depth of the stage ring and the TMEM columns
+// of one accumulator.  Both widths fill the same shared memory (2 x 96 KB or
+// 3 x 64 KB of stages).
+template <int BN>
+struct TileCfg {
+  static_assert(BN == 256 || BN == 128, "tile width");
+  static constexpr int B_TILE = BN * BK * 2;
+  static constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+  static constexpr int STAGES = BN == 256 ? 2 : 3;
+  static constexpr int TMEM_COLS = BN;
+};
 constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -220,6 +233,33 @@ __device__ __forceinline__ void epilogue_block(const TcEpi& e, int rowbase, int 
   __syncwarp();
 }
 
+// Pull the global inputs of a warp's epilogue share into L2 while the tile's
+// MMAs still run: the lane's row, columns c0 .. c0 + W - 1 (clipped to the
+// valid columns) of each array the epilogue reads.  Only addresses of valid
+// elements are named; one every 128 bytes plus the last covers every line.
+__device__ __forceinline__ void prefetch_l2(const float* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+template <int W>
+__device__ __forceinline__ void prefetch_row(const float* a, int ld, int row, int c0, int c1) {
+  const float* p = a + (size_t)row * ld;
+#pragma unroll
+  for (int c = 0; c < W; c += 32)
+    if (c0 + c < c1) prefetch_l2(p + c0 + c);
+  prefetch_l2(p + c1 - 1);
+}
+template <int W>
+__device__ __forceinline__ void prefetch_epilogue(const TcEpi& e, int row, int c0) {
+  const int c1 = min(c0 + W, e.n_valid);
+  if (row >= e.m_valid || c0 >= c1 || e.mode == kTcStore) return;
+  prefetch_row<W>(e.C, e.ldc, row, c0, c1);
+  if (e.mode == kTcSweepY) {
+    prefetch_row<W>(e.u_hi, e.ldu, row, c0, c1);
+    prefetch_row<W>(e.u_lo, e.ldu, row, c0, c1);
+    if (!e.first) prefetch_row<W>(e.u_d, e.ldu, row, c0, c1);
+  }
+}
+
 // Wait for a phase like mbar_wait, but give up at once when another role of
 // the CTA has aborted, and abort the CTA when the time limit runs out.
 __device__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
@@ -240,14 +280,16 @@ __device__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort
 // rows, column-major within a group, so that the tiles in flight at one time
 // share A and B panels in L2.
 constexpr int kGroupM = 8;
+template <int BN>
 __device__ __forceinline__ void tile_coords(const TcBatch& bt, int t, int* z, int* m0, int* n0) {
+  constexpr int per = BN / BOX;   // B boxes per tile width
   int k = 0;
   for (; k < bt.count - 1; ++k) {
-    const int nt = bt.in[k].tiles_m * bt.in[k].tiles_n;
+    const int nt = bt.in[k].tiles_m * (bt.in[k].boxes_n / per);
     if (t < nt) break;
     t -= nt;
   }
-  const int tm = bt.in[k].tiles_m, tn = bt.in[k].tiles_n;
+  const int tm = bt.in[k].tiles_m, tn = bt.in[k].boxes_n / per;
   const int per_group = kGroupM * tn;
   const int first_m = (t / per_group) * kGroupM;
   const int gsz = min(tm - first_m, kGroupM);
@@ -260,16 +302,24 @@ __device__ __forceinline__ void tile_coords(const TcBatch& bt, int t, int* z, in
 // Persistent kernel: one CTA per SM walks the tiles t = blockIdx.x,
 // blockIdx.x + gridDim.x, ...  Warp 0 (one thread) streams operand blocks by
 // TMA through the stage ring, warp 1 (one thread) issues the MMAs into one
-// of two TMEM accumulators (columns 0-255 and 256-511) and signals tmem_full;
+// of two TMEM accumulators (columns 0 .. BN-1 and BN .. 2BN-1) and signals tmem_full;
 // warps 2-9 run the epilogue of the other accumulator meanwhile (two warps
-// per TMEM lane quarter, one per column half) and free it through tmem_empty.  The ring and the accumulator pair carry over from
-// tile to tile.
+// per TMEM lane quarter, one per column half) and free it through
+// tmem_empty.  The ring and the accumulator pair carry over from tile to
+// tile.
 constexpr int EPI_WARPS = 8;
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr size_t EPI_BYTES = (size_t)EPI_WARPS * 32 * EPI_LD * sizeof(float);
-constexpr size_t PSMEM_BYTES = (size_t)STAGES * STAGE_BYTES + EPI_BYTES + 1024 + 128;
+template <int BN>
+constexpr size_t psmem_bytes() {
+  return (size_t)TileCfg<BN>::STAGES * TileCfg<BN>::STAGE_BYTES + EPI_BYTES + 1024 + 128;
+}
+static_assert(psmem_bytes<256>() <= 232448 && psmem_bytes<128>() <= 232448, "shared memory per CTA");
 
+template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int total, int* err) {
+  constexpr int STAGES = TileCfg<BN>::STAGES, STAGE_BYTES = TileCfg<BN>::STAGE_BYTES;
+  constexpr int B_TILE = TileCfg<BN>::B_TILE, TMEM_COLS = TileCfg<BN>::TMEM_COLS;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* epi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
@@ -312,7 +362,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
       int it = 0;
       for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
         int z, m0, n0;
-        tile_coords(bt, t, &z, &m0, &n0);
+        tile_coords<BN>(bt, t, &z, &m0, &n0);
         const TcInst& in = bt.in[z];
         const int nk = in.K / BK;
         for (int kb = 0; kb < nk; ++kb, ++it) {
@@ -323,8 +373,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
           mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
           tma_load_2d(su32(st), &in.a_hi, kb * BK, m0, full0 + 8 * s);
           tma_load_2d(su32(st + A_TILE), &in.a_lo, kb * BK, m0, full0 + 8 * s);
-          tma_load_2d(su32(st + 2 * A_TILE), &in.b_hi, kb * BK, n0, full0 + 8 * s);
-          tma_load_2d(su32(st + 2 * A_TILE + B_TILE), &in.b_lo, kb * BK, n0, full0 + 8 * s);
+#pragma unroll
+          for (int j = 0; j < BN / BOX; ++j) {
+            // 128-row boxes stacked in 16 KB steps continue the 8-row, 1024 B
+            // pattern of the swizzled layout
+            tma_load_2d(su32(st + 2 * A_TILE + j * BOX_BYTES), &in.b_hi, kb * BK, n0 + j * BOX, full0 + 8 * s);
+            tma_load_2d(su32(st + 2 * A_TILE + B_TILE + j * BOX_BYTES), &in.b_lo, kb * BK, n0 + j * BOX,
+                        full0 + 8 * s);
+          }
         }
       }
       if (*abort_flag) {
@@ -340,7 +396,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
       int it = 0, tl = 0;
       for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++tl) {
         int z, m0, n0;
-        tile_coords(bt, t, &z, &m0, &n0);
+        tile_coords<BN>(bt, t, &z, &m0, &n0);
         const int nk = bt.in[z].K / BK;
         const int b = tl & 1;
         const uint32_t ub = (uint32_t)(tl >> 1);
@@ -382,12 +438,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
     int tl = 0;
     for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
       int z, m0, n0;
-      tile_coords(bt, t, &z, &m0, &n0);
+      tile_coords<BN>(bt, t, &z, &m0, &n0);
       const int b = tl & 1;
       const uint32_t ub = (uint32_t)(tl >> 1);
+      const TcInst& in = bt.in[z];
+      prefetch_epilogue<BN / 2>(in.e, m0 + quarter * 32 + lane, n0 + half * (BN / 2));
       if (!wait_or_abort(tfull0 + 8 * b, ub & 1u, abort_flag) || *abort_flag) break;
       tc_fence_after();
-      const TcInst& in = bt.in[z];
       const uint32_t acc = tmem + (uint32_t)(b * TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
       for (int c = 0; c < BN / 64; ++c) {
@@ -404,7 +461,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
   __syncwarp();
   if (*abort_flag && threadIdx.x == 64) {
     int z, m0, n0;
-    tile_coords(bt, blockIdx.x, &z, &m0, &n0);
+    tile_coords<BN>(bt, blockIdx.x, &z, &m0, &n0);
     atomicExch(bt.in[z].e.err ? bt.in[z].e.err : err, 1);
   }
   tc_fence_before();
@@ -463,22 +520,24 @@ cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, cons
   cudaError_t e;
   if ((e = tc_encode(&in->a_hi, a_hi, M, K, BM))) return e;
   if ((e = tc_encode(&in->a_lo, a_lo, M, K, BM))) return e;
-  if ((e = tc_encode(&in->b_hi, b_hi, N, K, BN))) return e;
-  if ((e = tc_encode(&in->b_lo, b_lo, N, K, BN))) return e;
-  if (M % BM || N % BN || K % BK || K <= 0) return cudaErrorInvalidValue;
+  if ((e = tc_encode(&in->b_hi, b_hi, N, K, BOX))) return e;
+  if ((e = tc_encode(&in->b_lo, b_lo, N, K, BOX))) return e;
+  if (M % BM || N % BOX || K % BK || K <= 0) return cudaErrorInvalidValue;
   in->K = K;
   in->tiles_m = M / BM;
-  in->tiles_n = N / BN;
+  in->boxes_n = N / BOX;
   return cudaSuccess;
 }
 
 cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
   if (b.count < 1 || b.count > kTcMaxBatch) return cudaErrorInvalidValue;
-  int total = 0;
+  int boxes = 0;
+  bool even = true;
   for (int k = 0; k < b.count; ++k) {
     const TcInst& in = b.in[k];
-    if (in.K <= 0 || in.K % BK || in.tiles_m < 1 || in.tiles_n < 1) return cudaErrorInvalidValue;
-    total += in.tiles_m * in.tiles_n;
+    if (in.K <= 0 || in.K % BK || in.tiles_m < 1 || in.boxes_n < 1) return cudaErrorInvalidValue;
+    boxes += in.tiles_m * in.boxes_n;
+    even = even && in.boxes_n % 2 == 0;
   }
   static int sms = 0;
   if (!sms) {
@@ -486,14 +545,24 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tc_gemm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)PSMEM_BYTES);
+      e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<256>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<128>());
     if (e != cudaSuccess) {
       sms = 0;
       return e;
     }
   }
-  const int grid = total < sms ? total : sms;
-  k_tc_gemm<<<grid, GEMM_THREADS, PSMEM_BYTES, st>>>(b, total, err);
+  // 128 x 256 tiles while they give every SM at least one; below that the
+  // 128 x 128 tiles reach more SMs, and a CTA with two of them runs the
+  // epilogue of the first under the MMAs of the second
+  if (even && boxes / 2 >= sms) {
+    const int total = boxes / 2;
+    k_tc_gemm<256><<<sms, GEMM_THREADS, psmem_bytes<256>(), st>>>(b, total, err);
+  } else {
+    const int total = boxes;
+    k_tc_gemm<128><<<total < sms ? total : sms, GEMM_THREADS, psmem_bytes<128>(), st>>>(b, total, err);
+  }
   return cudaGetLastError();
 }
 
@@ -520,7 +589,7 @@ extern "C" sadi_status sadi_gemm_split_bf16(const float* A, const float* B, floa
                                             void* stream) {
   if (!A || !B || !C || M < 1 || N < 1 || K < 1 || M > 65536 || N > 65536 || K > 65536) return SADI_EINVAL;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int Mp = round_up(M, BM), Np = round_up(N, BN), Kp = round_up(K, BK);
+  const int Mp = round_up(M, BM), Np = round_up(N, kTcTileN), Kp = round_up(K, BK);
   unsigned short* buf = nullptr;
   int* err = nullptr;
   const size_t na = (size_t)Mp * Kp, nb = (size_t)Np * Kp;

@@ -161,7 +161,10 @@ cudaError_t run_dense_inverse(const double* a1, int N, double s, int npad, void*
 // ---- split-BF16 tensor-core GEMM, gemm_tc.cu ----------------------------------
 // ACC = A_hi B_hi^T + A_hi B_lo^T + A_lo B_hi^T over K-major BF16 operands
 // (row-major, K contiguous, zero-padded to whole tiles), then an epilogue.
-constexpr int kTcTileM = 128, kTcTileN = 256, kTcTileK = 64;
+// tile rows and K block; operands are padded to multiples of kTcTileN rows,
+// which the 256-wide tiles and the 128-wide tiles of the GEMM both divide;
+// every TMA box is kTcBox rows
+constexpr int kTcTileM = 128, kTcTileN = 256, kTcTileK = 64, kTcBox = 128;
 constexpr int kTcMaxBatch = 16;
 enum TcMode { kTcStore = 0, kTcSweepX = 1, kTcSweepY = 2 };
 struct TcEpi {
@@ -181,10 +184,10 @@ struct TcEpi {
 };
 struct TcInst {
   CUtensorMap a_hi, a_lo;     // A operand (M rows), box 128 x 64
-  CUtensorMap b_hi, b_lo;     // B operand (N rows), box 256 x 64
+  CUtensorMap b_hi, b_lo;     // B operand (N rows), box 128 x 64
   TcEpi e;
   int K;                      // padded contraction length (multiple of 64)
-  int tiles_m, tiles_n;       // padded M / 128 and N / 256 of this problem
+  int tiles_m, boxes_n;       // padded M / 128 and N / 128 of this problem
 };
 // passed by value as a __grid_constant__ kernel parameter (about 10 KB)
 struct TcBatch {
@@ -196,9 +199,10 @@ cudaError_t tc_encode(CUtensorMap* map, const void* base, int rows, int kdim, in
 // tensor maps and extents of one problem: A is M x K, B is N x K (padded sizes)
 cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, const void* b_hi, const void* b_lo,
                             int M, int N, int K);
-// one launch for all b.count problems (blockIdx.z); the grid covers the largest
-// problem and the CTAs beyond a smaller one exit at once; *err set on a
-// timed-out wait
+// one persistent launch for all b.count problems: at most one CTA per SM walks
+// the output tiles of every problem, 128 x 256 tiles when they number at least
+// one per SM (and every N is a multiple of 256), else 128 x 128; *err (or the
+// problem's own e.err) set on a timed-out wait
 cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st);
 // FP32 rows x cols (ld src_ld) -> zero-padded prow x pcol BF16 hi / lo
 cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,
