@@ -151,8 +151,18 @@ struct RegFFT {
     return (t + TT * j) + E * cbrev(p, LOGT);
   }
 
-  // Forward transform; ends with the buffer free (after a __syncthreads()).
+  // Barrier between the transpose's writes and reads: the whole block, or
+  // (WARP) only the warp, when every vector's TT threads lie in one warp and
+  // no other warp touches its buffer.
+  template <bool WARP>
+  __device__ static __forceinline__ void sync() {
+    if constexpr (WARP) __syncwarp();
+    else __syncthreads();
+  }
+
+  // Forward transform; ends with the buffer free (after a barrier).
   // tw1 may point to global or shared memory.
+  template <bool WARP = false>
   __device__ static __forceinline__ void fwd(cx<T>* x, cx<T>* sm, int t, const cx<T>* __restrict__ tw1) {
     dft_fwd<T, E>(x);
     static_for<0, E>([&](auto pc) {
@@ -160,7 +170,7 @@ struct RegFFT {
       constexpr int k1 = cbrev(p, LOGE);
       sm[k1 * ROW + t] = cmul(x[p], tw1[k1 * TT + t]);
     });
-    __syncthreads();
+    sync<WARP>();
     static_for<0, KPT>([&](auto jc) {
       constexpr int j = decltype(jc)::value;
       static_for<0, TT>([&](auto sc) {
@@ -168,11 +178,12 @@ struct RegFFT {
         x[j * TT + s] = sm[(t + TT * j) * ROW + s];
       });
     });
-    __syncthreads();
+    sync<WARP>();
     static_for<0, KPT>([&](auto jc) { dft_fwd<T, TT>(x + decltype(jc)::value * TT); });
   }
 
   // Inverse of fwd (times L); ends with the buffer free.
+  template <bool WARP = false>
   __device__ static __forceinline__ void inv(cx<T>* x, cx<T>* sm, int t, const cx<T>* __restrict__ tw1) {
     static_for<0, KPT>([&](auto jc) { dft_inv<T, TT>(x + decltype(jc)::value * TT); });
     static_for<0, KPT>([&](auto jc) {
@@ -182,13 +193,13 @@ struct RegFFT {
         sm[(t + TT * j) * ROW + s] = x[j * TT + s];
       });
     });
-    __syncthreads();
+    sync<WARP>();
     static_for<0, E>([&](auto pc) {
       constexpr int p = decltype(pc)::value;
       constexpr int k1 = cbrev(p, LOGE);
       x[p] = cmulc(sm[k1 * ROW + t], tw1[k1 * TT + t]);
     });
-    __syncthreads();
+    sync<WARP>();
     dft_inv<T, E>(x);
   }
 };

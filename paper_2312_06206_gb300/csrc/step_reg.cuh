@@ -47,10 +47,29 @@ struct RowCfg {
   using F = rf::RegFFT<float, LOGL>;
   static constexpr int VB = BLOCK / F::TT;                    // vectors (rows) per block
   static constexpr int SMV = vec_smem<LOGL>(F::TT & 15);      // transform buffer (float2)
-  static constexpr int STG = F::L;                            // staged u row (floats)
   static constexpr size_t tw_bytes = 2 * (size_t)F::L * sizeof(float2);   // tw1 and tw[0 .. L) staged
   static constexpr size_t bytes_r2c = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
-  static constexpr size_t bytes_solve = (size_t)VB * (SMV * sizeof(float2) + STG * sizeof(float)) + tw_bytes;
+  static constexpr size_t bytes_solve = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
+};
+// The convolution kernel: vectors owned by warps (as in the row kernels), CT
+// per block; the FFT buffers, the vectors' symbol rows (natural order) and
+// the staged table tw1.
+template <int LOGL, int BLOCK>
+struct ConvCfg {
+  using F = rf::RegFFT<float, LOGL>;
+  static constexpr int CT = BLOCK / F::TT;
+  static_assert(CT >= 4 && CT % 2 == 0, "item 0 reads item 1's vectors: two items per block at least");
+  // the staging copies of a half-warp cover CT vectors x 16/CT rows: a
+  // vector stride of 16/CT (mod 16) float2 puts them in distinct bank pairs
+  static constexpr int SMV = vec_smem<LOGL>(CT >= 16 ? 1 : 16 / CT);
+  // the half-angle twiddles tw[0 .. L) are staged too when the shared memory
+  // still admits the block count of the launch bounds
+  static constexpr size_t bytes_base =
+      (size_t)CT * SMV * sizeof(float2) + (size_t)CT * F::L * sizeof(float) + (size_t)F::L * sizeof(float2);
+  static constexpr int kBlocksPerSm = BLOCK >= 256 ? 2 : 3;
+  static constexpr bool STAGE_TW =
+      kBlocksPerSm * (bytes_base + F::L * sizeof(float2) + 1024) <= (size_t)228 * 1024;
+  static constexpr size_t bytes = bytes_base + (STAGE_TW ? F::L * sizeof(float2) : 0);
 };
 template <int LOGL, int BLOCK>
 struct ColCfg {
@@ -61,10 +80,8 @@ struct ColCfg {
   // bank pairs of a half-warp distinct
   static constexpr int SMV = vec_smem<LOGL>(CT >= 16 ? 1 : 16 / CT);
   static constexpr int STG = F::L;                            // staged state column (floats)
-  // FFT buffers, the parked symbol values, and the twiddle tables tw1 and
+  // FFT buffers, staged state columns and the twiddle tables tw1 and
   // tw[0 .. L) staged once per block
-  static constexpr size_t bytes_conv =
-      (size_t)CT * SMV * sizeof(float2) + (size_t)BLOCK * F::E * sizeof(float) + 2 * (size_t)F::L * sizeof(float2);
   static constexpr size_t bytes_solve =
       (size_t)CT * (SMV * sizeof(float2) + 3 * STG * sizeof(float)) + 2 * (size_t)F::L * sizeof(float2);
 };
@@ -80,6 +97,11 @@ __device__ __forceinline__ void cp_async8(void* dst, const void* src, bool pred)
   const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
   const int n = pred ? 8 : 0;
   asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
+}
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(dst);
+  const int n = pred ? 16 : 0;
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(src), "r"(n) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
@@ -99,7 +121,7 @@ __device__ __forceinline__ void stage_twiddles(const RegInst& I, float2* s_tw1, 
 // Gohberg-Semencul core (Algorithm 1 on the bordered matrix): x natural
 // (x[q] = Q v1 at t + TT q) -> x natural (vhat).  lam tables natural order
 // (global memory); tw1 and tw may be in global or shared memory.
-template <int LOGL>
+template <int LOGL, bool WARP = false>
 __device__ __forceinline__ void gs_reg(float2* x, float2* sm, int t, const float2* __restrict__ tw1,
                                        const float2* __restrict__ tw, const float2* __restrict__ lam_s,
                                        const float2* __restrict__ lam_c) {
@@ -109,12 +131,12 @@ __device__ __forceinline__ void gs_reg(float2* x, float2* sm, int t, const float
 #pragma unroll 1
   for (int round = 0; round < 2; ++round) {
     const float2* lam = round == 0 ? lam_s : lam_c;
-    F::fwd(x, sm, t, tw1);
+    F::template fwd<WARP>(x, sm, t, tw1);
     static_for<0, F::E>([&](auto rc) {
       constexpr int r = decltype(rc)::value;
       x[r] = cmul(x[r], __ldg(&lam[F::template freq_index<r>(t)]));
     });
-    F::inv(x, sm, t, tw1);
+    F::template inv<WARP>(x, sm, t, tw1);
     if (round == 0) {
       static_for<0, F::E>([&](auto qc) {
         constexpr int q = decltype(qc)::value;
@@ -167,7 +189,7 @@ __device__ __forceinline__ float real_at(const float2* sm, int k) {
 // Every kernel handles one instance per blockIdx.y (a batch of independent
 // problems with the same FFT length); blocks beyond an instance's extent exit.
 template <int LOGL, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ RegBatch B) {
+__global__ void __launch_bounds__(BLOCK, 4) kr_rows_r2c(const __grid_constant__ RegBatch B) {
   using F = rf::RegFFT<float, LOGL>;
   using C = RowCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -195,9 +217,10 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ 
   });
   cp_async_wait_all();
   __syncthreads();
-  F::fwd(x, sm, t, s_tw1);
+  // a row vector belongs to TT threads of one warp: warp barriers from here
+  F::template fwd<true>(x, sm, t, s_tw1);
   store_freq<LOGL>(x, sm, t);
-  __syncthreads();
+  __syncwarp();
   if (!valid) return;
   float2* srow = I.S + (size_t)row * F::L;
 #pragma unroll 2
@@ -214,82 +237,85 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_r2c(const __grid_constant__ 
 // ---------------------------------------------------------------------------
 // Items: 0 = x-frequency 0 (real part of slot 0), 1 = x-frequency N' (imag part
 // of slot 0), i >= 2 = x-frequency i - 1 (slot i - 1).  Each item has two
-// vectors (even / odd y-frequency halves) in consecutive columns c = 2 i + h.
+// vectors (even / odd y-frequency halves), vectors c = 2 i + h of the block.
+// A vector belongs to TT consecutive threads of one warp, so its transforms
+// synchronise the warp only.  The block's columns and symbol rows arrive in
+// shared memory by cp.async, so no registers are held while they are in
+// flight.
 template <int LOGL, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__ RegBatch B) {
+__global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_cols_conv(
+    const __grid_constant__ RegBatch B) {
   using F = rf::RegFFT<float, LOGL>;
-  using C = ColCfg<LOGL, BLOCK>;
+  using C = ConvCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const RegInst& I = B.in[blockIdx.y];
   const int N = I.N, Np = F::L;
-  const int c = threadIdx.x % C::CT, t = threadIdx.x / C::CT;
-  const int item = blockIdx.x * (C::CT / 2) + (c >> 1);
-  const int h = c & 1;
-  const bool valid = item <= Np;
-  const int k1 = (item == 0) ? 0 : (item == 1 ? Np : item - 1);
-  const int slot = (item <= 1 || !valid) ? 0 : item - 1;
-  float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
-  float* ls = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::CT * C::SMV);
-  // twiddles from shared memory: the transforms read them in their inner
-  // stages, where global (L1) loads would stall the few resident warps
-  float2* s_tw1 = reinterpret_cast<float2*>(ls + BLOCK * F::E);
+  const int c = threadIdx.x / F::TT, t = threadIdx.x % F::TT;
+  float* s_lam = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::CT * C::SMV);
+  float2* s_tw1 = reinterpret_cast<float2*>(s_lam + C::CT * F::L);
   float2* s_tw = s_tw1 + F::L;
-  for (int e = threadIdx.x; e < F::L; e += BLOCK) {
-    cp_async8(&s_tw1[e], I.tw1 + e, true);
-    cp_async8(&s_tw[e], I.tw + e, true);
+  const float2* twh = C::STAGE_TW ? s_tw : I.tw;   // tw[j] from shared or global memory
+  if constexpr (C::STAGE_TW)
+    for (int e = threadIdx.x; e < F::L; e += BLOCK) cp_async8(&s_tw[e], I.tw + e, true);
+  // item, x-frequency and spectrum slot of vector cc of this block
+  auto item_of = [&](int cc) { return (int)blockIdx.x * (C::CT / 2) + (cc >> 1); };
+  auto slot_of = [&](int it) { return (it <= 1 || it > Np) ? 0 : it - 1; };
+  auto kx_of = [&](int it) { return (it == 0 || it > Np) ? 0 : (it == 1 ? Np : it - 1); };
+  for (int e = threadIdx.x; e < F::L; e += BLOCK) cp_async8(&s_tw1[e], I.tw1 + e, true);
+  // the symbol rows (16-byte pieces; a row is L floats)
+  for (int e = threadIdx.x; e < C::CT * (F::L / 4); e += BLOCK) {
+    const int cc = e / (F::L / 4), p = e % (F::L / 4);
+    const float* src = I.lreg + ((size_t)kx_of(item_of(cc)) * 2 + (cc & 1)) * Np + 4 * p;
+    cp_async16(s_lam + cc * F::L + 4 * p, src, true);
+  }
+  // the columns, rows 0 .. N-1 (zero-filled to L): thread -> (vector, row) with
+  // the vectors fastest, so that a warp's copies cover whole row segments
+  for (int e = threadIdx.x; e < C::CT * F::L; e += BLOCK) {
+    const int cc = e % C::CT, j = e / C::CT, it = item_of(cc);
+    float2* dst = reinterpret_cast<float2*>(smem_raw) + cc * C::SMV + pad32(j);
+    cp_async8(dst, I.S + (size_t)(j < N ? j : 0) * Np + slot_of(it), it <= Np && j < N);
   }
   cp_async_commit();
-  // the column and this thread's symbol values (frequency layout) are loaded
-  // together (all loads in flight), the symbol values parked in shared memory
-  const float* lrow = I.lreg + ((size_t)(valid ? k1 : 0) * 2 + h) * Np;
+  cp_async_wait_all();
+  __syncthreads();
+
+  const int item = item_of(c), h = c & 1;
+  float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
+  const float* lam = s_lam + c * F::L;
   float2 x[F::E];
-  float lv[F::E];
+  load_nat<LOGL>(x, sm, t);
+  __syncwarp();
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
-    const int j = t + F::TT * q;
-    x[q] = (valid && j < N) ? I.S[(size_t)j * Np + slot] : make_float2(0.f, 0.f);
-    lv[q] = __ldg(lrow + F::template freq_index<q>(t));
-  });
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    const int j = t + F::TT * q;
     float2 val = x[q];
     if (item == 0) val.y = 0.f;
     else if (item == 1) val = make_float2(val.y, 0.f);
-    x[q] = val;
-    ls[q * BLOCK + threadIdx.x] = lv[q];
+    // odd half: y-frequencies 2 k2 + 1 of the length-2L transform
+    x[q] = h ? cmul(val, twh[t + F::TT * q]) : val;
   });
-  cp_async_wait_all();
-  __syncthreads();
-  if (h) {
-    static_for<0, F::E>([&](auto qc) {
-      constexpr int q = decltype(qc)::value;
-      x[q] = cmul(x[q], s_tw[t + F::TT * q]);
-    });
-  }
-  F::fwd(x, sm, t, s_tw1);
+  F::template fwd<true>(x, sm, t, s_tw1);
   static_for<0, F::E>([&](auto rc) {
     constexpr int r = decltype(rc)::value;
-    x[r] = cscale(x[r], ls[r * BLOCK + threadIdx.x]);
+    x[r] = cscale(x[r], lam[F::template freq_index<r>(t)]);
   });
-  F::inv(x, sm, t, s_tw1);
+  F::template inv<true>(x, sm, t, s_tw1);
   store_nat<LOGL>(x, sm, t);
   __syncthreads();
-  if (!valid || h != 0 || item == 1) return;
-  const float2* smo = sm + C::SMV;
-#pragma unroll 2
-  for (int q = 0; q < F::E; ++q) {
-    const int j = t + F::TT * q;
-    if (j < N) {
-      const float2 w = s_tw[j];
-      const float2 y = cadd(sm[pad32(j)], cmulc(smo[pad32(j)], w));
-      if (item == 0) {
-        // the x-frequency N' result lives in the next item's two vectors
-        const float2 yn = cadd(sm[2 * C::SMV + pad32(j)], cmulc(sm[3 * C::SMV + pad32(j)], w));
-        I.S[(size_t)j * Np] = make_float2(y.x, yn.x);
-      } else {
-        I.S[(size_t)j * Np + slot] = y;
-      }
+  // even + conj-twiddled odd half -> rows 0 .. N-1 of each item's column; the
+  // threads walk (item, row) with the items fastest.  Item 0 also holds the
+  // x-frequency N' result (item 1's pair) in the imaginary part of slot 0.
+  const float2* base = reinterpret_cast<const float2*>(smem_raw);
+  for (int e = threadIdx.x; e < (C::CT / 2) * N; e += BLOCK) {
+    const int i = e % (C::CT / 2), j = e / (C::CT / 2), it = item_of(2 * i);
+    if (it > Np || it == 1) continue;
+    const float2 w = twh[j];
+    const float2* se = base + (2 * i) * C::SMV;
+    const float2 y = cadd(se[pad32(j)], cmulc(se[C::SMV + pad32(j)], w));
+    if (it == 0) {
+      const float2 yn = cadd(se[2 * C::SMV + pad32(j)], cmulc(se[3 * C::SMV + pad32(j)], w));
+      I.S[(size_t)j * Np] = make_float2(y.x, yn.x);
+    } else {
+      I.S[(size_t)j * Np + slot_of(it)] = y;
     }
   }
 }
@@ -298,7 +324,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_conv(const __grid_constant__
 // DENSE: the dense-inverse form stops after B^n, which it writes to W (FP32)
 // and, split into BF16 pairs, to Bh / Bl (the first sweep GEMM's A operand).
 template <int LOGL, int BLOCK, bool DENSE = false>
-__global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant__ RegBatch B) {
+__global__ void __launch_bounds__(BLOCK, 4) kr_rows_solve(const __grid_constant__ RegBatch B) {
   using F = rf::RegFFT<float, LOGL>;
   using C = RowCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -310,24 +336,21 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
   const bool valid = row < N;
   const int rrow = valid ? row : 0;
   float2* sm = reinterpret_cast<float2*>(smem_raw) + v * C::SMV;
-  float* us = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV) + v * C::STG;
-  float2* s_tw1 = reinterpret_cast<float2*>(
-      reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV) + C::VB * C::STG);
+  float2* s_tw1 = reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV;
   float2* s_tw = s_tw1 + F::L;
   stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
-  // stage the spectrum row and the u^n row (the first step reads phi2 from
-  // global memory)
+  // stage the spectrum row (u^n, and phi2 on the first step, are read in the
+  // B^n epilogue together with the remainder)
   const float2* srow = I.S + (size_t)rrow * Np;
-  const float* ur = I.u_hi + (size_t)rrow * N;
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int k = t + F::TT * q;
     cp_async8(&sm[pad32(k)], srow + k, valid);
-    cp_async4(&us[k], ur + (k < N ? k : 0), valid && k < N);
   });
   cp_async_commit();
   cp_async_wait_all();
   __syncthreads();
+  // a row vector belongs to TT threads of one warp: warp barriers from here
   // half spectrum X[k] -> Z[k] = E + i O (spectrum of z[n] = x[2n] + i x[2n+1]),
   // in place on partner pairs (k, Np - k)
 #pragma unroll 2
@@ -350,13 +373,13 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
       sm[pad32(kp)] = cadd(Eq, cmul_pi(Oq));
     }
   }
-  __syncthreads();
+  __syncwarp();
   float2 x[F::E];
   load_freq<LOGL>(x, sm, t);
-  __syncthreads();
-  F::inv(x, sm, t, s_tw1);
+  __syncwarp();
+  F::template inv<true>(x, sm, t, s_tw1);
   store_nat<LOGL>(x, sm, t);
-  __syncthreads();
+  __syncwarp();
   // B^n in place: sm[n] holds the convolution at 2n, 2n+1 (real view).  The
   // remainder pairs of four q are loaded before any of them is stored (the
   // loads overlap instead of waiting one after another).
@@ -364,13 +387,14 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
   const size_t rbase = (size_t)rrow * N;
 #pragma unroll 1
   for (int q0 = 0; q0 < F::E; q0 += 4) {
-    float ch[8], cl[8];
+    float ch[8], cl[8], uv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int x = 2 * (t + F::TT * (q0 + (j >> 1))) + (j & 1);
       const bool ok = valid && x < N;
       ch[j] = ok ? I.C_hi[rbase + x] : 0.f;
       cl[j] = ok ? I.C_lo[rbase + x] : 0.f;
+      uv[j] = ok ? I.u_hi[rbase + x] : 0.f;
     }
 #pragma unroll
     for (int j2 = 0; j2 < 4; ++j2) {
@@ -390,7 +414,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
           const float c = s + l2;
           I.C_hi[rbase + x] = c;
           I.C_lo[rbase + x] = l2 - (c - s);
-          float gs = g_of_r<float>(I.gkind, us[x]);
+          float gs = g_of_r<float>(I.gkind, uv[2 * j2 + e]);
           if (I.F) gs += I.fsc * I.F[rbase + x];
           const float gg = tau2 * gs;
           b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
@@ -399,7 +423,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
       sm[pad32(n)] = make_float2(b[0], b[1]);
     }
   }
-  __syncthreads();
+  __syncwarp();
   if constexpr (DENSE) {
     if (!valid) return;
     float* wrow = I.W + (size_t)row * N;
@@ -422,10 +446,10 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_rows_solve(const __grid_constant_
     const int k = t + F::TT * q;
     x[q] = cmul(make_float2(real_at(sm, k), real_at(sm, Np - 1 - k)), s_tw[k]);
   });
-  __syncthreads();
-  gs_reg<LOGL>(x, sm, t, s_tw1, s_tw, I.lam_s, I.lam_c);
+  __syncwarp();
+  gs_reg<LOGL, true>(x, sm, t, s_tw1, s_tw, I.lam_s, I.lam_c);
   store_nat<LOGL>(x, sm, t);
-  __syncthreads();
+  __syncwarp();
   if (!valid) return;
   // (H^-1 B)[k] = Re vhat[k] + Im vhat[Np-1-k] + sum_q G[k,q] ybot[q],
   // ybot[q] = Re vhat[N+q] + Im vhat[r-1-q]
@@ -528,11 +552,13 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
 
 constexpr int kRowBlock = 128;
 constexpr int kColBlock = 128;
+constexpr int kConvBlock = 128;
 
 template <int LOGL>
 cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev, bool dense) {
   using RC = RowCfg<LOGL, kRowBlock>;
   using CC = ColCfg<LOGL, kColBlock>;
+  using VC = ConvCfg<LOGL, kConvBlock>;
   constexpr int Np = 1 << LOGL;
   static bool attr_done = false;
   if (!attr_done) {
@@ -542,19 +568,19 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
                          (int)RC::bytes_solve);
     cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)RC::bytes_solve);
-    cudaFuncSetAttribute(kr_cols_conv<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)CC::bytes_conv);
+    cudaFuncSetAttribute(kr_cols_conv<LOGL, kConvBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)VC::bytes);
     cudaFuncSetAttribute(kr_cols_solve<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)CC::bytes_solve);
     attr_done = true;
   }
   const dim3 rgrid((max_n + RC::VB - 1) / RC::VB, b.count);
-  const dim3 cgrid((Np + 1 + CC::CT / 2 - 1) / (CC::CT / 2), b.count);
+  const dim3 cgrid((Np + 1 + VC::CT / 2 - 1) / (VC::CT / 2), b.count);
   const dim3 sgrid((max_n + CC::CT - 1) / CC::CT, b.count);
   if (ev) cudaEventRecord(ev[0], st);
   kr_rows_r2c<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_r2c, st>>>(b);
   if (ev) cudaEventRecord(ev[1], st);
-  kr_cols_conv<LOGL, kColBlock><<<cgrid, kColBlock, CC::bytes_conv, st>>>(b);
+  kr_cols_conv<LOGL, kConvBlock><<<cgrid, kConvBlock, VC::bytes, st>>>(b);
   if (ev) cudaEventRecord(ev[2], st);
   if (dense) {
     kr_rows_solve<LOGL, kRowBlock, true><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
