@@ -336,7 +336,7 @@ def algorithmic(N, Np, es, dense=False):
     """Per-launch algorithmic work of the four timed phases of one instance,
     for the roofline: [(bytes, flops, bound)].  FFT flops are the nominal
     5 L log2 L of a complex FFT of length L; a split-BF16 sweep GEMM counts
-    three BF16 products of 2 N^3 flops."""
+    three BF16 products of 2 N^3 flops (both sweeps: 12 N^3)."""
     cs = 2 * es
     fft = 5.0 * Np * math.log2(Np)
     r2c = (N * N * es + N * Np * cs, N * fft, "alu")
@@ -344,10 +344,13 @@ def algorithmic(N, Np, es, dense=False):
     if not dense:
         return [r2c, conv, (N * Np * cs + 2 * N * N * es, N * 5 * fft, "alu"),
                 (4 * N * N * es, N * 4 * fft, "alu")]
-    gemm_bytes = 4 * N * N * 2 + 3 * N * N * es
-    # phase 2 is the B^n kernel followed by the x-sweep GEMM (one event pair)
-    return [r2c, conv, (N * Np * cs + 2 * N * N * es + 4 * N * N + gemm_bytes, N * fft + 6.0 * N ** 3, "mixed"),
-            (gemm_bytes + 4 * N * N * es, 6.0 * N ** 3, "tensor")]
+    # phase 2: the B^n kernel (spectrum row in; remainder pair read and
+    # written; u^n in; W and its BF16 pair out); phase 3: both sweep GEMMs in
+    # one launch (x: B pair, E pair, W in place, W^T pair out; y: E pair, W^T
+    # pair, W in, the state triple read and written)
+    rows = (N * Np * cs + 6 * N * N * es + 4 * N * N, N * fft, "alu")
+    gemms = (24 * N * N + 9 * N * N * es, 12.0 * N ** 3, "tensor")
+    return [r2c, conv, rows, gemms]
 
 
 def roofline_of(phase_ms, N, Np, dense, ninst, workload):
@@ -356,7 +359,7 @@ def roofline_of(phase_ms, N, Np, dense, ninst, workload):
     reg = Np <= 1024
     pre = "kr_" if reg else "k_"
     if dense:
-        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve<dense>+k_tc_gemm(x)", "k_tc_gemm(y)"]
+        names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve<dense>", "k_tc_gemm(x+y)"]
     else:
         names = [pre + "rows_r2c", pre + "cols_conv", pre + "rows_solve", pre + "cols_solve"]
     alg = algorithmic(N, Np, 4, dense)
@@ -819,7 +822,9 @@ def main():
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "how": "C ABI with pinned host buffers: sadi_set_initial once, then per step "
                            "sadi_batch_step(1) + sadi_get of u^{n+1} for each instance; wall clock"},
-            "gpu_launches": (5 if dense else 4) * a.steps,
+            # four launches per step in either form (dense: three FFT-path
+            # kernels and one launch of both sweep GEMMs), all instances in each
+            "gpu_launches": 4 * a.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

@@ -235,10 +235,12 @@ sadi_status sadi_set_tiles(sadi_ctx *ctx, int rows, int conv_cols, int solve_col
 sadi_status sadi_get_tiles(const sadi_ctx *ctx, int tiles[3]);
 
 /* Per-kernel timing (a tracing aid).  enable != 0: every later step records
- * CUDA events on the context's stream around each of its four kernels
+ * CUDA events on the context's stream around each of its four phases
  * (0 row FFT, 1 column convolution, 2 row inverse FFT + RHS + x sweep,
- * 3 y sweep + leapfrog); enable = 0 stops recording.  Recording adds event
- * records between the kernels, so time throughput with it disabled. */
+ * 3 y sweep + leapfrog; in the dense-inverse form 2 is the row inverse FFT +
+ * RHS alone and 3 both sweep GEMMs, which run as one launch); enable = 0
+ * stops recording.  Recording adds event records between the kernels, so
+ * time throughput with it disabled. */
 sadi_status sadi_profile(sadi_ctx *ctx, int enable);
 
 /* Wait for the context's stream, then return in ms[4] the milliseconds

@@ -11,7 +11,7 @@
 //
 // Persistent: one CTA per SM (at most one per tile) walks the output tiles
 // of all problems of the launch, 128 x 256 when there are enough of them to
-// give every SM one, else 128 x 128 (BN below), 10 warps:
+// give every SM two, else 128 x 128 (BN below), 10 warps:
 //   * thread 0 streams 64-wide K blocks of A_hi, A_lo (128 rows) and B_hi,
 //     B_lo (BN rows, in 128-row boxes) with TMA (cp.async.bulk.tensor,
 //     128-byte swizzle) into a ring of 2 (BN = 256) or 3 (BN = 128) stages
@@ -25,10 +25,18 @@
 //     half), transpose 32 x 32 blocks through shared memory and run the
 //     epilogue of the launch (plain store, or the two fused sweep epilogues of
 //     the dense S-ADI step) with coalesced global accesses.
-// Every mbarrier wait is bounded (about 1 s of %globaltimer); on expiry the
-// CTA sets *err, the other roles stop at their next wait, the producer waits
-// (bounded) for the copies it issued, all MMAs are waited for, and the
-// tensor memory is freed before the CTA returns.
+// Problems of one launch may depend on earlier ones by 128-column panels (the
+// two sweeps of the dense step: the y sweep reads the W that the x sweep
+// stores): the last epilogue warp of a tile raises the panel counters of its
+// columns after a GPU-scope fence, and the producer of a dependent tile waits
+// (acquire) for its panels before its first copy.  All tiles of the earlier
+// problems precede those of the later ones in every CTA's walk, and such a
+// launch is cooperative, so every counter is raised by a resident CTA that
+// never waits itself.
+// Every mbarrier and counter wait is bounded (about 1 s of %globaltimer); on
+// expiry the CTA sets *err, the other roles stop at their next wait, the
+// producer waits (bounded) for the copies it issued, all MMAs are waited for,
+// and the tensor memory is freed before the CTA returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -99,6 +107,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
           dst),
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
+}
+
+// Pull one box of a tensor into L2 (no shared memory, no completion to wait
+// for): the producer runs these some K blocks ahead of its loads, so that the
+// loads of the ring find their operands in L2.
+__device__ __forceinline__ void tma_prefetch_2d(const CUtensorMap* map, int x, int y) {
+  asm volatile("cp.async.bulk.prefetch.tensor.2d.L2.global.tile [%0, {%1, %2}];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(x), "r"(y)
+               : "memory");
 }
 
 // Shared-memory matrix descriptor of a K-major tile written by TMA with the
@@ -275,6 +293,34 @@ __device__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort
   return true;
 }
 
+// Bounded wait until *cnt >= need (acquire at GPU scope), for the order
+// between problems of one launch; sets the abort flag when the time runs out.
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ bool wait_count(const int* cnt, int need, volatile int* abort_flag) {
+  if (ld_acquire(cnt) >= need) return true;
+  const uint64_t t0 = gtimer();
+  while (ld_acquire(cnt) < need) {
+    if (*abort_flag) return false;
+    if (gtimer() - t0 > WAIT_LIMIT_NS) {
+      *abort_flag = 1;
+      return false;
+    }
+    __nanosleep(128);
+  }
+  return true;
+}
+// Wait for every 128-column panel of the columns n0 .. n0 + BN - 1.
+template <int BN>
+__device__ bool wait_panels(const TcInst& in, int n0, volatile int* abort_flag) {
+  for (int p = n0 / BOX; p < (n0 + BN) / BOX; ++p)
+    if (!wait_count(in.dep_wait + p, in.dep_need, abort_flag)) return false;
+  return true;
+}
+
 // Tile t of the launch -> problem z and tile origin (m0, n0).  Tiles are
 // numbered problem by problem; inside a problem in groups of kGroupM tile
 // rows, column-major within a group, so that the tiles in flight at one time
@@ -320,6 +366,10 @@ template <int BN>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int total, int* err) {
   constexpr int STAGES = TileCfg<BN>::STAGES, STAGE_BYTES = TileCfg<BN>::STAGE_BYTES;
   constexpr int B_TILE = TileCfg<BN>::B_TILE, TMEM_COLS = TileCfg<BN>::TMEM_COLS;
+  // K blocks prefetched into L2 beyond the ring, about 192 KB per SM, for the
+  // wide tiles (large problems, operands far beyond L2); the narrow tiles of
+  // small problems run without (measured slower with it at N = 1023)
+  constexpr int PF_LEAD = BN == 256 ? 2 : 0;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* epi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
@@ -327,6 +377,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
   // bars: full[STAGES], empty[STAGES], tmem_full[2], tmem_empty[2], mma_done
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  int* epi_arrive = reinterpret_cast<int*>(tmem_slot + 2);   // per accumulator
   const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
   const uint32_t tfull0 = su32(bars + 2 * STAGES), tempty0 = su32(bars + 2 * STAGES + 2);
   const uint32_t mdone = su32(bars + 2 * STAGES + 4);
@@ -343,6 +394,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
     }
     mbar_init(mdone, 1);
     *abort_flag = 0;
+    epi_arrive[0] = epi_arrive[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 0) {
@@ -359,15 +411,46 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
   if (warp == 0) {
     if (lane == 0) {
       // ---- TMA producer ----
+      // L2 prefetch cursor (tile pt, K block pkb; sequence number pseq): it
+      // runs PF_LEAD K blocks beyond the ring, which the loads fill
+      int pt = blockIdx.x, pkb = 0, pseq = 0;
+      auto prefetch_upto = [&](int seq_end) {
+        while (pseq < seq_end && pt < total) {
+          int pz, pm0, pn0;
+          tile_coords<BN>(bt, pt, &pz, &pm0, &pn0);
+          const TcInst& pin = bt.in[pz];
+          if (pseq >= STAGES) {   // the first ring fill is loaded at once
+            tma_prefetch_2d(&pin.a_hi, pkb * BK, pm0);
+            tma_prefetch_2d(&pin.a_lo, pkb * BK, pm0);
+#pragma unroll
+            for (int j = 0; j < BN / BOX; ++j) {
+              tma_prefetch_2d(&pin.b_hi, pkb * BK, pn0 + j * BOX);
+              tma_prefetch_2d(&pin.b_lo, pkb * BK, pn0 + j * BOX);
+            }
+          }
+          ++pseq;
+          if (++pkb == pin.K / BK) {
+            pkb = 0;
+            pt += gridDim.x;
+          }
+        }
+      };
       int it = 0;
       for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
         int z, m0, n0;
         tile_coords<BN>(bt, t, &z, &m0, &n0);
         const TcInst& in = bt.in[z];
         const int nk = in.K / BK;
+        if (in.dep_wait) {
+          // the B rows are written by an earlier problem of this launch with
+          // generic stores: acquire them, then order them before the copies
+          if (!wait_panels<BN>(in, n0, abort_flag)) break;
+          asm volatile("fence.proxy.async.global;" ::: "memory");
+        }
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t use = (uint32_t)(it / STAGES);
+          if constexpr (PF_LEAD > 0) prefetch_upto(it + STAGES + PF_LEAD);
           if (it >= STAGES && !wait_or_abort(empty0 + 8 * s, (use - 1) & 1u, abort_flag)) break;
           uint8_t* st = base + s * STAGE_BYTES;
           mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
@@ -445,6 +528,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
       prefetch_epilogue<BN / 2>(in.e, m0 + quarter * 32 + lane, n0 + half * (BN / 2));
       if (!wait_or_abort(tfull0 + 8 * b, ub & 1u, abort_flag) || *abort_flag) break;
       tc_fence_after();
+      if (in.dep_wait) {
+        // the epilogue reads W of the same panels (already complete: the
+        // producer waited for them before this tile's loads)
+        bool ok = true;
+        if (lane == 0) ok = wait_panels<BN>(in, n0, abort_flag);
+        if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
+      }
       const uint32_t acc = tmem + (uint32_t)(b * TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);
 #pragma unroll 1
       for (int c = 0; c < BN / 64; ++c) {
@@ -452,6 +542,22 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
         uint32_t r[32];
         tmem_ld32(acc + (uint32_t)(cc * 32), r);
         epilogue_block(in.e, m0 + quarter * 32, n0 + cc * 32, r, tile, lane);
+      }
+      if (in.dep_signal) {
+        // publish the tile: every warp's stores, then the last of the
+        // EPI_WARPS warps (arrival count modulo EPI_WARPS per accumulator;
+        // the accumulator is freed only after this, so uses do not overlap)
+        // releases the panel counters
+        asm volatile("fence.proxy.async.global;" ::: "memory");
+        __threadfence();
+        __syncwarp();
+        if (lane == 0) {
+          const int old = atomicAdd(&epi_arrive[b], 1);
+          if (old % EPI_WARPS == EPI_WARPS - 1) {
+            __threadfence();
+            for (int p = n0 / BOX; p < (n0 + BN) / BOX; ++p) atomicAdd(in.dep_signal + p, 1);
+          }
+        }
       }
       tc_fence_before();
       __syncwarp();
@@ -553,17 +659,34 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
       return e;
     }
   }
-  // 128 x 256 tiles while they give every SM at least one; below that the
-  // 128 x 128 tiles reach more SMs, and a CTA with two of them runs the
-  // epilogue of the first under the MMAs of the second
-  if (even && boxes / 2 >= sms) {
+  // 128 x 256 tiles (fewer operand bytes per flop) once they give every SM
+  // two or more; below that the 128 x 128 tiles balance better (measured:
+  // three N = 1023 problems per launch run faster as 192 narrow tiles than
+  // as 96 wide ones), and a CTA with several runs the epilogue of one under
+  // the MMAs of the next
+  // tiles of a waiting problem spin on counters that other CTAs raise, so
+  // all CTAs must be resident together: a cooperative launch (grid <= SMs,
+  // one CTA per SM by its shared memory)
+  bool coop = false;
+  for (int k = 0; k < b.count; ++k) coop = coop || b.in[k].dep_wait;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeCooperative;
+  attr[0].val.cooperative = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.blockDim = dim3(GEMM_THREADS);
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = coop ? 1 : 0;
+  if (even && boxes / 2 >= 2 * sms) {
     const int total = boxes / 2;
-    k_tc_gemm<256><<<sms, GEMM_THREADS, psmem_bytes<256>(), st>>>(b, total, err);
-  } else {
-    const int total = boxes;
-    k_tc_gemm<128><<<total < sms ? total : sms, GEMM_THREADS, psmem_bytes<128>(), st>>>(b, total, err);
+    cfg.gridDim = dim3(sms);
+    cfg.dynamicSmemBytes = psmem_bytes<256>();
+    return cudaLaunchKernelEx(&cfg, k_tc_gemm<256>, b, total, err);
   }
-  return cudaGetLastError();
+  const int total = boxes;
+  cfg.gridDim = dim3(total < sms ? total : sms);
+  cfg.dynamicSmemBytes = psmem_bytes<128>();
+  return cudaLaunchKernelEx(&cfg, k_tc_gemm<128>, b, total, err);
 }
 
 cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,

@@ -54,7 +54,7 @@ void free_all(sadi_ctx* c) {
                   c->ubuf[0], c->ubuf[1], c->ulo, c->F, c->phi2, c->S,      c->W,      c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
-  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->Chi, c->Clo};
+  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->tcdep, c->Chi, c->Clo};
   for (void* p : dense)
     if (p) cudaFree(p);
   for (auto& a : c->ev_pool)
@@ -133,6 +133,7 @@ sadi_status setup_dense(sadi_ctx* c) {
       return fail(c, SADI_ENOMEM, "cudaMalloc(dense-inverse buffers) failed");
   }
   CK(cudaMalloc(&c->tcerr, sizeof(int)), "cudaMalloc(error flag)");
+  CK(cudaMalloc(&c->tcdep, sizeof(int) * (np / kTcBox)), "cudaMalloc(panel counters)");
   cudaStream_t st = c->stream;
   CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), st), "error flag");
   for (int k = 2; k < 6; ++k) CK(cudaMemsetAsync(*bufs[k], 0, bytes, st), "dense padding");
@@ -499,16 +500,24 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
                           static_cast<const float*>(c->ubuf[1]), static_cast<const float*>(c->phi2), c->S,
                           static_cast<float*>(c->W), c->Chi, c->Clo, c->Bh, c->Bl, c->npad, st_, ev);
   }
-  // x sweeps of all members, then y sweeps (each in launches of <= kTcMaxBatch)
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], st_);
+  // Both sweeps of up to kTcMaxBatch / 2 members per launch: the x-sweep
+  // problems first, then the y-sweep problems, whose tiles wait per
+  // 128-column panel for the x-sweep tiles that store W (and its transposed
+  // split) there, so that the y sweep of one member runs beside the x sweep
+  // of the next.
   static thread_local TcBatch tb;
-  for (int pass = 0; pass < 2 && e == cudaSuccess; ++pass) {
-    for (int k0 = 0; e == cudaSuccess && k0 < count; k0 += kTcMaxBatch) {
-      const int m = count - k0 < kTcMaxBatch ? count - k0 : kTcMaxBatch;
-      tb.count = m;
-      for (int k = 0; k < m; ++k) {
-        const sadi_ctx* ck = cs[k0 + k];
-        tb.in[k] = pass == 0 ? *ck->tc_x : *ck->tc_y;
-        TcEpi& ep = tb.in[k].e;
+  constexpr int kPer = kTcMaxBatch / 2;
+  for (int k0 = 0; e == cudaSuccess && k0 < count; k0 += kPer) {
+    const int m = count - k0 < kPer ? count - k0 : kPer;
+    tb.count = 2 * m;
+    for (int k = 0; k < m && e == cudaSuccess; ++k) {
+      const sadi_ctx* ck = cs[k0 + k];
+      e = cudaMemsetAsync(ck->tcdep, 0, sizeof(int) * (ck->npad / kTcBox), st_);
+      for (int pass = 0; pass < 2; ++pass) {
+        TcInst& in = tb.in[pass * m + k];
+        in = pass == 0 ? *ck->tc_x : *ck->tc_y;
+        TcEpi& ep = in.e;
         ep = TcEpi{};
         ep.m_valid = ep.n_valid = ck->g.N;
         ep.C = static_cast<float*>(ck->W);
@@ -519,6 +528,9 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
           ep.t_hi = ck->WTh;
           ep.t_lo = ck->WTl;
           ep.ldt = ck->npad;
+          in.dep_wait = nullptr;
+          in.dep_need = 0;
+          in.dep_signal = ck->tcdep;
         } else {
           ep.mode = kTcSweepY;
           ep.u_hi = static_cast<float*>(ck->ubuf[0]);
@@ -526,12 +538,15 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
           ep.u_d = static_cast<float*>(ck->ubuf[1]);
           ep.ldu = ck->g.N;
           ep.first = ck->n == 0 ? 1 : 0;
+          in.dep_wait = ck->tcdep;
+          in.dep_need = ck->tc_x->tiles_m;   // x-sweep tiles per column panel
+          in.dep_signal = nullptr;
         }
       }
-      e = launch_tc_gemm(tb, cs[k0]->tcerr, st_);
     }
-    if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3 + pass], st_);
+    if (e == cudaSuccess) e = launch_tc_gemm(tb, cs[k0]->tcerr, st_);
   }
+  if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], st_);
   if (e != cudaSuccess) {
     for (int k = 0; k < count; ++k) cuda_fail(cs[k], e, "dense step launch");
     return SADI_ECUDA;

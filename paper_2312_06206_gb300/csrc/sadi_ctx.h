@@ -81,6 +81,7 @@ struct sadi_ctx {
   int npad = 0;
   unsigned short *Eh = nullptr, *El = nullptr, *Bh = nullptr, *Bl = nullptr, *WTh = nullptr, *WTl = nullptr;
   int* tcerr = nullptr;             // device flag: a bounded wait in a GEMM ran out
+  int* tcdep = nullptr;             // per 128-column panel: x-sweep tiles stored (zeroed each step)
   std::unique_ptr<TcInst> tc_x, tc_y;
   std::string tune_log;             // choice of sadi_autotune
 };

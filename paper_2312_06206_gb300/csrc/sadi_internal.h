@@ -188,6 +188,15 @@ struct TcInst {
   TcEpi e;
   int K;                      // padded contraction length (multiple of 64)
   int tiles_m, boxes_n;       // padded M / 128 and N / 128 of this problem
+  // Order between problems of one launch (nullptr: none), by 128-column
+  // panels: a tile of a problem with dep_wait starts (and reads its epilogue
+  // inputs) once dep_wait[p] >= dep_need for each panel p of its B rows; a
+  // problem with dep_signal adds 1 to dep_signal[p] for each panel p of a
+  // tile's output columns once the tile's epilogue has stored it.  Waiting
+  // problems must come after the problems they wait for in the launch.
+  int* dep_wait;
+  int dep_need;
+  int* dep_signal;
 };
 // passed by value as a __grid_constant__ kernel parameter (about 10 KB)
 struct TcBatch {
@@ -201,8 +210,9 @@ cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, cons
                             int M, int N, int K);
 // one persistent launch for all b.count problems: at most one CTA per SM walks
 // the output tiles of every problem, 128 x 256 tiles when they number at least
-// one per SM (and every N is a multiple of 256), else 128 x 128; *err (or the
-// problem's own e.err) set on a timed-out wait
+// two per SM (and every N is a multiple of 256), else 128 x 128; *err (or the
+// problem's own e.err) set on a timed-out wait.  With dependencies between
+// problems the launch is cooperative (every CTA resident at once).
 cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st);
 // FP32 rows x cols (ld src_ld) -> zero-padded prow x pcol BF16 hi / lo
 cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,

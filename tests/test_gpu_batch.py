@@ -47,9 +47,10 @@ def test_graph_replay_matches_batch_stepping_bitwise(S):
     S.sadi_batch_step(run, 1)                 # the n = 0 step is not replayed
     g = S.SadiGraph(run, nsteps=2)
     assert all(s.get()[1] == 1 for s in run)  # capture runs nothing
-    # two steps: register groups (N' = 64 FP32, N' = 256 dense: 3 kernels + 2
-    # GEMMs), two shared-memory contexts (4 and 3 + 2 kernels)
-    assert g.sadi_graph_kernels() == 2 * (4 + 5 + 4 + 5)
+    # two steps: register groups (N' = 64 FP32: 4 kernels; N' = 256 dense: 3
+    # kernels + one launch of both sweep GEMMs), two shared-memory contexts
+    # (4, and 3 + 1)
+    assert g.sadi_graph_kernels() == 2 * (4 + 4 + 4 + 4)
     g.launch(3)
     for s, w in zip(run, want):
         u, n = s.get()
