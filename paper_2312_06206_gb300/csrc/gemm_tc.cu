@@ -183,22 +183,19 @@ __device__ __forceinline__ void epilogue_block(const TcEpi& e, int rowbase, int 
       if (row < e.m_valid && cok) e.C[(size_t)row * e.ldc + col] = tile[rr * EPI_LD + lane];
     }
   } else if (e.mode == kTcSweepX) {
-    // W = B + B E (in place over B)
-#pragma unroll 1
-    for (int g = 0; g < 32; g += 8) {
-      float wv[8];
+    // W = B + B E (in place over B); all 32 rows of B loaded at once
+    float wv[32];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int row = rowbase + g + q;
-        wv[q] = (row < e.m_valid && cok) ? e.C[(size_t)row * e.ldc + col] : 0.f;
-      }
+    for (int q = 0; q < 32; ++q) {
+      const int row = rowbase + q;
+      wv[q] = (row < e.m_valid && cok) ? e.C[(size_t)row * e.ldc + col] : 0.f;
+    }
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int row = rowbase + g + q;
-        const float w = wv[q] + tile[(g + q) * EPI_LD + lane];
-        tile[(g + q) * EPI_LD + lane] = w;
-        if (row < e.m_valid && cok) e.C[(size_t)row * e.ldc + col] = w;
-      }
+    for (int q = 0; q < 32; ++q) {
+      const int row = rowbase + q;
+      const float w = wv[q] + tile[q * EPI_LD + lane];
+      tile[q * EPI_LD + lane] = w;
+      if (row < e.m_valid && cok) e.C[(size_t)row * e.ldc + col] = w;
     }
     __syncwarp();
     // the transposed BF16 split of W (the y-sweep GEMM's B operand): lane = row
@@ -214,36 +211,44 @@ __device__ __forceinline__ void epilogue_block(const TcEpi& e, int rowbase, int 
     }
   } else {
     // uhat = W + E W; compensated leapfrog d^{n+1} = d^n + uhat (d^1 = uhat),
-    // u^{n+1} = u^n + d^{n+1} with u = u_hi + u_lo (two-sum), in place
-#pragma unroll 1
-    for (int g = 0; g < 32; g += 8) {
-      float wv[8], dv[8], hv[8], lv[8];
+    // u^{n+1} = u^n + d^{n+1} with u = u_hi + u_lo (two-sum), in place.
+    // Groups of 8 rows, the loads of the next group issued before the
+    // current one is computed and stored (different rows: no overlap).
+    float wv[2][8], dv[2][8], hv[2][8], lv[2][8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int row = rowbase + g + q;
-        const bool ok = row < e.m_valid && cok;
-        const size_t idx = (size_t)row * e.ldu + col;
-        wv[q] = ok ? e.C[(size_t)row * e.ldc + col] : 0.f;
-        dv[q] = (ok && !e.first) ? e.u_d[idx] : 0.f;
-        hv[q] = ok ? e.u_hi[idx] : 0.f;
-        lv[q] = ok ? e.u_lo[idx] : 0.f;
-      }
+    for (int gi = 0; gi <= 4; ++gi) {
+      if (gi < 4) {
+        const int nb = gi & 1;
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        const int row = rowbase + g + q;
-        if (row < e.m_valid && cok) {
-          const float uh = wv[q] + tile[(g + q) * EPI_LD + lane];
-          const float d = dv[q] + uh;
-          const float hi = hv[q], lo = lv[q];
-          const float s = hi + d;
-          const float bb = s - hi;
-          const float err = (hi - (s - bb)) + (d - bb);
-          const float l2 = lo + err;
-          const float h2 = s + l2;
+        for (int q = 0; q < 8; ++q) {
+          const int row = rowbase + 8 * gi + q;
+          const bool ok = row < e.m_valid && cok;
           const size_t idx = (size_t)row * e.ldu + col;
-          e.u_hi[idx] = h2;
-          e.u_lo[idx] = l2 - (h2 - s);
-          e.u_d[idx] = d;
+          wv[nb][q] = ok ? e.C[(size_t)row * e.ldc + col] : 0.f;
+          dv[nb][q] = (ok && !e.first) ? e.u_d[idx] : 0.f;
+          hv[nb][q] = ok ? e.u_hi[idx] : 0.f;
+          lv[nb][q] = ok ? e.u_lo[idx] : 0.f;
+        }
+      }
+      if (gi > 0) {
+        const int g = gi - 1, cb = g & 1;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          const int row = rowbase + 8 * g + q;
+          if (row < e.m_valid && cok) {
+            const float uh = wv[cb][q] + tile[(8 * g + q) * EPI_LD + lane];
+            const float d = dv[cb][q] + uh;
+            const float hi = hv[cb][q], lo = lv[cb][q];
+            const float s = hi + d;
+            const float bb = s - hi;
+            const float err = (hi - (s - bb)) + (d - bb);
+            const float l2 = lo + err;
+            const float h2 = s + l2;
+            const size_t idx = (size_t)row * e.ldu + col;
+            e.u_hi[idx] = h2;
+            e.u_lo[idx] = l2 - (h2 - s);
+            e.u_d[idx] = d;
+          }
         }
       }
     }
