@@ -348,6 +348,16 @@ __global__ void __launch_bounds__(BLOCK, 4) kr_rows_solve(const __grid_constant_
     cp_async8(&sm[pad32(k)], srow + k, valid);
   });
   cp_async_commit();
+  // the rows the B^n epilogue reads (remainder pair, u^n) into L2 while the
+  // transform runs: one request per 128-byte line, valid elements only
+  if (valid) {
+    const size_t rb = (size_t)row * N;
+    for (int c0 = 32 * t; c0 < N; c0 += 32 * F::TT) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_hi + rb + c0));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_lo + rb + c0));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.u_hi + rb + c0));
+    }
+  }
   cp_async_wait_all();
   __syncthreads();
   // a row vector belongs to TT threads of one warp: warp barriers from here
