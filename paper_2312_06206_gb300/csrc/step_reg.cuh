@@ -22,11 +22,13 @@ namespace regk {
 
 using rf::static_for;
 
-template <typename T>
-__device__ __forceinline__ T g_of_r(int kind, T u) {
+// g(u) of the FP32 register path.  -sin u uses the hardware approximation:
+// its absolute error (about 2^-21 on [-pi, pi], growing slowly with |u|) is
+// scaled by tau^2 in B^n, far below the FP32 rounding of B^n itself.
+__device__ __forceinline__ float g_of_r(int kind, float u) {
   if (kind == 1) return -u * u * u;
-  if (kind == 2) return -sin(u);
-  return T(0);
+  if (kind == 2) return -__sinf(u);
+  return 0.f;
 }
 
 __host__ __device__ constexpr int pad32(int k) { return k + (k >> 5); }
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(BLOCK, 4) kr_rows_solve(const __grid_constant_
           const float c = s + l2;
           I.C_hi[rbase + x] = c;
           I.C_lo[rbase + x] = l2 - (c - s);
-          float gs = g_of_r<float>(I.gkind, uv[2 * j2 + e]);
+          float gs = g_of_r(I.gkind, uv[2 * j2 + e]);
           if (I.F) gs += I.fsc * I.F[rbase + x];
           const float gg = tau2 * gs;
           b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
