@@ -54,6 +54,7 @@ void free_all(sadi_ctx* c) {
                   c->ubuf[0], c->ubuf[1], c->ulo, c->F, c->phi2, c->S,      c->W,      c->stage};
   for (void* p : ptrs)
     if (p) cudaFree(p);
+  conv3_free(&c->c3);
   void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->tcdep, c->Chi, c->Clo};
   for (void* p : dense)
     if (p) cudaFree(p);
@@ -118,9 +119,16 @@ sadi_status alloc_state(sadi_ctx* c) {
   const size_t ses = (c->prec != SADI_PREC_FP64 && c->g.Np <= 4096) ? sizeof(double) : es;
   CK(cudaMalloc(&c->S, (size_t)c->g.N * c->g.Np * 2 * ses), "cudaMalloc(spectrum)");
   CK(cudaMalloc(&c->W, nn * es), "cudaMalloc(sweep)");
+  // FP32 forms on the shared-memory engine (N' = 2048 .. 8192): buffers and
+  // tables of the three-pass column convolution (kept once allocated)
+  if (c->prec != SADI_PREC_FP64 && !c->reg_path && conv3_supported(c->g.logNp) && !c->c3.ZE)
+    CK(conv3_setup(c->g.Np, c->g.logNp, c->lpb32, &c->c3, c->stream), "three-pass convolution setup");
   (void)e;
   return SADI_OK;
 }
+
+// The three-pass column convolution of a context, where it has one.
+const Conv3* c3_of(const sadi_ctx* c) { return c->c3.ZE ? &c->c3 : nullptr; }
 
 // Buffers, dense inverse and GEMM tensor maps of the dense-inverse form (once).
 sadi_status setup_dense(sadi_ctx* c) {
@@ -350,7 +358,7 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
       CK(launch_remainder<double>(c->g, tb, default_tiles<double>(c->g.Np), c->stage, c->S, c->Chi, c->Clo, st),
          "starting remainder");
     } else {
-      StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+      StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32, c3_of(c)};
       CK(launch_remainder<float>(c->g, tb, default_tiles<float>(c->g.Np), static_cast<const float*>(c->ubuf[0]),
                                  c->S, c->Chi, c->Clo, st),
          "starting remainder");
@@ -438,7 +446,7 @@ sadi_status step_smem(sadi_ctx* c, cudaEvent_t* ev, cudaStream_t st) {
                             static_cast<double*>(uoth), nullptr, static_cast<const double*>(c->phi2), c->S,
                             static_cast<double*>(c->W), st, ev);
   } else {
-    StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+    StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32, c3_of(c)};
     float* hi = static_cast<float*>(c->ubuf[0]);
     e = launch_step<float>(c->g, tb, c->tiles32, rp, hi, static_cast<float*>(c->ubuf[1]), hi, c->ulo,
                            static_cast<const float*>(c->phi2), c->S, static_cast<float*>(c->W), st, ev, c->Chi,
@@ -495,7 +503,7 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
     if (count != 1) return fail(c, SADI_EINVAL, "internal: shared-memory dense group of more than one");
     RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0, c->F,
                  c->F ? std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.0};
-    StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32};
+    StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32, c3_of(c)};
     e = launch_dense_rows(c->g, tb, c->tiles32, rp, static_cast<const float*>(c->ubuf[0]),
                           static_cast<const float*>(c->ubuf[1]), static_cast<const float*>(c->phi2), c->S,
                           static_cast<float*>(c->W), c->Chi, c->Clo, c->Bh, c->Bl, c->npad, st_, ev);

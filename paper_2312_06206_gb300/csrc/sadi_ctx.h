@@ -82,6 +82,7 @@ struct sadi_ctx {
   unsigned short *Eh = nullptr, *El = nullptr, *Bh = nullptr, *Bl = nullptr, *WTh = nullptr, *WTl = nullptr;
   int* tcerr = nullptr;             // device flag: a bounded wait in a GEMM ran out
   int* tcdep = nullptr;             // per 128-column panel: x-sweep tiles stored (zeroed each step)
+  sadi::Conv3 c3;                   // FP32 forms, N' = 2048 .. 8192: three-pass column convolution
   std::unique_ptr<TcInst> tc_x, tc_y;
   std::string tune_log;             // choice of sadi_autotune
 };

@@ -63,7 +63,31 @@ struct StepTables {
   const void* lam_s;   // cx<T>[Np]
   const void* lam_c;   // cx<T>[Np]
   const T* G;          // [N * r]
+  const struct Conv3* c3 = nullptr;   // FP32, N' = 2048 .. 8192: three-pass column convolution
 };
+
+// ---- three-pass column convolution (FP32, N' = 2048 .. 8192), conv3.cu -----
+// N' = R1 x 64; ZE / ZO hold the even / odd frequency halves between the
+// passes (N' rows x CW = N' + 16 columns); Lt is the symbol re-laid for the
+// middle pass; twM[k] = exp(-2 pi i k / N'); tw1a / tw1b are the twiddles of
+// the 64-point and R1-point register transforms.
+struct Conv3 {
+  float2* ZE = nullptr;
+  float2* ZO = nullptr;
+  float* Lt = nullptr;
+  float2* twM = nullptr;
+  float2* tw1a = nullptr;
+  float2* tw1b = nullptr;
+  int CW = 0, R1 = 0, logR1 = 0;
+};
+bool conv3_supported(int logNp);   // FFT lengths where the step uses it
+// allocate and fill the buffers and tables (once per context); lpb32 is the
+// shared-memory engine's symbol table
+cudaError_t conv3_setup(int Np, int logNp, const float* lpb32, Conv3* c, cudaStream_t st);
+void conv3_free(Conv3* c);
+// the convolution of every column of the FP32 spectrum S (N x N' float2) in
+// place; tw is the float2 table exp(-2 pi i k / 2N')
+cudaError_t launch_conv3(const Conv3& c, int N, int Np, void* S, const void* tw, cudaStream_t st);
 
 // Work decomposition of the four step kernels.
 struct Tiles {

@@ -516,6 +516,19 @@ bool tiles_valid(const Geom& g, const Tiles& t) {
   return true;
 }
 
+// The column convolution: the three-pass form where the FP32 tables carry it,
+// else the single-pass shared-memory kernel (CTc slots per block).
+template <typename T>
+cudaError_t launch_cols_conv(const Geom& g, const StepTables<T>& tb, int CTc, cx<T>* S, cudaStream_t st) {
+  if constexpr (sizeof(T) == 4) {
+    if (tb.c3) return launch_conv3(*tb.c3, g.N, g.Np, S, tb.tw, st);
+  }
+  const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
+  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, reinterpret_cast<const cx<T>*>(tb.stw),
+                                                                 reinterpret_cast<const cx<T>*>(tb.tw), tb.lpb, CTc);
+  return cudaGetLastError();
+}
+
 template <typename T>
 cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl, const RhsParams& rp, const T* u_cur,
                         T* u_prev, T* u_next, T* u_lo, const T* phi2, void* Sv, T* W, cudaStream_t st,
@@ -533,7 +546,8 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   // incremental remainder (Ch != nullptr): transform the increment d = u_prev
   k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(Ch ? u_prev : u_cur, S, g, stw, tw, NR);
   if (ev) cudaEventRecord(ev[1], st);
-  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
+  cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
+  if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
   k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch,
                                                           Cl);
@@ -568,7 +582,8 @@ cudaError_t launch_remainder(const Geom& g, const StepTables<T>& tb, const Tiles
   const int NR = tl.rows, CTc = tl.conv_cols;
   const int rblocks = (g.N + NR - 1) / NR;
   k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(u, S, g, stw, tw, NR);
-  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
+  cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
+  if (ce != cudaSuccess) return ce;
   k_rows_remainder<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, g, stw, tw, NR, Ch, Cl);
   return cudaGetLastError();
 }
@@ -594,7 +609,8 @@ cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const 
   if (ev) cudaEventRecord(ev[0], st);
   k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(d, S, g, stw, tw, NR);
   if (ev) cudaEventRecord(ev[1], st);
-  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, stw, tw, tb.lpb, CTc);
+  cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
+  if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
   k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR,
                                                                  Ch, Cl, Bh, Bl, ldp);
