@@ -16,11 +16,13 @@
 //           DFT, times exp(+2 pi i j1 m2 / N');
 //   pass C (block: one j1, 16 columns): inverse 64-point DFT over m2, then
 //           even half + conj(w^j) odd half -> rows j < N of the spectrum.
-// Every global access of a block covers 16 adjacent columns of a row (128
-// bytes), where the single-pass shared-memory kernel gathers one 8-byte
-// element per row; the two halves' intermediates (N' x (N' + 16) complex
-// each) live in HBM between the passes.  The small transforms are the
-// register FFT of regfft.cuh, one vector per TT threads of a warp.
+// Every global access covers 16 adjacent columns of a row (128 bytes),
+// where the single-pass shared-memory kernel gathers one 8-byte element per
+// row; the two halves' intermediates (N' x (N' + 16) complex each) live in
+// HBM between the passes.  The small transforms are the register FFT of
+// regfft.cuh, one vector per TT threads of a warp.  Each pass is a
+// persistent loop over its work items whose next item's tiles arrive by
+// cp.async while the current one is transformed and stored.
 //
 // Columns: 0 = the real part of slot 0 (x frequency 0), N' = its imaginary
 // part (x frequency N'), 1 .. N'-1 the other slots (bit-reversed x
@@ -37,9 +39,9 @@ namespace {
 
 using rf::static_for;
 
-constexpr int kGroup = 16;           // columns per block
+constexpr int kGroup = 16;           // columns per work item
 constexpr int kR2 = 64;              // length of the strided transforms (passes A, C)
-constexpr int kTP = kGroup + 1;      // padded tile row (float2)
+constexpr int kTP = kGroup + 2;      // tile row pitch (float2): 16-byte rows, spread banks
 constexpr int kThreadsAC = 32 * 8;   // 32 vectors x 8 threads (RegFFT<6>: TT = 8)
 
 template <int LOGL>
@@ -47,56 +49,113 @@ constexpr int vec_elems() {
   return rf::RegFFT<float, LOGL>::E * rf::RegFFT<float, LOGL>::ROW;
 }
 
-__device__ __forceinline__ float2 column_input(const float2* __restrict__ S, int Np, int N, int j, int gc) {
-  if (j >= N || gc > Np) return make_float2(0.f, 0.f);
-  if (gc == 0) return make_float2(S[(size_t)j * Np].x, 0.f);
-  if (gc == Np) return make_float2(S[(size_t)j * Np].y, 0.f);
-  return S[(size_t)j * Np + gc];
+// Asynchronous copies global -> shared; a false predicate zero-fills.
+__device__ __forceinline__ void cp16(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 16 : 0) : "memory");
+}
+__device__ __forceinline__ void cp8(void* dst, const void* src, bool pred) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(d), "l"(src), "r"(pred ? 8 : 0) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+// Copy `rows` rows of 16 columns (starting at column 16 grp of row row0 +
+// stride r) of a CW-column array into a tile, 16 bytes per copy.
+__device__ __forceinline__ void load_tile(float2* tile, const float2* Z, int CW, int row0, int stride, int rows,
+                                          int grp, int nthreads) {
+  for (int e = threadIdx.x; e < rows * (kGroup / 2); e += nthreads) {
+    const int r = e / (kGroup / 2), p = e % (kGroup / 2);
+    cp16(tile + r * kTP + 2 * p, Z + (size_t)(row0 + stride * r) * CW + kGroup * grp + 2 * p, true);
+  }
 }
 
-// shared memory of passes A and C: tiles (input / two halves), 32 transform
-// buffers and the 64-point twiddles
-constexpr size_t kSmemAC = (size_t)(3 * kR2 * kTP + 32 * vec_elems<6>() + 64) * sizeof(float2);
+// Pass A input: column gc of spectrum rows j1 + R1 r (zero from row N on).
+// The copies are raw; column 0 keeps only its real part and column N' (slot
+// 0 again) only its imaginary part, fixed when the tile is read.
+__device__ __forceinline__ void load_columns(float2* tile, const float2* S, int N, int Np, int j1, int R1,
+                                             int grp) {
+  const bool last = kGroup * grp == Np;
+  for (int e = threadIdx.x; e < kR2 * (kGroup / 2); e += kThreadsAC) {
+    const int r = e / (kGroup / 2), p = e % (kGroup / 2);
+    const int j = j1 + R1 * r;
+    const bool in = j < N;
+    const float2* row = S + (size_t)(in ? j : 0) * Np;
+    if (!last) {
+      cp16(tile + r * kTP + 2 * p, row + kGroup * grp + 2 * p, in);
+    } else {
+      cp8(tile + r * kTP + 2 * p, row, in && p == 0);
+      cp8(tile + r * kTP + 2 * p + 1, row, false);
+    }
+  }
+}
+
+__device__ __forceinline__ float2 column_value(float2 v, int gc, int Np) {
+  if (gc == 0) return make_float2(v.x, 0.f);
+  if (gc == Np) return make_float2(v.y, 0.f);
+  return gc > Np ? make_float2(0.f, 0.f) : v;
+}
+
+// shared memory: passes A and C hold two buffers of two tiles each, 32
+// transform buffers and the 64-point twiddles; pass B the same with R1-row tiles
+constexpr size_t kSmemAC = (size_t)(4 * kR2 * kTP + 32 * vec_elems<6>() + 64) * sizeof(float2);
 template <int LOGR1>
 constexpr size_t smem_b() {
-  return (size_t)(2 * (1 << LOGR1) * kTP + 32 * vec_elems<LOGR1>() + (1 << LOGR1)) * sizeof(float2);
+  return (size_t)(4 * (1 << LOGR1) * kTP + 32 * vec_elems<LOGR1>() + (1 << LOGR1)) * sizeof(float2);
 }
 
+// Each block walks the work items t = blockIdx.x, + gridDim.x, ...; the
+// copies of the next item are in flight while the current one is computed
+// and stored.  Barriers: (1) after the wait, the item's tiles are complete;
+// (2) after the compute, the results are in shared memory; (3) after the
+// stores, the buffer may be refilled.
 __global__ void __launch_bounds__(kThreadsAC) k_conv3_a(const float2* __restrict__ S, const float2* __restrict__ tw,
                                                         Conv3 c, int N, int Np) {
   using F = rf::RegFFT<float, 6>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* s_in = reinterpret_cast<float2*>(smem_raw);
-  float2* s_out = s_in + kR2 * kTP;                 // [2][kR2 * kTP]
-  float2* s_fft = s_out + 2 * kR2 * kTP;
+  float2* s_buf = reinterpret_cast<float2*>(smem_raw);   // [2 buffers][2 tiles][kR2 * kTP]
+  float2* s_fft = s_buf + 4 * kR2 * kTP;
   float2* s_tw1 = s_fft + 32 * vec_elems<6>();
-  const int grp = blockIdx.x, j1 = blockIdx.y, R1 = c.R1, tid = threadIdx.x;
+  const int groups = c.CW / kGroup, R1 = c.R1, total = groups * R1, tid = threadIdx.x;
   if (tid < 64) s_tw1[tid] = c.tw1a[tid];
-  for (int e = tid; e < kR2 * kGroup; e += kThreadsAC) {
-    const int r = e / kGroup, cc = e % kGroup;
-    s_in[r * kTP + cc] = column_input(S, Np, N, j1 + R1 * r, kGroup * grp + cc);
-  }
-  __syncthreads();
+  int it = blockIdx.x;
+  if (it < total) load_columns(s_buf, S, N, Np, it / groups, R1, it % groups);
+  cp_commit();
   const int v = tid / F::TT, t = tid % F::TT, cl = v >> 1, h = v & 1;
-  float2 x[F::E];
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    const int j2 = t + F::TT * q;
-    const float2 val = s_in[j2 * kTP + cl];
-    x[q] = h ? cmul(val, __ldg(&tw[j1 + R1 * j2])) : val;
-  });
-  F::template fwd<true>(x, s_fft + v * vec_elems<6>(), t, s_tw1);
-  static_for<0, F::E>([&](auto rc) {
-    constexpr int r = decltype(rc)::value;
-    const int m2 = F::template freq_index<r>(t);
-    s_out[h * kR2 * kTP + m2 * kTP + cl] = cmul(x[r], __ldg(&c.twM[j1 * m2]));
-  });
-  __syncthreads();
-  for (int e = tid; e < 2 * kR2 * kGroup; e += kThreadsAC) {
-    const int hh = e / (kR2 * kGroup), r = (e / kGroup) % kR2, cc = e % kGroup;
-    float2* Z = hh ? c.ZO : c.ZE;
-    Z[(size_t)(j1 + R1 * r) * c.CW + kGroup * grp + cc] = s_out[hh * kR2 * kTP + r * kTP + cc];
+  for (int b = 0; it < total; it += gridDim.x, b ^= 1) {
+    const int next = it + gridDim.x;
+    if (next < total) load_columns(s_buf + (b ^ 1) * 2 * kR2 * kTP, S, N, Np, next / groups, R1, next % groups);
+    cp_commit();
+    cp_wait<1>();
+    __syncthreads();
+    const int j1 = it / groups, grp = it % groups, gc = kGroup * grp + cl;
+    float2* in = s_buf + b * 2 * kR2 * kTP;   // tile 0: input; tiles 0 / 1 then hold the halves
+    float2 x[F::E];
+    static_for<0, F::E>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const int j2 = t + F::TT * q;
+      const float2 val = column_value(in[j2 * kTP + cl], gc, Np);
+      x[q] = h ? cmul(val, __ldg(&tw[j1 + R1 * j2])) : val;
+    });
+    __syncthreads();   // every vector has read the input tile
+    F::template fwd<true>(x, s_fft + v * vec_elems<6>(), t, s_tw1);
+    static_for<0, F::E>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      const int m2 = F::template freq_index<r>(t);
+      in[h * kR2 * kTP + m2 * kTP + cl] = cmul(x[r], __ldg(&c.twM[j1 * m2]));
+    });
+    __syncthreads();
+    for (int e = tid; e < 2 * kR2 * (kGroup / 2); e += kThreadsAC) {
+      const int hh = e / (kR2 * (kGroup / 2)), r = (e / (kGroup / 2)) % kR2, p = e % (kGroup / 2);
+      float2* Z = hh ? c.ZO : c.ZE;
+      const float4 val = *reinterpret_cast<const float4*>(in + hh * kR2 * kTP + r * kTP + 2 * p);
+      *reinterpret_cast<float4*>(Z + (size_t)(j1 + R1 * r) * c.CW + kGroup * grp + 2 * p) = val;
+    }
+    __syncthreads();
   }
+  cp_wait<0>();
 }
 
 template <int LOGR1>
@@ -105,85 +164,118 @@ __global__ void __launch_bounds__(32 * rf::RegFFT<float, LOGR1>::TT) k_conv3_b(C
   constexpr int R1 = 1 << LOGR1;
   constexpr int NT = 32 * F::TT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* s_t = reinterpret_cast<float2*>(smem_raw);   // [2][R1 * kTP]
-  float2* s_fft = s_t + 2 * R1 * kTP;
+  float2* s_buf = reinterpret_cast<float2*>(smem_raw);   // [2 buffers][2 halves][R1 * kTP]
+  float2* s_fft = s_buf + 4 * R1 * kTP;
   float2* s_tw1 = s_fft + 32 * vec_elems<LOGR1>();
-  const int grp = blockIdx.x, m2 = blockIdx.y, tid = threadIdx.x;
+  const int groups = c.CW / kGroup, total = groups * kR2, tid = threadIdx.x;
   for (int e = tid; e < R1; e += NT) s_tw1[e] = c.tw1b[e];
-  for (int e = tid; e < 2 * R1 * kGroup; e += NT) {
-    const int hh = e / (R1 * kGroup), r = (e / kGroup) % R1, cc = e % kGroup;
-    const float2* Z = hh ? c.ZO : c.ZE;
-    s_t[hh * R1 * kTP + r * kTP + cc] = Z[(size_t)(r + R1 * m2) * c.CW + kGroup * grp + cc];
-  }
-  __syncthreads();
+  auto load = [&](float2* buf, int item) {
+    const int m2 = item / groups, grp = item % groups;
+    load_tile(buf, c.ZE, c.CW, R1 * m2, 1, R1, grp, NT);
+    load_tile(buf + R1 * kTP, c.ZO, c.CW, R1 * m2, 1, R1, grp, NT);
+  };
+  int it = blockIdx.x;
+  if (it < total) load(s_buf, it);
+  cp_commit();
   const int v = tid / F::TT, t = tid % F::TT, cl = v >> 1, h = v & 1;
-  float2* tile = s_t + h * R1 * kTP;
-  float2 x[F::E];
-  // each element of the vector's column is read and later written by the same
-  // thread (natural layout before the forward and after the inverse transform)
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    x[q] = tile[(t + F::TT * q) * kTP + cl];
-  });
-  F::template fwd<true>(x, s_fft + v * vec_elems<LOGR1>(), t, s_tw1);
-  const float* lam = c.Lt + ((size_t)(m2 * c.CW + kGroup * grp + cl) * 2 + h) * R1;
-  static_for<0, F::E>([&](auto rc) {
-    constexpr int r = decltype(rc)::value;
-    x[r] = cscale(x[r], __ldg(lam + F::template freq_index<r>(t)));
-  });
-  F::template inv<true>(x, s_fft + v * vec_elems<LOGR1>(), t, s_tw1);
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    const int j1 = t + F::TT * q;
-    tile[j1 * kTP + cl] = cmulc(x[q], __ldg(&c.twM[j1 * m2]));
-  });
-  __syncthreads();
-  for (int e = tid; e < 2 * R1 * kGroup; e += NT) {
-    const int hh = e / (R1 * kGroup), r = (e / kGroup) % R1, cc = e % kGroup;
-    float2* Z = hh ? c.ZO : c.ZE;
-    Z[(size_t)(r + R1 * m2) * c.CW + kGroup * grp + cc] = s_t[hh * R1 * kTP + r * kTP + cc];
+  for (int b = 0; it < total; it += gridDim.x, b ^= 1) {
+    const int next = it + gridDim.x;
+    if (next < total) load(s_buf + (b ^ 1) * 2 * R1 * kTP, next);
+    cp_commit();
+    const int m2 = it / groups, grp = it % groups;
+    // the symbol values of this thread (frequency layout), loaded under the wait
+    const float* lam = c.Lt + ((size_t)(m2 * c.CW + kGroup * grp + cl) * 2 + h) * R1;
+    float lv[F::E];
+    static_for<0, F::E>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      lv[r] = __ldg(lam + F::template freq_index<r>(t));
+    });
+    cp_wait<1>();
+    __syncthreads();
+    // each element of the vector's column is read and later written by the
+    // same thread (natural layout before the forward, after the inverse)
+    float2* tile = s_buf + b * 2 * R1 * kTP + h * R1 * kTP;
+    float2 x[F::E];
+    static_for<0, F::E>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      x[q] = tile[(t + F::TT * q) * kTP + cl];
+    });
+    F::template fwd<true>(x, s_fft + v * vec_elems<LOGR1>(), t, s_tw1);
+    static_for<0, F::E>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      x[r] = cscale(x[r], lv[r]);
+    });
+    F::template inv<true>(x, s_fft + v * vec_elems<LOGR1>(), t, s_tw1);
+    static_for<0, F::E>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      const int j1 = t + F::TT * q;
+      tile[j1 * kTP + cl] = cmulc(x[q], __ldg(&c.twM[j1 * m2]));
+    });
+    __syncthreads();
+    const float2* buf = s_buf + b * 2 * R1 * kTP;
+    for (int e = tid; e < 2 * R1 * (kGroup / 2); e += NT) {
+      const int hh = e / (R1 * (kGroup / 2)), r = (e / (kGroup / 2)) % R1, p = e % (kGroup / 2);
+      float2* Z = hh ? c.ZO : c.ZE;
+      const float4 val = *reinterpret_cast<const float4*>(buf + hh * R1 * kTP + r * kTP + 2 * p);
+      *reinterpret_cast<float4*>(Z + (size_t)(r + R1 * m2) * c.CW + kGroup * grp + 2 * p) = val;
+    }
+    __syncthreads();
   }
+  cp_wait<0>();
 }
 
 __global__ void __launch_bounds__(kThreadsAC) k_conv3_c(float2* __restrict__ S, const float2* __restrict__ tw,
                                                         Conv3 c, int N, int Np) {
   using F = rf::RegFFT<float, 6>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float2* s_t = reinterpret_cast<float2*>(smem_raw);   // [2][kR2 * kTP]
-  float2* s_fft = s_t + 3 * kR2 * kTP;
+  float2* s_buf = reinterpret_cast<float2*>(smem_raw);   // [2 buffers][2 halves][kR2 * kTP]
+  float2* s_fft = s_buf + 4 * kR2 * kTP;
   float2* s_tw1 = s_fft + 32 * vec_elems<6>();
-  const int grp = blockIdx.x, j1 = blockIdx.y, R1 = c.R1, tid = threadIdx.x;
+  const int groups = c.CW / kGroup, R1 = c.R1, total = groups * R1, tid = threadIdx.x;
   if (tid < 64) s_tw1[tid] = c.tw1a[tid];
-  for (int e = tid; e < 2 * kR2 * kGroup; e += kThreadsAC) {
-    const int hh = e / (kR2 * kGroup), r = (e / kGroup) % kR2, cc = e % kGroup;
-    const float2* Z = hh ? c.ZO : c.ZE;
-    s_t[hh * kR2 * kTP + r * kTP + cc] = Z[(size_t)(j1 + R1 * r) * c.CW + kGroup * grp + cc];
-  }
-  __syncthreads();
+  auto load = [&](float2* buf, int item) {
+    const int j1 = item / groups, grp = item % groups;
+    load_tile(buf, c.ZE, c.CW, j1, R1, kR2, grp, kThreadsAC);
+    load_tile(buf + kR2 * kTP, c.ZO, c.CW, j1, R1, kR2, grp, kThreadsAC);
+  };
+  int it = blockIdx.x;
+  if (it < total) load(s_buf, it);
+  cp_commit();
   const int v = tid / F::TT, t = tid % F::TT, cl = v >> 1, h = v & 1;
-  float2* tile = s_t + h * kR2 * kTP;
-  float2 x[F::E];
-  static_for<0, F::E>([&](auto rc) {
-    constexpr int r = decltype(rc)::value;
-    x[r] = tile[F::template freq_index<r>(t) * kTP + cl];
-  });
-  // the transform's internal warp barriers order every read of the vector's
-  // column before the writes below
-  F::template inv<true>(x, s_fft + v * vec_elems<6>(), t, s_tw1);
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    tile[(t + F::TT * q) * kTP + cl] = x[q];
-  });
-  __syncthreads();
-  for (int e = tid; e < kR2 * kGroup; e += kThreadsAC) {
-    const int r = e / kGroup, cc = e % kGroup;
-    const int j = j1 + R1 * r, gc = kGroup * grp + cc;
-    if (j >= N || gc > Np) continue;
-    const float2 y = cadd(s_t[r * kTP + cc], cmulc(s_t[kR2 * kTP + r * kTP + cc], __ldg(&tw[j])));
-    if (gc == 0) reinterpret_cast<float*>(S + (size_t)j * Np)[0] = y.x;
-    else if (gc == Np) reinterpret_cast<float*>(S + (size_t)j * Np)[1] = y.x;
-    else S[(size_t)j * Np + gc] = y;
+  for (int b = 0; it < total; it += gridDim.x, b ^= 1) {
+    const int next = it + gridDim.x;
+    if (next < total) load(s_buf + (b ^ 1) * 2 * kR2 * kTP, next);
+    cp_commit();
+    cp_wait<1>();
+    __syncthreads();
+    const int j1 = it / groups, grp = it % groups;
+    float2* buf = s_buf + b * 2 * kR2 * kTP;
+    float2* tile = buf + h * kR2 * kTP;
+    float2 x[F::E];
+    static_for<0, F::E>([&](auto rc) {
+      constexpr int r = decltype(rc)::value;
+      x[r] = tile[F::template freq_index<r>(t) * kTP + cl];
+    });
+    // the transform's internal warp barriers order every read of the
+    // vector's column before the writes below
+    F::template inv<true>(x, s_fft + v * vec_elems<6>(), t, s_tw1);
+    static_for<0, F::E>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      tile[(t + F::TT * q) * kTP + cl] = x[q];
+    });
+    __syncthreads();
+    for (int e = tid; e < kR2 * kGroup; e += kThreadsAC) {
+      const int r = e / kGroup, cc = e % kGroup;
+      const int j = j1 + R1 * r, gc = kGroup * grp + cc;
+      if (j >= N || gc > Np) continue;
+      const float2 y = cadd(buf[r * kTP + cc], cmulc(buf[kR2 * kTP + r * kTP + cc], __ldg(&tw[j])));
+      if (gc == 0) reinterpret_cast<float*>(S + (size_t)j * Np)[0] = y.x;
+      else if (gc == Np) reinterpret_cast<float*>(S + (size_t)j * Np)[1] = y.x;
+      else S[(size_t)j * Np + gc] = y;
+    }
+    __syncthreads();
   }
+  cp_wait<0>();
 }
 
 // Tables: the symbol re-laid as Lt[((m2 * CW + col) * 2 + h) * R1 + m1] =
@@ -227,23 +319,42 @@ __global__ void k_conv3_twiddles(Conv3 c, int Np) {
   }
 }
 
+// Persistent grid: as many blocks as are resident at once (at most one per
+// work item).
+template <typename K>
+cudaError_t resident_grid(K kernel, int threads, size_t smem, int items, int* grid) {
+  int dev = 0, sms = 0, per = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, kernel, threads, smem);
+  if (e != cudaSuccess) return e;
+  const int g = sms * (per > 0 ? per : 1);
+  *grid = g < items ? g : items;
+  return cudaSuccess;
+}
+
 template <int LOGR1>
 cudaError_t launch_b(const Conv3& c, int groups, cudaStream_t st) {
-  static bool attr = false;
-  if (!attr) {
-    const cudaError_t e =
+  constexpr int NT = 32 * rf::RegFFT<float, LOGR1>::TT;
+  static int grid = 0;
+  if (!grid) {
+    cudaError_t e =
         cudaFuncSetAttribute(k_conv3_b<LOGR1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b<LOGR1>());
-    if (e != cudaSuccess) return e;
-    attr = true;
+    if (e == cudaSuccess) e = resident_grid(k_conv3_b<LOGR1>, NT, smem_b<LOGR1>(), 1 << 30, &grid);
+    if (e != cudaSuccess) {
+      grid = 0;
+      return e;
+    }
   }
-  k_conv3_b<LOGR1><<<dim3(groups, kR2), 32 * rf::RegFFT<float, LOGR1>::TT, smem_b<LOGR1>(), st>>>(c);
+  const int items = groups * kR2;
+  k_conv3_b<LOGR1><<<grid < items ? grid : items, NT, smem_b<LOGR1>(), st>>>(c);
   return cudaGetLastError();
 }
 
 }  // namespace
 
 // Used where it measured faster than the single-pass kernel: N' = 8192
-// (2.71 against 3.45 ms per step at N = 8191; at N' = 4096 it took 0.61
+// (1.83 against 3.45 ms per step at N = 8191; at N' = 4096 it took 0.44
 // against 0.41 ms).  The kernels themselves serve N' = 2048 .. 8192.
 bool conv3_supported(int logNp) { return logNp == 13; }
 
@@ -291,8 +402,17 @@ void conv3_free(Conv3* c) {
 cudaError_t launch_conv3(const Conv3& c, int N, int Np, void* Sv, const void* twv, cudaStream_t st) {
   float2* S = static_cast<float2*>(Sv);
   const float2* tw = static_cast<const float2*>(twv);
-  const int groups = c.CW / kGroup;
-  k_conv3_a<<<dim3(groups, c.R1), kThreadsAC, kSmemAC, st>>>(S, tw, c, N, Np);
+  const int groups = c.CW / kGroup, items = groups * c.R1;
+  static int grid_ac = 0;
+  if (!grid_ac) {
+    const cudaError_t e = resident_grid(k_conv3_a, kThreadsAC, kSmemAC, 1 << 30, &grid_ac);
+    if (e != cudaSuccess) {
+      grid_ac = 0;
+      return e;
+    }
+  }
+  const int gac = grid_ac < items ? grid_ac : items;
+  k_conv3_a<<<gac, kThreadsAC, kSmemAC, st>>>(S, tw, c, N, Np);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   if (c.logR1 == 5) e = launch_b<5>(c, groups, st);
@@ -300,7 +420,7 @@ cudaError_t launch_conv3(const Conv3& c, int N, int Np, void* Sv, const void* tw
   else if (c.logR1 == 7) e = launch_b<7>(c, groups, st);
   else e = cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
-  k_conv3_c<<<dim3(groups, c.R1), kThreadsAC, kSmemAC, st>>>(S, tw, c, N, Np);
+  k_conv3_c<<<gac, kThreadsAC, kSmemAC, st>>>(S, tw, c, N, Np);
   return cudaGetLastError();
 }
 
