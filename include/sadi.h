@@ -124,8 +124,9 @@ sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
  * sadi_step would, but batched: FP32 and FP32_DENSE contexts with FFT length
  * N' <= 1024 are grouped by precision and N' (at most 32 per group) and each
  * group runs one launch per kernel for all its members (independent problems
- * of possibly different N, alpha, kappa, tau and g; the dense sweeps in GEMM
- * launches of up to 16 problems); the other contexts step one after another.
+ * of possibly different N, alpha, kappa, tau and g; both dense sweeps of up
+ * to 8 members in one GEMM launch); the other contexts step one after
+ * another.
  * All contexts must be initialised and distinct (SADI_EINVAL / SADI_ESTATE
  * otherwise).  The work
  * is issued on the first context's stream, ordered after the work already
@@ -227,7 +228,9 @@ sadi_status sadi_get_info(const sadi_ctx *ctx, int *fft_len, int *border_rank);
  * return SADI_EINVAL and leave the setting unchanged.  The tiles change the
  * order of some rounding steps (the column convolution multiplies the symbol
  * fused into its transforms or in a separate pass), so results of different
- * tiles agree to rounding, not bitwise.  Call after sadi_set_options. */
+ * tiles agree to rounding, not bitwise.  The FP32 forms at N' = 8192 run their
+ * column convolution as three passes of fixed shape and ignore conv_cols.
+ * Call after sadi_set_options. */
 sadi_status sadi_set_tiles(sadi_ctx *ctx, int rows, int conv_cols, int solve_cols);
 
 /* Current tiles of the selected precision: tiles[0..2] = rows, conv_cols,
