@@ -354,6 +354,17 @@ def algorithmic(N, Np, es, dense=False):
     return [r2c, conv, rows, gemms]
 
 
+def launches_per_step(Np, dense):
+    """Kernel launches of one batched step (all instances in each): row FFT,
+    column convolution (three passes at N' = 8192), row kernel, and either
+    one launch of both sweep GEMMs (dense form) or the y sweep (on the
+    shared-memory engine: transpose, row solve, transpose with leapfrog)."""
+    conv = 3 if Np == 8192 else 1
+    if dense:
+        return 2 + conv + 1
+    return 2 + conv + (3 if Np > 1024 else 1)
+
+
 def roofline_of(phase_ms, N, Np, dense, ninst, workload):
     """Roofline entry of the dominant kernel from the per-phase times (ms per
     step, one launch per phase covering ninst instances of size N)."""
@@ -363,7 +374,8 @@ def roofline_of(phase_ms, N, Np, dense, ninst, workload):
     if dense:
         names = [pre + "rows_r2c", conv, pre + "rows_solve<dense>", "k_tc_gemm(x+y)"]
     else:
-        names = [pre + "rows_r2c", conv, pre + "rows_solve", pre + "cols_solve"]
+        ysweep = "kr_cols_solve" if reg else "k_transpose+k_rows_gs+k_transpose_leapfrog"
+        names = [pre + "rows_r2c", conv, pre + "rows_solve", ysweep]
     alg = algorithmic(N, Np, 4, dense)
     peaks = {}
     try:
@@ -824,10 +836,7 @@ def main():
             "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
                     "how": "C ABI with pinned host buffers: sadi_set_initial once, then per step "
                            "sadi_batch_step(1) + sadi_get of u^{n+1} for each instance; wall clock"},
-            # launches per step, all instances in each: four (dense: three FFT
-            # kernels and one launch of both sweep GEMMs); six at N' = 8192,
-            # whose FP32 column convolution runs as three passes
-            "gpu_launches": (6 if Np == 8192 else 4) * a.steps,
+            "gpu_launches": launches_per_step(Np, chosen == "fp32_dense") * a.steps,
             "clocks": clocks,
         }
         print(json.dumps(line), flush=True)

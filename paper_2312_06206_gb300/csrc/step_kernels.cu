@@ -471,6 +471,79 @@ k_cols_solve(const T* __restrict__ W, const T* u_cur, T* u_prev, T* u_next, T* u
   }
 }
 
+// ---------------------------------------------------------------------------
+// The y sweep of the FP32 forms on the shared-memory engine, as the x sweep of
+// the transpose (both sweeps apply the same H^-1, Sec. 3): W -> W^T by 32 x 32
+// tiles, k_rows_gs on rows of W^T (whole rows, coalesced, where k_cols_solve
+// gathers 4-byte column elements), and the transpose back fused with the
+// leapfrog.  W^T and uhat^T live in the spectrum scratch, free at this point.
+// ---------------------------------------------------------------------------
+constexpr int kTT = 32;   // transpose tile
+
+__global__ void __launch_bounds__(kTT * 8) k_transpose_f32(const float* __restrict__ A, float* __restrict__ AT, int N) {
+  __shared__ float tile[kTT][kTT + 1];
+  const int x0 = blockIdx.x * kTT, y0 = blockIdx.y * kTT;
+  for (int r = threadIdx.y; r < kTT; r += 8) {
+    const int y = y0 + r, x = x0 + threadIdx.x;
+    tile[r][threadIdx.x] = (y < N && x < N) ? A[(size_t)y * N + x] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < kTT; r += 8) {
+    const int y = x0 + r, x = y0 + threadIdx.x;   // AT[y][x] = A[x][y]
+    if (y < N && x < N) AT[(size_t)y * N + x] = tile[threadIdx.x][r];
+  }
+}
+
+// rows i of W^T (columns of W): uhat_i^T = H^-1 W^T_i, as in k_cols_solve
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rows_gs(const T* __restrict__ WT, T* __restrict__ UT, Geom g, const cx<T>* __restrict__ stw,
+          const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c,
+          const T* __restrict__ G, int NR) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
+  const int N = g.N, Np = g.Np;
+  const int vs = vstride<T>(Np);
+  const int row0 = blockIdx.x * NR;
+  const int nrows = min(NR, N - row0);
+  for (int t = threadIdx.x; t < NR * Np; t += blockDim.x) {
+    const int v = t / Np, k = t % Np, k2 = Np - 1 - k;
+    T a = T(0), b = T(0);
+    if (v < nrows) {
+      const T* row = WT + (size_t)(row0 + v) * N;
+      if (k < N) a = row[k];
+      if (k2 < N) b = row[k2];
+    }
+    buf[v * vs + sidx<T>(k)] = cmul(mkc(a, b), __ldg(&tw[k]));
+  }
+  __syncthreads();
+  gs_core<T>(buf, NR, vs, g, stw, tw, lam_s, lam_c);
+  for (int t = threadIdx.x; t < nrows * N; t += blockDim.x) {
+    const int v = t / N, j = t % N;
+    UT[(size_t)(row0 + v) * N + j] = gs_out<T>(buf + v * vs, j, g, G);
+  }
+}
+
+// u^{n+1} from uhat^T by 32 x 32 tiles: the compensated leapfrog of
+// k_cols_solve, element (j, i) with uhat = UT[i][j]
+__global__ void __launch_bounds__(kTT * 8) k_transpose_leapfrog(const float* __restrict__ UT, float* u_cur,
+                                                                 float* d, float* u_lo, int N, int first) {
+  __shared__ float tile[kTT][kTT + 1];
+  const int i0 = blockIdx.x * kTT, j0 = blockIdx.y * kTT;
+  for (int r = threadIdx.y; r < kTT; r += 8) {
+    const int i = i0 + r, j = j0 + threadIdx.x;
+    tile[r][threadIdx.x] = (i < N && j < N) ? UT[(size_t)i * N + j] : 0.f;
+  }
+  __syncthreads();
+  for (int r = threadIdx.y; r < kTT; r += 8) {
+    const int j = j0 + r, i = i0 + threadIdx.x;
+    if (j < N && i < N) {
+      const size_t idx = (size_t)j * N + i;
+      leapfrog_comp<float>(u_cur[idx], tile[threadIdx.x][r], first, idx, d, u_cur, u_lo);
+    }
+  }
+}
+
 }  // namespace
 
 template <typename T>
@@ -482,6 +555,7 @@ cudaError_t step_setup_attributes() {
   if ((e = cudaFuncSetAttribute(k_rows_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_cols_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_rows_remainder<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_gs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if constexpr (sizeof(T) == 4) {
     if ((e = cudaFuncSetAttribute(k_rows_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   }
@@ -514,6 +588,13 @@ bool tiles_valid(const Geom& g, const Tiles& t) {
   if (t.rows * (g.Np / 2) > kMaxPairs * kThreads) return false;
   if (t.rows * vbytes > lim || 2 * t.conv_cols * vbytes > lim || t.solve_cols * vbytes > lim) return false;
   return true;
+}
+
+// The y sweep runs on the transpose for the FP32 compensated form (state in
+// place: u_next == u_cur), where the spectrum scratch holds W^T and uhat^T.
+template <typename T>
+bool transposed_y_sweep(const T* u_lo) {
+  return sizeof(T) == 4 && u_lo != nullptr;
 }
 
 // The column convolution: the three-pass form where the FP32 tables carry it,
@@ -552,8 +633,21 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch,
                                                           Cl);
   if (ev) cudaEventRecord(ev[3], st);
-  k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, u_lo, g, rp.first,
-                                                                          stw, tw, ls, lc, tb.G, CTs);
+  if (transposed_y_sweep<T>(u_lo)) {
+    // FP32 compensated form: the y sweep on rows of W^T (S is free scratch)
+    float* WT = reinterpret_cast<float*>(S);
+    float* UT = WT + (size_t)g.N * g.N;
+    const dim3 tg((g.N + kTT - 1) / kTT, (g.N + kTT - 1) / kTT), tb8(kTT, 8);
+    k_transpose_f32<<<tg, tb8, 0, st>>>(reinterpret_cast<const float*>(W), WT, g.N);
+    k_rows_gs<T><<<rblocks, kThreads, NR * vbytes, st>>>(reinterpret_cast<const T*>(WT), reinterpret_cast<T*>(UT), g,
+                                                        stw, tw, ls, lc, tb.G, NR);
+    k_transpose_leapfrog<<<tg, tb8, 0, st>>>(UT, reinterpret_cast<float*>(const_cast<T*>(u_cur)),
+                                             reinterpret_cast<float*>(u_prev), reinterpret_cast<float*>(u_lo), g.N,
+                                             rp.first);
+  } else {
+    k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, u_lo, g,
+                                                                            rp.first, stw, tw, ls, lc, tb.G, CTs);
+  }
   if (ev) cudaEventRecord(ev[4], st);
   return cudaGetLastError();
 }

@@ -49,8 +49,8 @@ def test_graph_replay_matches_batch_stepping_bitwise(S):
     assert all(s.get()[1] == 1 for s in run)  # capture runs nothing
     # two steps: register groups (N' = 64 FP32: 4 kernels; N' = 256 dense: 3
     # kernels + one launch of both sweep GEMMs), two shared-memory contexts
-    # (4, and 3 + 1)
-    assert g.sadi_graph_kernels() == 2 * (4 + 4 + 4 + 4)
+    # (FP32: 3 + the y sweep on the transpose, 3; dense: 3 + 1)
+    assert g.sadi_graph_kernels() == 2 * (4 + 4 + 6 + 4)
     g.launch(3)
     for s, w in zip(run, want):
         u, n = s.get()
