@@ -196,6 +196,24 @@ const char *sadi_tuning_log(const sadi_ctx *ctx);
  * the dense-inverse form ran out since the context was created. */
 sadi_status sadi_get(sadi_ctx *ctx, double *u_out, long long *n_out);
 
+/* Asynchronous read of the state u^n = phi^n (the scheme's solution after n
+ * steps, Sec. 3): queue the copy of u^n (N*N doubles, row-major, x fastest)
+ * into host memory u_out and return at once.  u_out should be page-locked
+ * (pinned) host memory; it is written when sadi_wait returns and must not be
+ * read or freed before.  The state is first joined into the context's
+ * staging buffer on its stream, then copied to the host on a stream of the
+ * context's own, so steps queued after this call run while the copy is in
+ * flight; a later sadi_get_async, sadi_get, sadi_set_initial or
+ * sadi_set_source waits for the copy before reusing the buffer.  Not to be
+ * called while the context's stream is being captured into a CUDA graph.
+ * SADI_EINVAL for u_out NULL, SADI_ESTATE before sadi_set_initial. */
+sadi_status sadi_get_async(sadi_ctx *ctx, double *u_out);
+
+/* Wait for all work queued on the context's stream and for its
+ * sadi_get_async copies.  Returns SADI_ETIMEOUT (the context then becomes
+ * unusable) under the same condition as sadi_get. */
+sadi_status sadi_wait(sadi_ctx *ctx);
+
 /* Copy u^n device-to-device into dst (N*N contiguous elements of dtype 0 =
  * double or 1 = float, device memory owned by the caller), on the context's
  * stream (asynchronous). */

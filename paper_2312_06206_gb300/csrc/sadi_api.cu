@@ -65,6 +65,9 @@ void free_all(sadi_ctx* c) {
   c->ev_pool.clear();
   c->ev_free.clear();
   if (c->order_ev) cudaEventDestroy(c->order_ev);
+  if (c->ev_staged) cudaEventDestroy(c->ev_staged);
+  if (c->ev_copied) cudaEventDestroy(c->ev_copied);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   if (c->own_stream) cudaStreamDestroy(c->own_stream);
 }
 
@@ -319,6 +322,7 @@ sadi_status sadi_set_source(sadi_ctx* c, const double* F, double omega, double p
   const size_t nn = (size_t)c->g.N * c->g.N;
   CK(cudaMalloc(&c->F, nn * esize(c->prec)), "cudaMalloc(source)");
   cudaStream_t st = c->stream;
+  CK(stage_acquire(c), "order after the last asynchronous read");
   CK(cudaMemcpyAsync(c->stage, F, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy source");
   if (c->prec == SADI_PREC_FP64)
     CK(cudaMemcpyAsync(c->F, c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "source");
@@ -345,6 +349,7 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   const size_t nn = (size_t)c->g.N * c->g.N;
   cudaStream_t st = c->stream;
   c->cur = 0;
+  CK(stage_acquire(c), "order after the last asynchronous read");
   CK(cudaMemcpyAsync(c->stage, phi1, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy phi1");
   if (c->prec == SADI_PREC_FP64) {
     CK(cudaMemcpyAsync(c->ubuf[0], c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "phi1");
@@ -563,6 +568,23 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
   return SADI_OK;
 }
 
+// The tensor-core sweeps' device error flag (a bounded wait ran out): the
+// context's state is then invalid.
+sadi_status check_gemm_flag(sadi_ctx* c) {
+  if (!c->tcerr) return SADI_OK;
+  int flag = 0;
+  CK(cudaMemcpy(&flag, c->tcerr, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
+  if (flag) {
+    c->broken = true;
+    return fail(c, SADI_ETIMEOUT, "a bounded wait in a tensor-core sweep ran out; the state is invalid");
+  }
+  return SADI_OK;
+}
+
+cudaError_t stage_acquire(sadi_ctx* c) {
+  return c->ev_copied ? cudaStreamWaitEvent(c->stream, c->ev_copied, 0) : cudaSuccess;
+}
+
 sadi_status check_steppable(sadi_ctx* c) {
   if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
   if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_step before sadi_set_initial");
@@ -701,20 +723,50 @@ sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {
   if (c->prec == SADI_PREC_FP64) {
     CK(cudaMemcpyAsync(u_out, c->ubuf[c->cur], nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   } else {
+    CK(stage_acquire(c), "order after the last asynchronous read");
     CK(launch_join_ff2d(static_cast<const float*>(c->ubuf[0]), c->ulo, c->stage, nn, st), "u join");
     CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   }
   CK(cudaStreamSynchronize(st), "sadi_get");
-  if (c->tcerr) {
-    int flag = 0;
-    CK(cudaMemcpy(&flag, c->tcerr, sizeof(int), cudaMemcpyDeviceToHost), "error flag");
-    if (flag) {
-      c->broken = true;
-      return fail(c, SADI_ETIMEOUT, "a bounded wait in a tensor-core sweep ran out; the state is invalid");
-    }
-  }
+  const sadi_status es = check_gemm_flag(c);
+  if (es != SADI_OK) return es;
   if (n_out) *n_out = c->n;
   return SADI_OK;
+}
+
+sadi_status sadi_get_async(sadi_ctx* c, double* u_out) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_get_async before sadi_set_initial");
+  if (!u_out) return fail(c, SADI_EINVAL, "u_out is NULL");
+  if (!c->copy_stream) {
+    CK(cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking), "cudaStreamCreate(copies)");
+    CK(cudaEventCreateWithFlags(&c->ev_staged, cudaEventDisableTiming), "cudaEventCreate");
+    CK(cudaEventCreateWithFlags(&c->ev_copied, cudaEventDisableTiming), "cudaEventCreate");
+  }
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  cudaStream_t st = c->stream;
+  // u^n into the staging buffer on the step stream (after the previous copy
+  // out of it), then the copy to the host on the copy stream, so that later
+  // steps on the step stream run while it is in flight
+  CK(stage_acquire(c), "order after the last asynchronous read");
+  if (c->prec == SADI_PREC_FP64)
+    CK(cudaMemcpyAsync(c->stage, c->ubuf[c->cur], nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "stage u");
+  else
+    CK(launch_join_ff2d(static_cast<const float*>(c->ubuf[0]), c->ulo, c->stage, nn, st), "u join");
+  CK(cudaEventRecord(c->ev_staged, st), "cudaEventRecord");
+  CK(cudaStreamWaitEvent(c->copy_stream, c->ev_staged, 0), "cudaStreamWaitEvent");
+  CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, c->copy_stream), "copy u");
+  CK(cudaEventRecord(c->ev_copied, c->copy_stream), "cudaEventRecord");
+  return SADI_OK;
+}
+
+sadi_status sadi_wait(sadi_ctx* c) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  CK(cudaStreamSynchronize(c->stream), "sadi_wait");
+  if (c->copy_stream) CK(cudaStreamSynchronize(c->copy_stream), "sadi_wait (copies)");
+  return check_gemm_flag(c);
 }
 
 sadi_status sadi_get_device(sadi_ctx* c, void* dst, int dtype) {

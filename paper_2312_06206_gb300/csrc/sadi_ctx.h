@@ -73,6 +73,11 @@ struct sadi_ctx {
   double phase_ms[4] = {0, 0, 0, 0};
   long long phase_steps = 0;
   cudaEvent_t order_ev = nullptr;   // cross-stream ordering in sadi_batch_step
+  // sadi_get_async: device -> host copies of the staging buffer on their own
+  // stream; ev_staged orders a copy after the staging, ev_copied orders later
+  // writers of the staging buffer after the last copy
+  cudaStream_t copy_stream = nullptr;
+  cudaEvent_t ev_staged = nullptr, ev_copied = nullptr;
   // optional source term f^n = cos(omega t_n + phase) F(x)
   void* F = nullptr;                // T, N x N
   double f_omega = 0.0, f_phase = 0.0;
@@ -94,6 +99,12 @@ sadi_status fail(sadi_ctx* c, sadi_status st, const std::string& msg);
 // message from a CUDA error; the context becomes unusable; returns SADI_ECUDA
 sadi_status cuda_fail(sadi_ctx* c, cudaError_t e, const char* what);
 sadi_status check_steppable(sadi_ctx* c);
+// order the context's stream after the last sadi_get_async copy (which reads
+// the staging buffer) before the buffer is written again
+cudaError_t stage_acquire(sadi_ctx* c);
+// SADI_ETIMEOUT (and the context marked unusable) if a tensor-core sweep's
+// bounded wait ran out
+sadi_status check_gemm_flag(sadi_ctx* c);
 bool is_dense(const sadi_ctx* c);
 // issue nsteps steps of count validated, distinct contexts (what
 // sadi_batch_step does after its argument checks)

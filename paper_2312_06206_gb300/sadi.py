@@ -33,6 +33,8 @@ _SIGS = {
     "sadi_step": (C.c_int, [C.c_void_p, C.c_int]),
     "sadi_batch_step": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int]),
     "sadi_get": (C.c_int, [C.c_void_p, C.c_void_p, C.POINTER(C.c_longlong)]),
+    "sadi_get_async": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sadi_wait": (C.c_int, [C.c_void_p]),
     "sadi_get_device": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sadi_get_setup": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_size_t]),
     "sadi_get_info": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
@@ -210,6 +212,14 @@ class Sadi:
         n = C.c_longlong()
         _check(lib().sadi_get(self.ctx, u.ctypes.data, C.byref(n)), self.ctx)
         return u, int(n.value)
+
+    def sadi_get_async(self, host_ptr: int):
+        """Queue the copy of u^n into host memory at host_ptr (N*N doubles,
+        pinned); valid after sadi_wait()."""
+        _check(lib().sadi_get_async(self.ctx, C.c_void_p(host_ptr)), self.ctx)
+
+    def sadi_wait(self):
+        _check(lib().sadi_wait(self.ctx), self.ctx)
 
     def sadi_get_device(self, dst_ptr: int, dtype: int):
         _check(lib().sadi_get_device(self.ctx, C.c_void_p(dst_ptr), int(dtype)), self.ctx)

@@ -1,5 +1,7 @@
 """Checkpoint and resume through the C ABI (sadi_save_state /
-sadi_load_state): a resumed context continues bitwise as the saved one."""
+sadi_load_state): a resumed context continues bitwise as the saved one; and
+asynchronous reads of the state (sadi_get_async / sadi_wait) equal the
+synchronous ones."""
 import numpy as np
 import pytest
 
@@ -66,3 +68,40 @@ def test_load_rejects_a_foreign_blob(S):
         b.sadi_load_state(b"x" * len(blob))
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("N,prec", [(200, 0), (200, 1), (200, 2), (1500, 1)])
+def test_async_reads_match_synchronous_reads(S, N, prec):
+    # sadi_get_async of consecutive steps into separate pinned buffers, waited
+    # for once, returns the same fields as sadi_get after each step; a read
+    # queued before sadi_set_initial (which rewrites the staging buffer) still
+    # returns the state it was queued for
+    import torch
+    phi1 = WL.gaussian_bumps(N, 5, 910 + N)
+    phi2 = 0.2 * WL.random_field(N, 911 + N)
+    ref = []
+    with _ctx(S, N, prec) as s:
+        s.set_initial(phi1, phi2)
+        for _ in range(4):
+            s.step(1)
+            ref.append(s.get()[0])
+    bufs = [torch.empty((N, N), dtype=torch.float64).pin_memory() for _ in range(5)]
+    with _ctx(S, N, prec) as s:
+        s.set_initial(phi1, phi2)
+        for k in range(4):
+            s.step(1)
+            s.sadi_get_async(bufs[k].data_ptr())
+        s.sadi_wait()
+        for k in range(4):
+            assert np.array_equal(bufs[k].numpy(), ref[k])
+        s.sadi_get_async(bufs[4].data_ptr())
+        s.set_initial(phi2, None)
+        s.sadi_wait()
+        assert np.array_equal(bufs[4].numpy(), ref[3])
+        with pytest.raises(S.SadiError) as ei:
+            s.sadi_get_async(0)
+        assert ei.value.status == S.SADI_EINVAL
+    with _ctx(S, N, prec) as s:
+        with pytest.raises(S.SadiError) as ei:
+            s.sadi_get_async(bufs[0].data_ptr())
+        assert ei.value.status == S.SADI_ESTATE
