@@ -61,8 +61,9 @@ struct ConvCfg {
   using F = rf::RegFFT<float, LOGL>;
   static constexpr int CT = BLOCK / F::TT;
   static_assert(CT >= 4 && CT % 2 == 0, "item 0 reads item 1's vectors: two items per block at least");
-  // the staging copies of a half-warp cover CT vectors x 16/CT rows: a
-  // vector stride of 16/CT (mod 16) float2 puts them in distinct bank pairs
+  // the staging copies of a half-warp cover CT/2 items (even vectors, 2 SMV
+  // apart) x 32/CT rows: a vector stride of 16/CT (mod 16) float2 puts them
+  // in distinct bank pairs
   static constexpr int SMV = vec_smem<LOGL>(CT >= 16 ? 1 : 16 / CT);
   // the half-angle twiddles tw[0 .. L) are staged too when the shared memory
   // still admits the block count of the launch bounds
@@ -270,11 +271,13 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
     const float* src = I.lreg + ((size_t)kx_of(item_of(cc)) * 2 + (cc & 1)) * Np + 4 * p;
     cp_async16(s_lam + cc * F::L + 4 * p, src, true);
   }
-  // the columns, rows 0 .. N-1 (zero-filled to L): thread -> (vector, row) with
-  // the vectors fastest, so that a warp's copies cover whole row segments
-  for (int e = threadIdx.x; e < C::CT * F::L; e += BLOCK) {
-    const int cc = e % C::CT, j = e / C::CT, it = item_of(cc);
-    float2* dst = reinterpret_cast<float2*>(smem_raw) + cc * C::SMV + pad32(j);
+  // each item's column, rows 0 .. N-1 (zero-filled to L), once, into the
+  // buffer of its even-half vector: thread -> (item, row) with the items
+  // fastest, so that a warp's copies cover whole row segments
+  constexpr int NI = C::CT / 2;
+  for (int e = threadIdx.x; e < NI * F::L; e += BLOCK) {
+    const int ci = e % NI, j = e / NI, it = item_of(2 * ci);
+    float2* dst = reinterpret_cast<float2*>(smem_raw) + 2 * ci * C::SMV + pad32(j);
     cp_async8(dst, I.S + (size_t)(j < N ? j : 0) * Np + slot_of(it), it <= Np && j < N);
   }
   cp_async_commit();
@@ -285,8 +288,11 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
   const float* lam = s_lam + c * F::L;
   float2 x[F::E];
-  load_nat<LOGL>(x, sm, t);
-  __syncwarp();
+  // both halves read the column from the even vector's buffer; the barrier
+  // keeps the even half's transform from overwriting it before the odd half
+  // has read it
+  load_nat<LOGL>(x, reinterpret_cast<const float2*>(smem_raw) + (c & ~1) * C::SMV, t);
+  __syncthreads();
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     float2 val = x[q];
