@@ -336,8 +336,8 @@ k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ 
 // ---------------------------------------------------------------------------
 // DENSE: the dense-inverse form stops after B^n, which it writes to W and,
 // split into BF16 pairs, to Bh / Bl (ld ldp).
-template <typename T, bool DENSE = false>
-__global__ void __launch_bounds__(kThreads)
+template <typename T, bool DENSE = false, int NT = kThreads>
+__global__ void __launch_bounds__(NT)
 k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ phi2, T* __restrict__ W,
              Geom g, RhsParams rp, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
              const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR,
@@ -353,9 +353,10 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
   // B^n and v1 = Q (v' + i J v'), staged through registers (in place).
   const int halfNp = Np >> 1;
   const int npairs = NR * halfNp;
-  T ra[kMaxPairs], rb[kMaxPairs];
+  constexpr int MP = kMaxPairs * kThreads / NT;   // same pair capacity at any block size
+  T ra[MP], rb[MP];
 #pragma unroll
-  for (int it = 0; it < kMaxPairs; ++it) {
+  for (int it = 0; it < MP; ++it) {
     const int t = threadIdx.x + it * blockDim.x;
     ra[it] = T(0);
     rb[it] = T(0);
@@ -387,7 +388,7 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
   }
   if constexpr (DENSE) {
 #pragma unroll
-    for (int it = 0; it < kMaxPairs; ++it) {
+    for (int it = 0; it < MP; ++it) {
       const int t = threadIdx.x + it * blockDim.x;
       if (t < npairs) {
         const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
@@ -408,7 +409,7 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
   }
   __syncthreads();
 #pragma unroll
-  for (int it = 0; it < kMaxPairs; ++it) {
+  for (int it = 0; it < MP; ++it) {
     const int t = threadIdx.x + it * blockDim.x;
     if (t < npairs) {
       const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
@@ -558,6 +559,9 @@ cudaError_t step_setup_attributes() {
   if ((e = cudaFuncSetAttribute(k_rows_gs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if constexpr (sizeof(T) == 4) {
     if ((e = cudaFuncSetAttribute(k_rows_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+    if ((e = cudaFuncSetAttribute(k_rows_solve<T, true, 2 * kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  mx)))
+      return e;
   }
   return cudaSuccess;
 }
@@ -588,6 +592,16 @@ bool tiles_valid(const Geom& g, const Tiles& t) {
   if (t.rows * (g.Np / 2) > kMaxPairs * kThreads) return false;
   if (t.rows * vbytes > lim || 2 * t.conv_cols * vbytes > lim || t.solve_cols * vbytes > lim) return false;
   return true;
+}
+
+// Block size of the dense form's Bn kernel: 512 threads from N' = 4096 on,
+// where its long-latency loads need more warps than the one to three
+// 256-thread blocks the shared-memory vectors leave room for (N' = 8192:
+// 1446 -> 1081 us; N' = 4096: 295 -> 270 us).  The kernels that also run
+// Algorithm 1 and the row FFT ran slower with 512 and keep 256.
+template <typename T>
+bool wide_rows(const Geom& g) {
+  return sizeof(T) == 4 && g.Np >= 4096;
 }
 
 // The y sweep runs on the transpose for the FP32 compensated form (state in
@@ -706,8 +720,12 @@ cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const 
   cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
   if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
-  k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR,
-                                                                 Ch, Cl, Bh, Bl, ldp);
+  if (wide_rows<T>(g))
+    k_rows_solve<T, true, 2 * kThreads><<<rblocks, 2 * kThreads, NR * vbytes, st>>>(
+        S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
+  else
+    k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR,
+                                                                   Ch, Cl, Bh, Bl, ldp);
   return cudaGetLastError();
 }
 
