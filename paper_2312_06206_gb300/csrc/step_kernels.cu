@@ -13,11 +13,14 @@
 // bordered Toeplitz matrix H' (size Np = power of two) followed by a rank-r
 // correction (r = Np - N) that recovers H^-1 exactly.
 //
-// Four kernels per step, all FFTs of the single length Np in shared memory:
+// Kernels per step, all FFTs of the single length Np in shared memory:
 //   k_rows_r2c   rows of u^n -> half spectrum along x (real FFT of length 2Np)
 //   k_cols_conv  per x frequency: FFT along y, x symbol, inverse FFT along y
+//                (FP32 at Np = 8192: the three passes of conv3.cu instead)
 //   k_rows_solve inverse real FFT along x + B^n epilogue + x sweep (Algorithm 1)
-//   k_cols_solve y sweep (Algorithm 1) + leapfrog epilogue
+//   k_cols_solve y sweep (Algorithm 1) + leapfrog epilogue (FP64); the FP32
+//                forms run it on the transpose: k_transpose_f32, k_rows_gs,
+//                k_transpose_leapfrog
 #include <cuda_runtime.h>
 
 #include "fft.cuh"
