@@ -241,14 +241,15 @@ sadi_status sadi_get_info(const sadi_ctx *ctx, int *fft_len, int *border_rank);
 /* Work decomposition of the four step kernels for the precision currently
  * selected: grid rows per block of the row kernels, spectrum slots per block
  * of the column convolution (a divisor of N'), grid columns per block of the
- * y sweep.  All zero restores the defaults.  Invalid combinations (shared
- * memory above 227 KB per block, or more rows than the row kernel stages)
+ * y sweep.  conv_cols = -1 selects the three-pass column convolution (a
+ * four-step FFT through HBM; FP32 forms, N' = 2048 .. 8192; the default at
+ * N' = 8192; its buffers, about 24 N'^2 bytes, are allocated on first use).
+ * All zero restores the defaults.  Invalid combinations (shared memory above
+ * 227 KB per block, more rows than the row kernel stages, -1 elsewhere)
  * return SADI_EINVAL and leave the setting unchanged.  The tiles change the
  * order of some rounding steps (the column convolution multiplies the symbol
  * fused into its transforms or in a separate pass), so results of different
- * tiles agree to rounding, not bitwise.  The FP32 forms at N' = 8192 run their
- * column convolution as three passes of fixed shape and ignore conv_cols.
- * Call after sadi_set_options. */
+ * tiles agree to rounding, not bitwise.  Call after sadi_set_options. */
 sadi_status sadi_set_tiles(sadi_ctx *ctx, int rows, int conv_cols, int solve_cols);
 
 /* Current tiles of the selected precision: tiles[0..2] = rows, conv_cols,

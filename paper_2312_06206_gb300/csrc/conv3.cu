@@ -353,10 +353,10 @@ cudaError_t launch_b(const Conv3& c, int groups, cudaStream_t st) {
 
 }  // namespace
 
-// Used where it measured faster than the single-pass kernel: N' = 8192
-// (1.83 against 3.45 ms per step at N = 8191; at N' = 4096 it took 0.44
-// against 0.41 ms).  The kernels themselves serve N' = 2048 .. 8192.
-bool conv3_supported(int logNp) { return logNp == 13; }
+// The kernels serve N' = 2048 .. 8192; the step's default uses them at 8192,
+// where they measured faster than the single-pass kernel (1.83 against 3.45
+// ms per step at N = 8191; at N' = 4096 0.44 against 0.41 ms).
+bool conv3_supported(int logNp) { return logNp >= 11 && logNp <= 13; }
 
 cudaError_t conv3_setup(int Np, int logNp, const float* lpb32, Conv3* c, cudaStream_t st) {
   if (!conv3_supported(logNp) || Np != (1 << logNp)) return cudaErrorInvalidValue;

@@ -241,12 +241,14 @@ sadi_status sadi_autotune(sadi_ctx** ctxs, int count, int g, int flags) {
       if ((st = time_group(grp, 5, &ms)) != SADI_OK) return st;
       if (!reg) {
         // coordinate descent over the shared-memory engine's decomposition
-        // (the dense form leaves the y-sweep tile unused)
+        // (the dense form leaves the y-sweep tile unused); the column
+        // convolution may also run as three passes (kConvThreePass)
         Tiles t = grp[0]->tiles32;
         const int nfields = prec == SADI_PREC_FP32 ? 3 : 2;
-        const int opts[3][4] = {{1, 2, 4, 8}, {1, 2, 4, 8}, {1, 2, 4, 8}};
+        const int opts[3][5] = {{1, 2, 4, 8, 0}, {kConvThreePass, 1, 2, 4, 8}, {1, 2, 4, 8, 0}};
         for (int f = 0; f < nfields; ++f) {
           for (int v : opts[f]) {
+            if (v == 0) continue;
             Tiles tt = t;
             (f == 0 ? tt.rows : f == 1 ? tt.conv_cols : tt.solve_cols) = v;
             if ((f == 0 ? t.rows : f == 1 ? t.conv_cols : t.solve_cols) == v) continue;

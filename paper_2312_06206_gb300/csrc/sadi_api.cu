@@ -122,11 +122,24 @@ sadi_status alloc_state(sadi_ctx* c) {
   const size_t ses = (c->prec != SADI_PREC_FP64 && c->g.Np <= 4096) ? sizeof(double) : es;
   CK(cudaMalloc(&c->S, (size_t)c->g.N * c->g.Np * 2 * ses), "cudaMalloc(spectrum)");
   CK(cudaMalloc(&c->W, nn * es), "cudaMalloc(sweep)");
-  // FP32 forms on the shared-memory engine (N' = 2048 .. 8192): buffers and
-  // tables of the three-pass column convolution (kept once allocated)
-  if (c->prec != SADI_PREC_FP64 && !c->reg_path && conv3_supported(c->g.logNp) && !c->c3.ZE)
-    CK(conv3_setup(c->g.Np, c->g.logNp, c->lpb32, &c->c3, c->stream), "three-pass convolution setup");
+  // FP32 forms whose tiles select the three-pass column convolution (the
+  // default at N' = 8192): its buffers and tables (kept once allocated)
+  if (c->prec != SADI_PREC_FP64 && c->tiles32.conv_cols == kConvThreePass) {
+    const sadi_status s3 = ensure_conv3(c);
+    if (s3 != SADI_OK) return s3;
+  }
   (void)e;
+  return SADI_OK;
+}
+
+// The three-pass column convolution's buffers and tables (once per context).
+sadi_status ensure_conv3(sadi_ctx* c) {
+  if (c->c3.ZE) return SADI_OK;
+  if (c->reg_path || !conv3_supported(c->g.logNp))
+    return fail(c, SADI_EINVAL, "the three-pass convolution serves FFT lengths 2048 .. 8192");
+  const cudaError_t e = conv3_setup(c->g.Np, c->g.logNp, c->lpb32, &c->c3, c->stream);
+  if (e == cudaErrorMemoryAllocation) return fail(c, SADI_ENOMEM, "cudaMalloc(three-pass convolution) failed");
+  if (e != cudaSuccess) return cuda_fail(c, e, "three-pass convolution setup");
   return SADI_OK;
 }
 
@@ -842,6 +855,10 @@ sadi_status sadi_set_tiles(sadi_ctx* c, int rows, int conv_cols, int solve_cols)
     t = f64 ? default_tiles<double>(c->g.Np) : default_tiles<float>(c->g.Np);
   const bool ok = f64 ? tiles_valid<double>(c->g, t) : tiles_valid<float>(c->g, t);
   if (!ok) return fail(c, SADI_EINVAL, "tile sizes invalid for this N and precision");
+  if (!f64 && t.conv_cols == kConvThreePass) {
+    const sadi_status s3 = ensure_conv3(c);
+    if (s3 != SADI_OK) return s3;
+  }
   if (f64) c->tiles64 = t;
   else c->tiles32 = t;
   return SADI_OK;

@@ -102,6 +102,8 @@ sadi_status check_steppable(sadi_ctx* c);
 // order the context's stream after the last sadi_get_async copy (which reads
 // the staging buffer) before the buffer is written again
 cudaError_t stage_acquire(sadi_ctx* c);
+// allocate and fill the three-pass convolution's buffers (FP32, N' 2048 .. 8192)
+sadi_status ensure_conv3(sadi_ctx* c);
 // SADI_ETIMEOUT (and the context marked unusable) if a tensor-core sweep's
 // bounded wait ran out
 sadi_status check_gemm_flag(sadi_ctx* c);

@@ -80,7 +80,7 @@ struct Conv3 {
   float2* tw1b = nullptr;
   int CW = 0, R1 = 0, logR1 = 0;
 };
-bool conv3_supported(int logNp);   // FFT lengths where the step uses it
+bool conv3_supported(int logNp);   // FFT lengths its kernels serve (2048 .. 8192)
 // allocate and fill the buffers and tables (once per context); lpb32 is the
 // shared-memory engine's symbol table
 cudaError_t conv3_setup(int Np, int logNp, const float* lpb32, Conv3* c, cudaStream_t st);
@@ -92,9 +92,11 @@ cudaError_t launch_conv3(const Conv3& c, int N, int Np, void* S, const void* tw,
 // Work decomposition of the four step kernels.
 struct Tiles {
   int rows;        // grid rows per block (row kernels)
-  int conv_cols;   // spectrum slots per block (column convolution)
+  int conv_cols;   // spectrum slots per block (column convolution), or kConvThreePass
   int solve_cols;  // grid columns per block (y sweep)
 };
+// conv_cols value selecting the three-pass column convolution (conv3.cu)
+constexpr int kConvThreePass = -1;
 
 template <typename T>
 Tiles default_tiles(int Np);

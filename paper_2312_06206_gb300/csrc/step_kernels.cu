@@ -583,6 +583,8 @@ Tiles default_tiles(int Np) {
   if (t.solve_cols < 1) t.solve_cols = 1;
   if (t.conv_cols > 8) t.conv_cols = 8;
   if (t.solve_cols > 16) t.solve_cols = 16;
+  // FP32 at N' = 8192: the three-pass column convolution (conv_cols = -1)
+  if (sizeof(T) == 4 && Np == 8192) t.conv_cols = kConvThreePass;
   return t;
 }
 
@@ -590,10 +592,14 @@ template <typename T>
 bool tiles_valid(const Geom& g, const Tiles& t) {
   const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
   const size_t lim = 227 * 1024;
-  if (t.rows < 1 || t.conv_cols < 1 || t.solve_cols < 1) return false;
-  if (g.Np % t.conv_cols != 0) return false;
+  if (t.rows < 1 || t.solve_cols < 1) return false;
+  if (t.conv_cols == kConvThreePass) {
+    if (sizeof(T) != 4 || !conv3_supported(g.logNp)) return false;
+  } else if (t.conv_cols < 1 || g.Np % t.conv_cols != 0 || 2 * t.conv_cols * vbytes > lim) {
+    return false;
+  }
   if (t.rows * (g.Np / 2) > kMaxPairs * kThreads) return false;
-  if (t.rows * vbytes > lim || 2 * t.conv_cols * vbytes > lim || t.solve_cols * vbytes > lim) return false;
+  if (t.rows * vbytes > lim || t.solve_cols * vbytes > lim) return false;
   return true;
 }
 
@@ -614,12 +620,16 @@ bool transposed_y_sweep(const T* u_lo) {
   return sizeof(T) == 4 && u_lo != nullptr;
 }
 
-// The column convolution: the three-pass form where the FP32 tables carry it,
-// else the single-pass shared-memory kernel (CTc slots per block).
+// The column convolution: the three-pass form for conv_cols = kConvThreePass
+// (its buffers in tb.c3), else the single-pass shared-memory kernel with CTc
+// slots per block.
 template <typename T>
 cudaError_t launch_cols_conv(const Geom& g, const StepTables<T>& tb, int CTc, cx<T>* S, cudaStream_t st) {
-  if constexpr (sizeof(T) == 4) {
-    if (tb.c3) return launch_conv3(*tb.c3, g.N, g.Np, S, tb.tw, st);
+  if (CTc == kConvThreePass) {
+    if constexpr (sizeof(T) == 4) {
+      if (tb.c3) return launch_conv3(*tb.c3, g.N, g.Np, S, tb.tw, st);
+    }
+    return cudaErrorInvalidValue;
   }
   const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
   k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, reinterpret_cast<const cx<T>*>(tb.stw),

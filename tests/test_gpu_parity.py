@@ -255,3 +255,41 @@ def test_large_n_fp32_against_fp64(S, N, alpha, g, steps):
         ref = O.run(P, phi1, np.zeros_like(phi1), 2, tier="fft")
         u2 = _run_gpu(S, N, alpha, kappa, tau, g, phi1, None, 2, S.SADI_PREC_FP64)
         assert O.rel_l2(u2, ref) <= 1e-10, O.rel_l2(u2, ref)
+
+
+@pytest.mark.parametrize("N,alpha,g,steps", [(2047, 1.4, 1, 5), (4095, 1.7, 2, 3)])
+@pytest.mark.parametrize("prec_name", ["SADI_PREC_FP32", "SADI_PREC_FP32_DENSE"])
+def test_three_pass_convolution_against_fp64(S, N, alpha, g, steps, prec_name):
+    # conv_cols = -1: the column convolution as three passes of a four-step
+    # FFT (64-point transforms over strided rows, R1 = 32 at N' = 2048 and 64
+    # at N' = 4096; R1 = 128 at N' = 8192 is the default there and covered by
+    # the full-size tests), against the FP64 path with the FP32 forms'
+    # tolerance and against the single-pass kernel (rounding only)
+    prec = getattr(S, prec_name)
+    tau, kappa = 5e-4, 0.5
+    phi1 = WL.gaussian_bumps(N, 8, 2100 + N)
+    phi2 = 0.1 * WL.gaussian_bumps(N, 3, 2200 + N)
+    u64 = _run_gpu(S, N, alpha, kappa, tau, g, phi1, phi2, steps, S.SADI_PREC_FP64)
+    with S.Sadi(N, alpha, kappa, tau) as s:
+        s.set_options(g, prec)
+        t = s.sadi_get_tiles()
+        s.sadi_set_tiles(t[0], -1, t[2])
+        assert s.sadi_get_tiles()[1] == -1
+        s.set_initial(phi1, phi2)
+        s.step(steps)
+        u3, _ = s.get()
+    assert O.rel_l2(u3, u64) <= 1e-5, O.rel_l2(u3, u64)
+    u1 = _run_gpu(S, N, alpha, kappa, tau, g, phi1, phi2, steps, prec)
+    assert O.rel_l2(u3, u1) <= 1e-6, O.rel_l2(u3, u1)
+
+
+def test_three_pass_convolution_rejected_where_it_does_not_apply(S):
+    # FP64, and the register path (N' <= 1024), have no three-pass form
+    for N, prec in ((2047, S.SADI_PREC_FP64), (1023, S.SADI_PREC_FP32)):
+        with S.Sadi(N, 1.5, 1.0, 1e-3) as s:
+            s.set_options(0, prec)
+            t = s.sadi_get_tiles()
+            with pytest.raises(S.SadiError) as ei:
+                s.sadi_set_tiles(t[0], -1, t[2])
+            assert ei.value.status == S.SADI_EINVAL
+            assert s.sadi_get_tiles() == t
