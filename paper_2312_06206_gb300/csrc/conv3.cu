@@ -336,7 +336,10 @@ cudaError_t resident_grid(K kernel, int threads, size_t smem, int items, int* gr
 template <int LOGR1>
 cudaError_t launch_b(const Conv3& c, int groups, cudaStream_t st) {
   constexpr int NT = 32 * rf::RegFFT<float, LOGR1>::TT;
-  static int grid = 0;
+  static int grids[kLauncherDevices] = {};
+  const int dev = device_slot();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  int& grid = grids[dev];
   if (!grid) {
     cudaError_t e =
         cudaFuncSetAttribute(k_conv3_b<LOGR1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b<LOGR1>());
@@ -379,14 +382,19 @@ cudaError_t conv3_setup(int Np, int logNp, const float* lpb32, Conv3* c, cudaStr
     conv3_free(&z);
     return e;
   }
-  static bool attr = false;
-  if (!attr) {
+  static bool attrs[kLauncherDevices] = {};
+  const int dev = device_slot();
+  if (dev < 0) {
+    conv3_free(&z);
+    return cudaErrorInvalidDevice;
+  }
+  if (!attrs[dev]) {
     if ((e = cudaFuncSetAttribute(k_conv3_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAC)) ||
         (e = cudaFuncSetAttribute(k_conv3_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAC))) {
       conv3_free(&z);
       return e;
     }
-    attr = true;
+    attrs[dev] = true;
   }
   *c = z;
   return cudaSuccess;
@@ -403,7 +411,10 @@ cudaError_t launch_conv3(const Conv3& c, int N, int Np, void* Sv, const void* tw
   float2* S = static_cast<float2*>(Sv);
   const float2* tw = static_cast<const float2*>(twv);
   const int groups = c.CW / kGroup, items = groups * c.R1;
-  static int grid_ac = 0;
+  static int grids_ac[kLauncherDevices] = {};
+  const int dev = device_slot();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  int& grid_ac = grids_ac[dev];
   if (!grid_ac) {
     const cudaError_t e = resident_grid(k_conv3_a, kThreadsAC, kSmemAC, 1 << 30, &grid_ac);
     if (e != cudaSuccess) {

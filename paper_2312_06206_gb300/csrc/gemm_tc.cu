@@ -650,11 +650,12 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
     boxes += in.tiles_m * in.boxes_n;
     even = even && in.boxes_n % 2 == 0;
   }
-  static int sms = 0;
+  static int sms_of[kLauncherDevices] = {};
+  const int dev = device_slot();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  int& sms = sms_of[dev];
   if (!sms) {
-    int dev = 0;
-    cudaError_t e = cudaGetDevice(&dev);
-    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<256>());
     if (e == cudaSuccess)

@@ -66,6 +66,15 @@ struct StepTables {
   const struct Conv3* c3 = nullptr;   // FP32, N' = 2048 .. 8192: three-pass column convolution
 };
 
+// One-time launcher state (kernel attributes, launch shapes) is per device:
+// launchers keep it in arrays indexed by the current device.
+constexpr int kLauncherDevices = 64;
+inline int device_slot() {
+  int d = 0;
+  if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kLauncherDevices) return -1;
+  return d;
+}
+
 // ---- three-pass column convolution (FP32, N' = 2048 .. 8192), conv3.cu -----
 // N' = R1 x 64; ZE / ZO hold the even / odd frequency halves between the
 // passes (N' rows x CW = N' + 16 columns); Lt is the symbol re-laid for the

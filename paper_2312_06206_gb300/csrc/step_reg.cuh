@@ -578,19 +578,23 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
   using CC = ColCfg<LOGL, kColBlock>;
   using VC = ConvCfg<LOGL, kConvBlock>;
   constexpr int Np = 1 << LOGL;
-  static bool attr_done = false;
-  if (!attr_done) {
-    cudaFuncSetAttribute(kr_rows_r2c<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RC::bytes_r2c);
-    cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RC::bytes_solve);
-    cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)RC::bytes_solve);
-    cudaFuncSetAttribute(kr_cols_conv<LOGL, kConvBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)VC::bytes);
-    cudaFuncSetAttribute(kr_cols_solve<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)CC::bytes_solve);
-    attr_done = true;
+  static bool attr_done[kLauncherDevices] = {};
+  const int dev = device_slot();
+  if (dev < 0) return cudaErrorInvalidDevice;
+  if (!attr_done[dev]) {
+    cudaError_t e;
+    if ((e = cudaFuncSetAttribute(kr_rows_r2c<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)RC::bytes_r2c)) ||
+        (e = cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)RC::bytes_solve)) ||
+        (e = cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::bytes_solve)) ||
+        (e = cudaFuncSetAttribute(kr_cols_conv<LOGL, kConvBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)VC::bytes)) ||
+        (e = cudaFuncSetAttribute(kr_cols_solve<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)CC::bytes_solve)))
+      return e;
+    attr_done[dev] = true;
   }
   const dim3 rgrid((max_n + RC::VB - 1) / RC::VB, b.count);
   const dim3 cgrid((Np + 1 + VC::CT / 2 - 1) / (VC::CT / 2), b.count);
