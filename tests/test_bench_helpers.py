@@ -1,0 +1,37 @@
+"""bench.py's per-step bookkeeping on the CPU: launches per step of each
+step form and FFT length, and the roofline entry's kernel names, bounds and
+traffic lookup (the per-phase times here are made up; only the bookkeeping
+is checked)."""
+import bench
+
+
+def test_launches_per_step_of_each_form():
+    # register path (N' <= 1024): row FFT, convolution, row kernel, and the
+    # y sweep (GS form) or one launch of both sweep GEMMs (dense form)
+    assert bench.launches_per_step(1024, dense=False) == 4
+    assert bench.launches_per_step(1024, dense=True) == 4
+    # shared-memory engine: the GS form's y sweep is transpose, row solve and
+    # transpose with leapfrog; at N' = 8192 the convolution is three passes
+    assert bench.launches_per_step(4096, dense=False) == 6
+    assert bench.launches_per_step(4096, dense=True) == 4
+    assert bench.launches_per_step(8192, dense=False) == 8
+    assert bench.launches_per_step(8192, dense=True) == 6
+
+
+def test_roofline_names_bounds_and_traffic():
+    phase_ms = [0.019, 0.057, 0.044, 0.077]
+    r = bench.roofline_of(phase_ms, 1023, 1024, True, 3, "n1023")
+    assert list(r["kernels"]) == ["kr_rows_r2c", "kr_cols_conv", "kr_rows_solve<dense>", "k_tc_gemm(x+y)"]
+    # the dominant phase here is the merged GEMM, reported against the BF16 peak
+    assert r["kernel"] == "k_tc_gemm(x+y)" and r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["traffic"] == bench.NCU_TRAFFIC[("n1023", "k_tc_gemm(x+y)")]
+    assert abs(r["frac"] - r["achieved"] / r["peak"]) < 1e-12
+    # 12 N^3 flops per instance for both sweeps
+    assert r["kernels"]["k_tc_gemm(x+y)"]["alg_flops"] == 12.0 * 1023 ** 3 * 3
+    # the shared-memory engine's names; no capture -> no traffic
+    r8 = bench.roofline_of([0.68, 1.82, 2.68, 2.24], 8191, 8192, False, 1, "n8191")
+    assert list(r8["kernels"]) == ["k_rows_r2c", "k_conv3_a+b+c", "k_rows_solve",
+                                  "k_transpose+k_rows_gs+k_transpose_leapfrog"]
+    assert r8["bound"] == "alu" and r8["traffic"] is None
+    r4 = bench.roofline_of([0.15, 0.41, 0.30, 0.58], 4095, 4096, True, 1, "n4095")
+    assert "k_cols_conv" in r4["kernels"] and r4["kernel"] == "k_tc_gemm(x+y)"
