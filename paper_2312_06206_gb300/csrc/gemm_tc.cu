@@ -198,15 +198,22 @@ __device__ __forceinline__ void epilogue_block(const TcEpi& e, int rowbase, int 
       if (row < e.m_valid && cok) e.C[(size_t)row * e.ldc + col] = w;
     }
     __syncwarp();
-    // the transposed BF16 split of W (the y-sweep GEMM's B operand): lane = row
-    const int row = rowbase + lane;
-    if (row < e.m_valid) {
+    // the transposed BF16 split of W (the y-sweep GEMM's B operand): lanes
+    // 0-15 take the row pairs of column j, lanes 16-31 those of column j + 1,
+    // one 4-byte store of two adjacent rows per lane.  Rows beyond m_valid
+    // (padding up to the GEMM tile) hold W = 0 there (their B rows and
+    // accumulator rows are zero), so the pairs are stored whole.
+    const int p = lane & 15, jj = lane >> 4;
+    const int row = rowbase + 2 * p;
 #pragma unroll 4
-      for (int j = 0; j < 32; ++j) {
-        if (col0 + j < e.n_valid) {
-          const size_t t = (size_t)(col0 + j) * e.ldt + row;
-          split_bf16(tile[lane * EPI_LD + j], e.t_hi + t, e.t_lo + t);
-        }
+    for (int j = 0; j < 32; j += 2) {
+      const int cj = j + jj;
+      if (col0 + cj < e.n_valid) {
+        unsigned hi, lo;
+        split_bf16x2(tile[(2 * p) * EPI_LD + cj], tile[(2 * p + 1) * EPI_LD + cj], &hi, &lo);
+        const size_t t = (size_t)(col0 + cj) * e.ldt + row;
+        *reinterpret_cast<unsigned*>(e.t_hi + t) = hi;
+        *reinterpret_cast<unsigned*>(e.t_lo + t) = lo;
       }
     }
   } else {
