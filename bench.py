@@ -329,8 +329,8 @@ def aggregate(times, world_size, pts_per_step, steps_list, reduce_max=None):
 # kernel in a workload, from the ncu captures summarised under profiles/
 # (kr_cols_conv_n1023.md, k_tc_gemm_n1023.md, k_tc_gemm_n4095.md); absent =
 # no capture of the current kernel, reported as null.
-NCU_TRAFFIC = {("n1023", "kr_cols_conv"): 50.52e6, ("n1023", "k_tc_gemm(x+y)"): 86.5e6,
-               ("n4095", "k_tc_gemm(x+y)"): 1681.5e6}
+NCU_TRAFFIC = {("n1023", "kr_cols_conv"): 50.52e6, ("n1023", "k_tc_gemm(x+y)"): 86.1e6,
+               ("n4095", "k_tc_gemm(x+y)"): 1687.3e6}
 
 
 def algorithmic(N, Np, es, dense=False):
