@@ -447,13 +447,21 @@ __global__ void __launch_bounds__(BLOCK, 4) kr_rows_solve(const __grid_constant_
     float* wrow = I.W + (size_t)row * N;
     unsigned short* bh = I.Bh + (size_t)row * I.ldp;
     unsigned short* bl = I.Bl + (size_t)row * I.ldp;
+    // B^n at x = 2m and 2m + 1 (one float2 of the buffer) per lane: the BF16
+    // pairs go out as one 4-byte store each (the row pitch ldp is even; at
+    // x = N, the zero padding, the split of 0 is stored)
 #pragma unroll 2
-    for (int q = 0; q < F::E; ++q) {
-      const int k = t + F::TT * q;
+    for (int q = 0; q < F::E / 2; ++q) {
+      const int m = t + F::TT * q, k = 2 * m;
       if (k < N) {
-        const float b = real_at(sm, k);
-        wrow[k] = b;
-        split_bf16(b, bh + k, bl + k);
+        const float2 v = sm[pad32(m)];
+        const bool two = k + 1 < N;
+        wrow[k] = v.x;
+        if (two) wrow[k + 1] = v.y;
+        unsigned hi, lo;
+        split_bf16x2(v.x, two ? v.y : 0.f, &hi, &lo);
+        *reinterpret_cast<unsigned*>(bh + k) = hi;
+        *reinterpret_cast<unsigned*>(bl + k) = lo;
       }
     }
     return;
