@@ -155,6 +155,22 @@ def test_factored_step_equals_literal_three_level_scheme(N, alpha, g):
     assert np.abs(u2f - u2l).max() < 1e-12 * np.abs(u2l).max()
 
 
+@pytest.mark.parametrize("tier", ["direct", "fft"])
+def test_transposed_data_gives_the_transposed_solution(tier):
+    # the scheme is symmetric in x and y (Sec. 3: the two factors act on
+    # different indices and commute, and a_ij = a_ji), so data phi^T must give
+    # u^T; asymmetric data and forcing make any x/y mix-up of the oracle show
+    N, steps = 15, 4
+    P = S.Problem(N, 1.6, 0.8, 0.05, -1.0, 1.0, 1)
+    rng = _rng(77)
+    phi1 = rng.uniform(-1, 1, (N, N))
+    phi2 = 0.3 * rng.uniform(-1, 1, (N, N))
+    u = S.run(P, phi1, phi2, steps, tier=tier)
+    ut = S.run(P, phi1.T.copy(), phi2.T.copy(), steps, tier=tier)
+    assert np.abs(u - u.T).max() > 1e-3 * np.abs(u).max()    # the data is asymmetric
+    assert np.abs(ut - u.T).max() <= 1e-12 * np.abs(u).max()
+
+
 def test_energy_conserved_without_nonlinearity():
     # Sec. 4 stability theorem: with g = 0, (H_n^2 - H_{n-1}^2)/tau = I_2 = 0,
     # so H_n is constant from n = 0 (the start step included).
