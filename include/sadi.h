@@ -44,7 +44,7 @@ typedef enum {
   SADI_ESTATE = 5,        /* call out of order (e.g. step before set_initial)   */
   SADI_ETIMEOUT = 6,      /* a bounded device wait ran out                      */
   SADI_ENONFINITE = 7,    /* non-finite value detected in the state             */
-  SADI_EUNSUPPORTED = 8   /* valid request this build does not implement       */
+  SADI_EUNSUPPORTED = 8   /* valid request this library version does not implement */
 } sadi_status;
 
 /* Nonlinearity g(u) of Sec. 1 (Sec. 6 uses -sin u and -u^3). */
@@ -145,7 +145,7 @@ sadi_status sadi_batch_step(sadi_ctx **ctxs, int count, int nsteps);
  * the same N, alpha, kappa, tau and domain and set to the same g and
  * precision (SADI_EINVAL otherwise); the context continues exactly as the
  * saved one would (bitwise).  Both are synchronous on the context's stream.
- * The blob is tied to this build's layout; it is not an interchange format. */
+ * The blob is tied to this library version's layout; it is not an interchange format. */
 sadi_status sadi_save_state(sadi_ctx *ctx, void *buf, size_t *bytes);
 sadi_status sadi_load_state(sadi_ctx *ctx, const void *buf, size_t bytes);
 
