@@ -23,6 +23,9 @@
  *    error (SADI_ECUDA) the context refuses further steps with SADI_ESTATE.
  *  - All device work of a context is issued on its stream (sadi_set_stream);
  *    calls on one context must not run concurrently from several host threads.
+ *    Different contexts may be driven at the same time, from several host
+ *    threads or on several streams: a context's results do not depend on
+ *    what runs beside it (sadi_step_noalloc excepted, see there).
  */
 #ifndef SADI_H
 #define SADI_H

@@ -336,18 +336,16 @@ cudaError_t resident_grid(K kernel, int threads, size_t smem, int items, int* gr
 template <int LOGR1>
 cudaError_t launch_b(const Conv3& c, int groups, cudaStream_t st) {
   constexpr int NT = 32 * rf::RegFFT<float, LOGR1>::TT;
-  static int grids[kLauncherDevices] = {};
+  static LaunchCache grids[kLauncherDevices];
   const int dev = device_slot();
   if (dev < 0) return cudaErrorInvalidDevice;
-  int& grid = grids[dev];
+  int grid = grids[dev].load(std::memory_order_acquire);
   if (!grid) {
     cudaError_t e =
         cudaFuncSetAttribute(k_conv3_b<LOGR1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_b<LOGR1>());
     if (e == cudaSuccess) e = resident_grid(k_conv3_b<LOGR1>, NT, smem_b<LOGR1>(), 1 << 30, &grid);
-    if (e != cudaSuccess) {
-      grid = 0;
-      return e;
-    }
+    if (e != cudaSuccess) return e;
+    grids[dev].store(grid, std::memory_order_release);
   }
   const int items = groups * kR2;
   k_conv3_b<LOGR1><<<grid < items ? grid : items, NT, smem_b<LOGR1>(), st>>>(c);
@@ -382,19 +380,19 @@ cudaError_t conv3_setup(int Np, int logNp, const float* lpb32, Conv3* c, cudaStr
     conv3_free(&z);
     return e;
   }
-  static bool attrs[kLauncherDevices] = {};
+  static LaunchCache attrs[kLauncherDevices];
   const int dev = device_slot();
   if (dev < 0) {
     conv3_free(&z);
     return cudaErrorInvalidDevice;
   }
-  if (!attrs[dev]) {
+  if (!attrs[dev].load(std::memory_order_acquire)) {
     if ((e = cudaFuncSetAttribute(k_conv3_a, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAC)) ||
         (e = cudaFuncSetAttribute(k_conv3_c, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemAC))) {
       conv3_free(&z);
       return e;
     }
-    attrs[dev] = true;
+    attrs[dev].store(1, std::memory_order_release);
   }
   *c = z;
   return cudaSuccess;
@@ -411,16 +409,14 @@ cudaError_t launch_conv3(const Conv3& c, int N, int Np, void* Sv, const void* tw
   float2* S = static_cast<float2*>(Sv);
   const float2* tw = static_cast<const float2*>(twv);
   const int groups = c.CW / kGroup, items = groups * c.R1;
-  static int grids_ac[kLauncherDevices] = {};
+  static LaunchCache grids_ac[kLauncherDevices];
   const int dev = device_slot();
   if (dev < 0) return cudaErrorInvalidDevice;
-  int& grid_ac = grids_ac[dev];
+  int grid_ac = grids_ac[dev].load(std::memory_order_acquire);
   if (!grid_ac) {
     const cudaError_t e = resident_grid(k_conv3_a, kThreadsAC, kSmemAC, 1 << 30, &grid_ac);
-    if (e != cudaSuccess) {
-      grid_ac = 0;
-      return e;
-    }
+    if (e != cudaSuccess) return e;
+    grids_ac[dev].store(grid_ac, std::memory_order_release);
   }
   const int gac = grid_ac < items ? grid_ac : items;
   k_conv3_a<<<gac, kThreadsAC, kSmemAC, st>>>(S, tw, c, N, Np);

@@ -604,15 +604,18 @@ CUresult (*g_encode)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const
                      const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
                      CUtensorMapL2promotion, CUtensorMapFloatOOBfill) = nullptr;
 
+// Looked up once per process; the static's initialisation is thread-safe.
 cudaError_t get_encoder() {
-  if (g_encode) return cudaSuccess;
-  void* fn = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess) return e;
-  if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
-  g_encode = reinterpret_cast<decltype(g_encode)>(fn);
-  return cudaSuccess;
+  static const cudaError_t status = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q);
+    if (e != cudaSuccess) return e;
+    if (q != cudaDriverEntryPointSuccess || !fn) return cudaErrorNotSupported;
+    g_encode = reinterpret_cast<decltype(g_encode)>(fn);
+    return cudaSuccess;
+  }();
+  return status;
 }
 
 }  // namespace
@@ -657,20 +660,18 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
     boxes += in.tiles_m * in.boxes_n;
     even = even && in.boxes_n % 2 == 0;
   }
-  static int sms_of[kLauncherDevices] = {};
+  static LaunchCache sms_of[kLauncherDevices];
   const int dev = device_slot();
   if (dev < 0) return cudaErrorInvalidDevice;
-  int& sms = sms_of[dev];
+  int sms = sms_of[dev].load(std::memory_order_acquire);
   if (!sms) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<256>());
     if (e == cudaSuccess)
       e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<128>());
-    if (e != cudaSuccess) {
-      sms = 0;
-      return e;
-    }
+    if (e != cudaSuccess) return e;
+    sms_of[dev].store(sms, std::memory_order_release);
   }
   // 128 x 256 tiles (fewer operand bytes per flop) once they give every SM
   // two or more; below that the 128 x 128 tiles balance better (measured:
@@ -735,7 +736,7 @@ extern "C" sadi_status sadi_gemm_split_bf16(const float* A, const float* B, floa
     return SADI_ENOMEM;
   }
   unsigned short *ah = buf, *al = buf + na, *bh = buf + 2 * na, *bl = buf + 2 * na + nb;
-  static TcBatch bt;   // about 1.2 KB of tensor maps; built on the host only
+  static thread_local TcBatch bt;   // about 1.2 KB of tensor maps; built on the host only
   std::memset(&bt, 0, sizeof(bt));
   bt.count = 1;
   TcEpi& e = bt.in[0].e;

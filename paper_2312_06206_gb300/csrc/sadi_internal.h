@@ -6,6 +6,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <atomic>
+
 namespace sadi {
 
 // Sizes of one instance.  N interior points per direction; the FFT length
@@ -67,8 +69,12 @@ struct StepTables {
 };
 
 // One-time launcher state (kernel attributes, launch shapes) is per device:
-// launchers keep it in arrays indexed by the current device.
+// launchers keep it in arrays indexed by the current device.  Host threads
+// driving different contexts may make a device's first launches at the same
+// time, so a cached value is stored (release) only after what it vouches for
+// (the kernel attributes) has been set, and loaded with acquire; 0 = not yet.
 constexpr int kLauncherDevices = 64;
+using LaunchCache = std::atomic<int>;
 inline int device_slot() {
   int d = 0;
   if (cudaGetDevice(&d) != cudaSuccess || d < 0 || d >= kLauncherDevices) return -1;

@@ -586,10 +586,10 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
   using CC = ColCfg<LOGL, kColBlock>;
   using VC = ConvCfg<LOGL, kConvBlock>;
   constexpr int Np = 1 << LOGL;
-  static bool attr_done[kLauncherDevices] = {};
+  static LaunchCache attr_done[kLauncherDevices];
   const int dev = device_slot();
   if (dev < 0) return cudaErrorInvalidDevice;
-  if (!attr_done[dev]) {
+  if (!attr_done[dev].load(std::memory_order_acquire)) {
     cudaError_t e;
     if ((e = cudaFuncSetAttribute(kr_rows_r2c<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)RC::bytes_r2c)) ||
@@ -602,7 +602,7 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
         (e = cudaFuncSetAttribute(kr_cols_solve<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)CC::bytes_solve)))
       return e;
-    attr_done[dev] = true;
+    attr_done[dev].store(1, std::memory_order_release);
   }
   const dim3 rgrid((max_n + RC::VB - 1) / RC::VB, b.count);
   const dim3 cgrid((Np + 1 + VC::CT / 2 - 1) / (VC::CT / 2), b.count);

@@ -8,6 +8,7 @@ from __future__ import annotations
 
 import ctypes as C
 import os
+import threading
 
 import numpy as np
 
@@ -77,12 +78,15 @@ def load_library(path: str = LIB_PATH) -> C.CDLL:
 
 
 _lib = None
+_lib_lock = threading.Lock()
 
 
 def lib() -> C.CDLL:
     global _lib
     if _lib is None:
-        _lib = load_library()
+        with _lib_lock:
+            if _lib is None:
+                _lib = load_library()
     return _lib
 
 
