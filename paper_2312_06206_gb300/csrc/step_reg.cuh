@@ -52,6 +52,9 @@ struct RowCfg {
   static constexpr size_t tw_bytes = 2 * (size_t)F::L * sizeof(float2);   // tw1 and tw[0 .. L) staged
   static constexpr size_t bytes_r2c = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
   static constexpr size_t bytes_solve = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
+  // resident blocks per SM promised to the compiler (its register budget):
+  // four narrow blocks, or one wide block of up to 2048 threads
+  static constexpr int kMinBlocks = BLOCK >= 512 ? 1 : 4;
 };
 // The convolution kernel: vectors owned by warps (as in the row kernels), CT
 // per block; the FFT buffers, the vectors' symbol rows (natural order) and
@@ -192,7 +195,7 @@ __device__ __forceinline__ float real_at(const float2* sm, int k) {
 // Every kernel handles one instance per blockIdx.y (a batch of independent
 // problems with the same FFT length); blocks beyond an instance's extent exit.
 template <int LOGL, int BLOCK>
-__global__ void __launch_bounds__(BLOCK, 4) kr_rows_r2c(const __grid_constant__ RegBatch B) {
+__global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_rows_r2c(const __grid_constant__ RegBatch B) {
   using F = rf::RegFFT<float, LOGL>;
   using C = RowCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -332,7 +335,7 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
 // DENSE: the dense-inverse form stops after B^n, which it writes to W (FP32)
 // and, split into BF16 pairs, to Bh / Bl (the first sweep GEMM's A operand).
 template <int LOGL, int BLOCK, bool DENSE = false>
-__global__ void __launch_bounds__(BLOCK, 4) kr_rows_solve(const __grid_constant__ RegBatch B) {
+__global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_rows_solve(const __grid_constant__ RegBatch B) {
   using F = rf::RegFFT<float, LOGL>;
   using C = RowCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -579,6 +582,28 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
 constexpr int kRowBlock = 128;
 constexpr int kColBlock = 128;
 constexpr int kConvBlock = 128;
+// Wide row blocks at N' = 1024: 21 rows (672 threads, 96 registers a thread
+// at most, 192 KB of shared memory with the twiddles staged once), one block
+// per SM, against four narrow blocks of 4 rows.  The row kernels take them
+// when they need fewer waves: three 1023-row instances are 147 wide blocks
+// in one wave, or 768 narrow ones in 1.26 waves of 608.
+constexpr int kRowBlockWide = 672;
+
+// SM count and resident narrow / wide blocks per SM, packed (0 = unknown)
+inline int pack_shape(int sms, int narrow, int wide) {
+  return sms > 0 && sms < 32768 && narrow > 0 && narrow < 256 && wide > 0 && wide < 256
+             ? (sms << 16) | (narrow << 8) | wide
+             : 0;
+}
+// true when blocks of wide_rows rows take fewer waves than blocks of
+// narrow_rows rows for count instances of up to max_n rows
+inline bool fewer_waves(int shape, int count, int max_n, int narrow_rows, int wide_rows) {
+  if (!shape) return false;
+  const long sms = shape >> 16, on = (shape >> 8) & 255, ow = shape & 255;
+  const long nb = (long)count * ((max_n + narrow_rows - 1) / narrow_rows);
+  const long wb = (long)count * ((max_n + wide_rows - 1) / wide_rows);
+  return (wb + sms * ow - 1) / (sms * ow) < (nb + sms * on - 1) / (sms * on);
+}
 
 template <int LOGL>
 cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev, bool dense) {
@@ -586,11 +611,38 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
   using CC = ColCfg<LOGL, kColBlock>;
   using VC = ConvCfg<LOGL, kConvBlock>;
   constexpr int Np = 1 << LOGL;
+  using RW = RowCfg<LOGL, kRowBlockWide>;
   static LaunchCache attr_done[kLauncherDevices];
+  // narrow / wide occupancy of the row kernels (r2c, GS solve, dense B^n),
+  // written before attr_done is published and read after it
+  static LaunchCache shape[3][kLauncherDevices];
   const int dev = device_slot();
   if (dev < 0) return cudaErrorInvalidDevice;
   if (!attr_done[dev].load(std::memory_order_acquire)) {
     cudaError_t e;
+    if constexpr (LOGL == 10) {
+      int sms = 0;
+      if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
+      // (kernel narrow, kernel wide, shared memory) per row kernel
+      auto measure = [&](auto kn, auto kw, size_t bn, size_t bw, LaunchCache& out) {
+        int on = 0, ow = 0;
+        cudaError_t r;
+        if ((r = cudaFuncSetAttribute(kn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bn)) ||
+            (r = cudaFuncSetAttribute(kw, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bw)) ||
+            (r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&on, kn, kRowBlock, bn)) ||
+            (r = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&ow, kw, kRowBlockWide, bw)))
+          return r;
+        out.store(pack_shape(sms, on, ow), std::memory_order_relaxed);
+        return cudaSuccess;
+      };
+      if ((e = measure(kr_rows_r2c<LOGL, kRowBlock>, kr_rows_r2c<LOGL, kRowBlockWide>, RC::bytes_r2c, RW::bytes_r2c,
+                       shape[0][dev])) ||
+          (e = measure(kr_rows_solve<LOGL, kRowBlock>, kr_rows_solve<LOGL, kRowBlockWide>, RC::bytes_solve,
+                       RW::bytes_solve, shape[1][dev])) ||
+          (e = measure(kr_rows_solve<LOGL, kRowBlock, true>, kr_rows_solve<LOGL, kRowBlockWide, true>,
+                       RC::bytes_solve, RW::bytes_solve, shape[2][dev])))
+        return e;
+    }
     if ((e = cudaFuncSetAttribute(kr_rows_r2c<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)RC::bytes_r2c)) ||
         (e = cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -607,16 +659,25 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
   const dim3 rgrid((max_n + RC::VB - 1) / RC::VB, b.count);
   const dim3 cgrid((Np + 1 + VC::CT / 2 - 1) / (VC::CT / 2), b.count);
   const dim3 sgrid((max_n + CC::CT - 1) / CC::CT, b.count);
+  // wide row blocks where they take fewer waves (N' = 1024 only)
+  bool wide[3] = {false, false, false};
+  if constexpr (LOGL == 10)
+    for (int k = 0; k < 3; ++k)
+      wide[k] = fewer_waves(shape[k][dev].load(std::memory_order_relaxed), b.count, max_n, RC::VB, RW::VB);
+  const dim3 wgrid((max_n + RW::VB - 1) / RW::VB, b.count);
   if (ev) cudaEventRecord(ev[0], st);
-  kr_rows_r2c<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_r2c, st>>>(b);
+  if (wide[0]) kr_rows_r2c<LOGL, kRowBlockWide><<<wgrid, kRowBlockWide, RW::bytes_r2c, st>>>(b);
+  else kr_rows_r2c<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_r2c, st>>>(b);
   if (ev) cudaEventRecord(ev[1], st);
   kr_cols_conv<LOGL, kConvBlock><<<cgrid, kConvBlock, VC::bytes, st>>>(b);
   if (ev) cudaEventRecord(ev[2], st);
   if (dense) {
-    kr_rows_solve<LOGL, kRowBlock, true><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
+    if (wide[2]) kr_rows_solve<LOGL, kRowBlockWide, true><<<wgrid, kRowBlockWide, RW::bytes_solve, st>>>(b);
+    else kr_rows_solve<LOGL, kRowBlock, true><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
     return cudaGetLastError();
   }
-  kr_rows_solve<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
+  if (wide[1]) kr_rows_solve<LOGL, kRowBlockWide><<<wgrid, kRowBlockWide, RW::bytes_solve, st>>>(b);
+  else kr_rows_solve<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
   if (ev) cudaEventRecord(ev[3], st);
   kr_cols_solve<LOGL, kColBlock><<<sgrid, kColBlock, CC::bytes_solve, st>>>(b);
   if (ev) cudaEventRecord(ev[4], st);

@@ -163,3 +163,34 @@ def test_long_run_fp32_forms_track_fp64(S, N):
     for prec in (S.SADI_PREC_FP32, S.SADI_PREC_FP32_DENSE):
         u = _run(S, N, alpha, kappa, tau, g, phi1, None, steps, prec)
         assert O.rel_l2(u, u64) <= 1e-6, (prec, O.rel_l2(u, u64))
+
+
+def test_wide_row_blocks_match_narrow_ones_bitwise(S):
+    # three N' = 1024 instances per form exceed one wave of the narrow row
+    # blocks (4 rows, 4 per SM), so the batch takes the wide ones (21 rows,
+    # one per SM) for the row transform, the B^n kernel and the GS x sweep;
+    # a context stepped alone takes the narrow ones.  Every row's arithmetic
+    # is the same either way: the fields agree bitwise.
+    specs = [(1023, 1.2, 1.0, 1e-3, 2, 2), (1023, 1.5, 1.0, 1e-3, 2, 2), (1001, 1.8, 0.9, 1e-3, 1, 2),
+             (1023, 1.4, 0.9, 1e-3, 1, 1), (900, 1.6, 1.1, 1e-3, 2, 1), (1023, 1.3, 0.8, 1e-3, 2, 1)]
+
+    def make():
+        out = []
+        for k, (N, al, ka, ta, g, prec) in enumerate(specs):
+            s = S.Sadi(N, al, ka, ta)
+            s.set_options(g, prec)
+            s.set_initial(WL.gaussian_bumps(N, 6, 1300 + k), 0.3 * WL.random_field(N, 1400 + k))
+            out.append(s)
+        return out
+    single = make()
+    for s in single:
+        s.step(4)
+    ref = [s.get()[0] for s in single]
+    batch = make()
+    S.sadi_batch_step(batch, 4)
+    for k, (s, r) in enumerate(zip(batch, ref)):
+        u, n = s.get()
+        assert n == 4
+        assert np.array_equal(u, r), f"instance {k} {specs[k]}"
+    for s in single + batch:
+        s.close()
