@@ -582,9 +582,10 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
 constexpr int kRowBlock = 128;
 constexpr int kColBlock = 128;
 constexpr int kConvBlock = 128;
-// Wide row blocks at N' = 1024: 21 rows (672 threads, 96 registers a thread
-// at most, 192 KB of shared memory with the twiddles staged once), one block
-// per SM, against four narrow blocks of 4 rows.  The row kernels take them
+// Wide row blocks at N' = 1024: 21 rows (672 threads, at most 96 registers a
+// thread, which the row kernels meet without spilling; 192 KB of shared
+// memory with the twiddles staged once), one block per SM, against four
+// narrow blocks of 4 rows.  The row kernels take them
 // when they need fewer waves: three 1023-row instances are 147 wide blocks
 // in one wave, or 768 narrow ones in 1.26 waves of 608.
 constexpr int kRowBlockWide = 672;
@@ -610,8 +611,8 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
   using RC = RowCfg<LOGL, kRowBlock>;
   using CC = ColCfg<LOGL, kColBlock>;
   using VC = ConvCfg<LOGL, kConvBlock>;
-  constexpr int Np = 1 << LOGL;
   using RW = RowCfg<LOGL, kRowBlockWide>;
+  constexpr int Np = 1 << LOGL;
   static LaunchCache attr_done[kLauncherDevices];
   // narrow / wide occupancy of the row kernels (r2c, GS solve, dense B^n),
   // written before attr_done is published and read after it
@@ -623,7 +624,7 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
     if constexpr (LOGL == 10) {
       int sms = 0;
       if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev))) return e;
-      // (kernel narrow, kernel wide, shared memory) per row kernel
+      // resident narrow and wide blocks per SM of one row kernel
       auto measure = [&](auto kn, auto kw, size_t bn, size_t bw, LaunchCache& out) {
         int on = 0, ow = 0;
         cudaError_t r;
