@@ -132,7 +132,7 @@ __device__ __forceinline__ void gs_reg(float2* x, float2* sm, int t, const float
                                        const float2* __restrict__ tw, const float2* __restrict__ lam_s,
                                        const float2* __restrict__ lam_c) {
   using F = rf::RegFFT<float, LOGL>;
-  // round 0: x lambda_s then Q^H; round 1: x lambda_c.  Rolled so that the
+  // first pass: x lambda_s then Q^H; second pass: x lambda_c.  Rolled so that the
   // kernel holds one forward and one inverse transform body.
 #pragma unroll 1
   for (int round = 0; round < 2; ++round) {
