@@ -194,3 +194,26 @@ def test_wide_row_blocks_match_narrow_ones_bitwise(S):
         assert np.array_equal(u, r), f"instance {k} {specs[k]}"
     for s in single + batch:
         s.close()
+
+
+def test_bench_launch_configuration_against_the_oracle(S):
+    # the N = 1023 workload as the benchmark steps it: its three alpha
+    # instances batched in the dense form (one launch per kernel, the wide row
+    # blocks, both sweeps of all three in one GEMM launch), each instance
+    # against the oracle's FFT tier
+    ws = [WL.bumps_1023(al, steps=4) for al in (1.2, 1.5, 1.8)]
+    ctxs = []
+    for w in ws:
+        s = S.Sadi(w.N, w.alpha, w.kappa, w.tau, (w.a, w.b))
+        s.set_options(w.g, S.SADI_PREC_FP32_DENSE)
+        s.set_initial(w.phi1, w.phi2)
+        ctxs.append(s)
+    S.sadi_batch_step(ctxs, 4)
+    for w, s in zip(ws, ctxs):
+        u, n = s.get()
+        s.close()
+        assert n == 4
+        P = O.Problem(w.N, w.alpha, w.kappa, w.tau, w.a, w.b, w.g)
+        ref = O.run(P, w.phi1, w.phi2, w.steps, tier="fft")
+        err = O.rel_l2(u, ref)
+        assert err <= 1e-5, (w.alpha, err)
