@@ -87,3 +87,29 @@ def test_batch_instances_follow_the_recipe():
         assert 1.1 <= al <= 1.9 and 0.5 <= ka <= 2.0 and ta == 1.0 / (N + 1)
     assert len({x[0] for x in inst}) == 5
     assert inst == bench.batch_instances(bench.PRESETS["batch256"])   # seeded
+
+
+def test_reference_arm_under_torchrun_prints_one_line_from_rank_0():
+    # the reference arm launched the way every arm is launched for N > 1
+    # (torchrun, one process per GPU): rank 0 times the oracle and prints one
+    # JSON line; the other rank exits 0 without work
+    import json
+    import socket
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+           "--master-addr", "127.0.0.1", "--master-port", str(port), "bench.py",
+           "--impl", "reference", "--gpus", "2", "--steps", "2", "--warmup", "1", "--N", "63"]
+    r = subprocess.run(cmd, cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-3000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1, r.stdout[-3000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["steps"] == 2 and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
