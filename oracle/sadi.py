@@ -37,6 +37,7 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 
 import numpy as np
+import scipy.fft
 import scipy.linalg
 
 from . import weights as W
@@ -74,6 +75,8 @@ class Problem:
     g: int = G_ZERO
     A2: np.ndarray | None = field(default=None, repr=False)   # a_ij, 0<=i,j<N
     a1: np.ndarray | None = field(default=None, repr=False)   # a_i, 0<=i<N
+    fft_size: int | None = None      # circulant size Q >= 2N - 1 of the fft tier (default 2N)
+    fft_workers: int | None = None   # threads of its transforms (default 1)
 
     def __post_init__(self):
         self.h, self.x = grid(self.N, self.a, self.b)
@@ -121,16 +124,25 @@ def lh_fft(P: Problem, u: np.ndarray) -> np.ndarray:
     """L_h u by embedding the block-Toeplitz-Toeplitz-block matrix into a block
     circulant one of size Q x Q (Q >= 2N - 1) and multiplying with 2D FFTs
     (Sec. 3): the wrapped kernel holds a_{|i|,|j|} at (i mod Q, j mod Q) for
-    |i|, |j| <= N - 1 and zero elsewhere."""
+    |i|, |j| <= N - 1 and zero elsewhere.  Any Q >= 2N - 1 gives the same
+    product (no wrapped term reaches the kept N x N block); Q = P.fft_size,
+    default 2N.  The kernel's transform is computed once per Problem and Q."""
     N = P.N
-    Q = 2 * N
-    dist = np.minimum(np.arange(Q), Q - np.arange(Q))     # |i| of the wrapped index
-    ok = dist <= N - 1
-    dc = np.minimum(dist, N - 1)
-    K = np.where(ok[:, None] & ok[None, :], P.A2[dc[:, None], dc[None, :]], 0.0)
+    Q = P.fft_size or 2 * N
+    if Q < 2 * N - 1:
+        raise ValueError(f"circulant size {Q} < 2N - 1 = {2 * N - 1}")
+    cache = P.__dict__.setdefault("_khat", {})
+    if Q not in cache:
+        dist = np.minimum(np.arange(Q), Q - np.arange(Q))     # |i| of the wrapped index
+        ok = dist <= N - 1
+        dc = np.minimum(dist, N - 1)
+        K = np.where(ok[:, None] & ok[None, :], P.A2[dc[:, None], dc[None, :]], 0.0)
+        cache[Q] = scipy.fft.rfft2(K, workers=P.fft_workers)
+        del K
     U = np.zeros((Q, Q))
     U[:N, :N] = u
-    conv = np.fft.irfft2(np.fft.rfft2(K) * np.fft.rfft2(U), s=(Q, Q))
+    conv = scipy.fft.irfft2(cache[Q] * scipy.fft.rfft2(U, workers=P.fft_workers), s=(Q, Q),
+                            workers=P.fft_workers)
     return conv[:N, :N] / P.h ** P.alpha
 
 

@@ -47,6 +47,18 @@ def test_lh_fft_equals_direct(N):
     assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
 
 
+@pytest.mark.parametrize("N,Q", [(16, 31), (16, 64), (31, 61), (31, 70), (1, 1)])
+def test_lh_fft_any_circulant_size_equals_direct(N, Q):
+    # Sec. 3: the block-circulant embedding reproduces the block-Toeplitz
+    # product for every size Q >= 2N - 1 (the smallest one included)
+    P = S.Problem(N, 1.4, 1.0, 0.1, fft_size=Q, fft_workers=2)
+    u = _rng(N + Q).standard_normal((N, N))
+    a, b = S.lh_fft(P, u), S.lh_direct(P, u)
+    assert np.abs(a - b).max() < 1e-12 * np.abs(b).max()
+    with pytest.raises(ValueError):
+        S.lh_fft(S.Problem(N + 1, 1.4, 1.0, 0.1, fft_size=2 * N), u)
+
+
 @pytest.mark.parametrize("alpha", [1.3, 1.7])
 def test_lh_unit_disk_closed_form(alpha):
     # (-Delta)^{alpha/2} (1 - r^2)_+^{alpha/2} = 2^alpha Gamma(1 + alpha/2)^2 for

@@ -47,6 +47,15 @@ def test_trapezoid_cosine_shortcut_equals_bruteforce_dft():
         assert np.abs(A - B).max() < 1e-15
 
 
+def test_trapezoid_blocked_evaluation_equals_bruteforce_dft():
+    # the blocked, threaded evaluation (ragged last block) sums the same
+    # trapezoid rule: it must equal the literal 2D DFT as well
+    for alpha, N, M, chunk in [(1.3, 9, 64, 5), (1.6, 20, 128, 7), (1.9, 33, 128, 64)]:
+        A = W.lap2d_trap_single(alpha, N, M, chunk=chunk, workers=3)
+        B = W.lap2d_trap_bruteforce(alpha, N, M)
+        assert np.abs(A - B).max() < 1e-15, (alpha, N, M, chunk)
+
+
 @pytest.mark.parametrize("alpha", [1.2, 1.5, 1.8])
 def test_lap2d_trapezoid_vs_bessel_integral(alpha):
     # Sec. 2 eq. "center discretization": W1 (trapezoid + Richardson) against
@@ -100,3 +109,31 @@ def test_lap2d_diagonal_sum_rule():
         sums.append(full)
     assert sums[0] > sums[1] > sums[2] > 0
     assert 2 ** 1.3 < sums[0] / sums[1] < 2 ** 1.7
+
+
+def test_bessel_integral_large_argument_branch():
+    # the Hankel expansion that replaces scipy's ive above z = 1e8 agrees with
+    # it just below the switch, for orders up to the largest grid offset
+    import scipy.special as sp
+    z = 0.99 * W._IVE_SWITCH
+    saved = W._IVE_SWITCH
+    try:
+        W._IVE_SWITCH = 0.0
+        for n in (0, 1, 17, 1000, 8190):
+            assert abs(W._ive(n, z) - sp.ive(n, z)) <= 1e-14 * sp.ive(n, z), n
+    finally:
+        W._IVE_SWITCH = saved
+
+
+@pytest.mark.parametrize("alpha", [1.2, 1.6, 1.9])
+def test_bessel_weights_far_field_constant(alpha):
+    # far from the origin a_ij -> -C rho^-(2+alpha) with the kernel constant of
+    # the fractional Laplacian in two dimensions, C = 2^alpha Gamma(1 + alpha/2)
+    # / (pi |Gamma(-alpha/2)|) (Sec. 1); the relative correction is O(rho^-2),
+    # so at rho >= 3000 the Bessel-integral weights must match to 1e-5.  This
+    # pins the integrator where the integrand peaks at t ~ rho^2 / 4.
+    C = 2 ** alpha * math.gamma(1 + alpha / 2) / (math.pi * abs(math.gamma(-alpha / 2)))
+    for (i, j) in [(3000, 0), (3000, 4000), (8190, 0), (8190, 8190)]:
+        rho = math.hypot(i, j)
+        a = W.lap2d_bessel(alpha, i, j)
+        assert abs(a * rho ** (2 + alpha) / -C - 1.0) < 1e-5, (i, j, a)
