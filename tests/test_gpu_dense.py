@@ -76,6 +76,7 @@ def test_dense_step_parity(S, N, alpha, g):
     ref = O.run(P, phi1, phi2, steps, tier="fft" if N > 40 else "direct")
     u = _run(S, N, alpha, kappa, tau, g, phi1, phi2, steps, S.SADI_PREC_FP32_DENSE)
     assert O.rel_l2(u, ref) <= 1e-5, O.rel_l2(u, ref)
+    assert np.abs(u - ref).max() <= 1e-5 * np.abs(ref).max()   # element-wise too
 
 
 def test_dense_full_size_1023(S):
@@ -84,6 +85,7 @@ def test_dense_full_size_1023(S):
     ref = O.run(P, w.phi1, w.phi2, w.steps, tier="fft")
     u = _run(S, w.N, w.alpha, w.kappa, w.tau, w.g, w.phi1, w.phi2, w.steps, S.SADI_PREC_FP32_DENSE)
     assert O.rel_l2(u, ref) <= 1e-5, O.rel_l2(u, ref)
+    assert np.abs(u - ref).max() <= 1e-5 * np.abs(ref).max()   # element-wise too
 
 
 @pytest.mark.parametrize("N,alpha,g,steps", [(2047, 1.4, 1, 5), (4095, 1.7, 1, 3)])
@@ -217,3 +219,5 @@ def test_bench_launch_configuration_against_the_oracle(S):
         ref = O.run(P, w.phi1, w.phi2, w.steps, tier="fft")
         err = O.rel_l2(u, ref)
         assert err <= 1e-5, (w.alpha, err)
+        ew = np.abs(u - ref).max() / np.abs(ref).max()
+        assert ew <= 1e-5, (w.alpha, ew)   # element-wise too

@@ -104,6 +104,7 @@ def test_fp32_step_parity(S, N, alpha, g):
     ref = O.run(P, phi1, phi2, steps, tier="fft")
     u = _run_gpu(S, N, alpha, kappa, tau, g, phi1, phi2, steps, S.SADI_PREC_FP32)
     assert O.rel_l2(u, ref) <= 1e-5, O.rel_l2(u, ref)
+    assert np.abs(u - ref).max() <= 1e-5 * np.abs(ref).max()   # element-wise too
 
 
 def test_full_size_1023_fp64_and_fp32(S):
@@ -116,6 +117,8 @@ def test_full_size_1023_fp64_and_fp32(S):
     assert O.rel_l2(u64, ref) <= 1e-10, O.rel_l2(u64, ref)
     u32 = _run_gpu(S, w.N, w.alpha, w.kappa, w.tau, w.g, w.phi1, w.phi2, w.steps, S.SADI_PREC_FP32)
     assert O.rel_l2(u32, ref) <= 1e-5, O.rel_l2(u32, ref)
+    assert np.abs(u32 - ref).max() <= 1e-5 * np.abs(ref).max()
+    assert np.abs(u64 - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
 def test_rerun_is_bitwise_identical_and_symmetric(S):
