@@ -333,25 +333,35 @@ NCU_TRAFFIC = {("n1023", "kr_cols_conv"): 50.52e6, ("n1023", "k_tc_gemm(x+y)"): 
                ("n4095", "k_tc_gemm(x+y)"): 1687.3e6}
 
 
-def algorithmic(N, Np, es, dense=False):
-    """Per-launch algorithmic work of the four timed phases of one instance,
-    for the roofline: [(bytes, flops, bound)].  FFT flops are the nominal
-    5 L log2 L of a complex FFT of length L; a split-BF16 sweep GEMM counts
-    three BF16 products of 2 N^3 flops (both sweeps: 12 N^3)."""
-    cs = 2 * es
-    fft = 5.0 * Np * math.log2(Np)
-    r2c = (N * N * es + N * Np * cs, N * fft, "alu")
-    conv = (2 * N * Np * cs + 2 * Np * Np * es, Np * 4 * fft, "alu")
+# Algorithmic work per grid point of one instance and step, per kernel
+# (the method's own bytes of the FP32 design: the per-kernel input and output
+# each step must move, and the method's FFT flops at the nominal 5 L log2 L of
+# a complex FFT of length L).  a1 row FFT: u^n in (4), spectrum row out (8);
+# a2 column convolution: spectrum in and out (16), symbol (N'+1)^2 ~ N^2
+# floats (4); a3 row inverse FFT + B^n + x sweep: spectrum in (8), u^n in (4),
+# W out (4); a4 + a5 y sweep + leapfrog: W, u^n, u^{n-1} in, u^{n+1} out (16).
+# The dense form splits a3: its B^n kernel writes B (4) instead of W, and one
+# GEMM launch runs the x sweep (B in, W out: 8) and a4 + a5 (16).  The dense
+# form's sweeps run no FFT flops; the tensor work they do instead (three
+# BF16 products of 2 N^3 per sweep) is reported separately as a dense
+# equivalent, not as the method's work.
+BYTES_PER_PT = {"rows_r2c": 12, "cols_conv": 20, "rows_solve": 16, "cols_solve": 16,
+                "rows_solve<dense>": 16, "tc_gemm": 24}
+
+
+def algorithmic(N, Np, dense=False):
+    """[(bytes, flops)] of the four timed phases for one instance (flops None
+    where the kernel runs none of the method's arithmetic)."""
+    pts = N * N
+    fft = 5.0 * Np * math.log2(Np)           # one complex FFT of length N'
+    r2c = (BYTES_PER_PT["rows_r2c"] * pts, N * fft)                  # one transform per row
+    conv = (BYTES_PER_PT["cols_conv"] * pts, 4 * Np * fft)          # 2 + 2 per column pair, N' pairs
     if not dense:
-        return [r2c, conv, (N * Np * cs + 2 * N * N * es, N * 5 * fft, "alu"),
-                (4 * N * N * es, N * 4 * fft, "alu")]
-    # phase 2: the B^n kernel (spectrum row in; remainder pair read and
-    # written; u^n in; W and its BF16 pair out); phase 3: both sweep GEMMs in
-    # one launch (x: B pair, E pair, W in place, W^T pair out; y: E pair, W^T
-    # pair, W in, the state triple read and written)
-    rows = (N * Np * cs + 6 * N * N * es + 4 * N * N, N * fft, "alu")
-    gemms = (24 * N * N + 9 * N * N * es, 12.0 * N ** 3, "tensor")
-    return [r2c, conv, rows, gemms]
+        return [r2c, conv,
+                (BYTES_PER_PT["rows_solve"] * pts, N * 5 * fft),    # inverse row FFT + Algorithm 1 (4)
+                (BYTES_PER_PT["cols_solve"] * pts, N * 4 * fft)]    # Algorithm 1 per column
+    return [r2c, conv, (BYTES_PER_PT["rows_solve<dense>"] * pts, N * fft),
+            (BYTES_PER_PT["tc_gemm"] * pts, None)]
 
 
 def launches_per_step(Np, dense):
@@ -365,9 +375,29 @@ def launches_per_step(Np, dense):
     return 2 + conv + (3 if Np > 1024 else 1)
 
 
+def peaks_of():
+    """Roofline denominators: the measured copy bandwidth and sustained BF16
+    rate (MEASURED_PEAKS.json), and the FP32 FMA peak at the measured maximum
+    SM clock (152 SMs x 128 lanes x 2 flops)."""
+    peaks = {}
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            peaks = json.load(f)
+    except Exception:
+        pass
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    return {"fp32_tflops": 152 * 128 * 2 * sm_max * 1e6 / 1e12, "sm_max_mhz": sm_max,
+            "hbm_gbs": float(peaks.get("hbm_gbs", 6800.0)),
+            "bf16_tflops_sustained": float(peaks.get("bf16_tflops_sustained", 1700.0)),
+            "source": "measured" if peaks else "fallback"}
+
+
 def roofline_of(phase_ms, N, Np, dense, ninst, workload):
     """Roofline entry of the dominant kernel from the per-phase times (ms per
-    step, one launch per phase covering ninst instances of size N)."""
+    step, one launch per phase covering ninst instances of size N).  Each
+    kernel's bound is the roof its algorithmic intensity (method flops per
+    method byte) meets first: HBM below the ridge FP32 peak / HBM peak, the
+    FP32 pipes above it; a kernel with no method flops is HBM-bound."""
     reg = Np <= 1024
     pre = "kr_" if reg else "k_"
     conv = "kr_cols_conv" if reg else ("k_conv3_a+b+c" if Np == 8192 else "k_cols_conv")   # three passes at 8192
@@ -376,39 +406,75 @@ def roofline_of(phase_ms, N, Np, dense, ninst, workload):
     else:
         ysweep = "kr_cols_solve" if reg else "k_transpose+k_rows_gs+k_transpose_leapfrog"
         names = [pre + "rows_r2c", conv, pre + "rows_solve", ysweep]
-    alg = algorithmic(N, Np, 4, dense)
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    fp32_peak = 152 * 128 * 2 * sm_max * 1e6 / 1e12
-    hbm_peak = float(peaks.get("hbm_gbs", 6750.0))
-    bf16_peak = float(peaks.get("bf16_tflops_sustained", 1711.7))
+    alg = algorithmic(N, Np, dense)
+    pk = peaks_of()
+    fp32_peak, hbm_peak, bf16_peak = pk["fp32_tflops"], pk["hbm_gbs"], pk["bf16_tflops_sustained"]
+    ridge = fp32_peak * 1e12 / (hbm_peak * 1e9)
     per_kernel = {}
     for k, nm in enumerate(names):
-        b_alg, f_alg, bound = alg[k]
+        b_alg, f_alg = alg[k]
         dur = phase_ms[k] / 1e3
-        peak = bf16_peak if bound == "tensor" else fp32_peak
-        ach = f_alg * ninst / dur / 1e12
-        per_kernel[nm] = {"us": phase_ms[k] * 1e3, "share": phase_ms[k] / sum(phase_ms), "bound": bound,
-                          "achieved_tflops": ach, "frac": None if bound == "mixed" else ach / peak,
-                          "hbm_gbs": b_alg * ninst / dur / 1e9, "alg_bytes": b_alg * ninst,
-                          "alg_flops": f_alg * ninst, "traffic": NCU_TRAFFIC.get((workload, nm))}
-    dom = max((k for k in range(4) if alg[k][2] != "mixed"), key=lambda k: phase_ms[k])
+        inten = None if f_alg is None else f_alg / b_alg
+        bound = "hbm" if inten is None or inten < ridge else "alu"
+        gbs = b_alg * ninst / dur / 1e9
+        tfl = None if f_alg is None else f_alg * ninst / dur / 1e12
+        ach, peak, unit = (gbs, hbm_peak, "GB/s") if bound == "hbm" else (tfl, fp32_peak, "TFLOP/s")
+        e = {"us": phase_ms[k] * 1e3, "share": phase_ms[k] / sum(phase_ms), "bound": bound,
+             "intensity_flop_per_byte": inten, "achieved": ach, "peak": peak, "unit": unit, "frac": ach / peak,
+             "hbm_gbs": gbs, "hbm_frac": gbs / hbm_peak, "fp32_tflops": tfl,
+             "alg_bytes": b_alg * ninst, "alg_flops": None if f_alg is None else f_alg * ninst,
+             "traffic": NCU_TRAFFIC.get((workload, nm))}
+        if nm.startswith("k_tc_gemm"):
+            dflops = 12.0 * N ** 3 * ninst
+            e["dense_equivalent"] = {"what": "split-BF16 tensor work of the dense-inverse sweeps (3 BF16 "
+                                             "products of 2N^3 per sweep), not the method's work",
+                                     "tflops": dflops / dur / 1e12, "peak": bf16_peak,
+                                     "frac": dflops / dur / 1e12 / bf16_peak}
+        per_kernel[nm] = e
+    dom = max(range(4), key=lambda k: phase_ms[k])
     dname = names[dom]
     dk = per_kernel[dname]
-    return {"kernel": dname, "bound": "tensor" if dk["bound"] == "tensor" else "alu",
-            "achieved": dk["achieved_tflops"],
-            "peak": bf16_peak if dk["bound"] == "tensor" else fp32_peak, "unit": "TFLOP/s",
-            "frac": dk["frac"], "traffic": dk["traffic"], "avg_launch_us": dk["us"],
-            "traffic_note": "ncu dram bytes per launch from profiles/ (null if no capture of this kernel)",
-            "peak_note": ("bf16 dense sustained of measured (MEASURED_PEAKS.json), split-BF16 counted "
-                          "as three BF16 products" if dk["bound"] == "tensor" else
-                          f"FP32 FMA peak at the measured max clock: 152 SM x 128 lanes x 2 x {sm_max:.0f} MHz"),
-            "hbm_view": {"achieved_gbs": dk["hbm_gbs"], "peak_gbs": hbm_peak, "frac": dk["hbm_gbs"] / hbm_peak},
-            "kernels": per_kernel}
+    src = pk["source"]
+    out = {"kernel": dname, "bound": dk["bound"], "achieved": dk["achieved"], "peak": dk["peak"],
+           "unit": dk["unit"], "frac": dk["frac"], "traffic": dk["traffic"], "avg_launch_us": dk["us"],
+           "units_per_launch": f"{ninst} x {N}^2 grid points",
+           "per_unit": (f"{alg[dom][0] // (N * N)} B/pt" +
+                        ("" if alg[dom][1] is None else f", {alg[dom][1] / (N * N):.0f} flop/pt")),
+           "traffic_note": "ncu dram bytes per launch from profiles/ (null if no capture of this kernel)",
+           "peak_note": (f"copy bandwidth, {src} (MEASURED_PEAKS.json)" if dk["bound"] == "hbm" else
+                         f"FP32 FMA peak at the {src} max clock: 152 SM x 128 lanes x 2 x "
+                         f"{pk['sm_max_mhz']:.0f} MHz"),
+           "ridge_flop_per_byte": ridge, "kernels": per_kernel}
+    if "dense_equivalent" in dk:
+        out["dense_equivalent"] = dk["dense_equivalent"]
+    return out
+
+
+def c1_latency(S, stream, reps=3):
+    """The small configuration (N = 63, alpha = 1.5, kappa = 1, tau = 1/64,
+    64 steps, g = -u^3, FP64, one instance): microseconds per step, CUDA
+    events on the launching stream around sadi_step(64) after set_initial,
+    best of reps runs after one warm-up run.  Latency-bound (4 launches of a
+    few blocks per step)."""
+    import torch
+    from paper_2312_06206_gb300 import workloads as WL
+    w = WL.small_fp64(63)
+    best = float("inf")
+    with S.Sadi(w.N, w.alpha, w.kappa, w.tau, (w.a, w.b)) as s:
+        s.set_options(w.g, S.SADI_PREC_FP64)
+        s.set_stream(stream.cuda_stream)
+        for r in range(reps + 1):
+            s.set_initial(w.phi1, w.phi2)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            s.step(w.steps)
+            e1.record(stream)
+            e1.synchronize()
+            if r > 0:
+                best = min(best, e0.elapsed_time(e1))
+    return {"workload": "sadi N=63 alpha=1.5 kappa=1 tau=1/64 64 steps g=-u^3 phi1=exp(-20r^2) phi2=0, FP64",
+            "us_per_step": best * 1e3 / w.steps, "value": w.N * w.N * w.steps / (best / 1e3), "unit": UNIT,
+            "timing": f"CUDA events around sadi_step({w.steps}) after set_initial, best of {reps}"}
 
 
 def run_batch(a):
@@ -818,6 +884,7 @@ def main():
     agg = aggregate([res[chosen]["ms"], ms64 if has64 else 1.0, dt_e2e], ws, pts, (a.steps, K64, Ke), reduce_max)
     agg_o = {n: aggregate([res[n]["ms"], 1.0, 1.0], ws, pts, (a.steps, 1, 1), reduce_max) for n in others}
     value, value64, e2e_val = agg["value"], agg["value64"], agg["e2e"]
+    c1 = c1_latency(S, stream) if rank == 0 and a.workload == "n1023" else None
     if rank == 0:
         cpu = None
         rel_oracle = None
@@ -855,6 +922,7 @@ def main():
             "speedup_vs_fp64": value / value64 if has64 else None,
             "forms": forms_out,
             "rel_l2_vs_oracle_4steps": rel_oracle,
+            "c1_small": c1,
             "roofline": roofline,
             "batched": "one launch per kernel covers all instances (sadi_batch_step)",
             "cpu_baseline": None if cpu is None else {k: cpu[k] for k in ("value", "unit", "cores", "kind", "sample")},
