@@ -114,3 +114,41 @@ def test_noalloc_rejects_what_it_cannot_serve(env):
         with pytest.raises(S.SadiError) as ei:
             s.sadi_step_noalloc(d[0].data_ptr(), d[1].data_ptr(), d[2].data_ptr(), 1)
         assert ei.value.status == S.SADI_EUNSUPPORTED
+
+
+def test_noalloc_allocates_nothing_and_checks_buffer_lengths(env):
+    S, torch = env
+    dev = torch.device("cuda:0")
+    N = 512
+    nn_bytes = N * N * 8
+    with S.Sadi(N, 1.5, 1.0, 2.0 / (N + 1)) as s:
+        s.set_options(1, S.SADI_PREC_FP64)
+        st = torch.cuda.Stream(device=dev)
+        s.sadi_set_stream(st.cuda_stream)
+        u = [torch.tensor(WL.gaussian_bumps(N, 4, seed=WL.SEED_BASE + 50 + k), dtype=torch.float64, device=dev)
+             for k in range(3)]
+        torch.cuda.synchronize()
+        s.sadi_step_noalloc(u[0].data_ptr(), u[1].data_ptr(), u[2].data_ptr(), 1)   # device set-up done
+        st.synchronize()
+        free0 = torch.cuda.mem_get_info(dev)[0]
+        for k in range(4):
+            s.sadi_step_noalloc(u[k % 3].data_ptr(), u[(k + 1) % 3].data_ptr(), u[(k + 2) % 3].data_ptr(), 2 + k)
+        st.synchronize()
+        assert torch.cuda.mem_get_info(dev)[0] == free0, "a call changed the free device memory"
+        assert all(bool(torch.isfinite(x).all()) for x in u)
+        # a buffer that ends one grid row early inside its allocation: a fresh
+        # 12 MiB tensor (above the caching allocator's 10 MB threshold, so it
+        # gets an allocation of its own), pointers placed near its end
+        torch.cuda.empty_cache()
+        T = torch.zeros((12 << 20) // 8, dtype=torch.float64, device=dev)
+        end = T.data_ptr() + (12 << 20)
+        short = end - (nn_bytes - 8 * N)
+        exact = end - nn_bytes
+        for args in ((short, u[1].data_ptr(), u[2].data_ptr()), (u[0].data_ptr(), short, u[2].data_ptr()),
+                     (u[0].data_ptr(), u[1].data_ptr(), short)):
+            with pytest.raises(S.SadiError) as ei:
+                s.sadi_step_noalloc(*args, 3)
+            assert ei.value.status == S.SADI_EINVAL and "shorter" in str(ei.value)
+        s.sadi_step_noalloc(u[0].data_ptr(), u[1].data_ptr(), exact, 3)   # exactly N*N doubles: accepted
+        st.synchronize()
+        assert bool(torch.isfinite(T).all())
