@@ -72,7 +72,10 @@ typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2 } sadi_g
  *   s = kappa tau^2 / (2 h^alpha): near-FP32 while s a_0 is small (a_0 the
  *   first 1D weight), visibly coarser once E is O(1) (s a_0 of order 1 or
  *   more); prefer SADI_PREC_FP32 there. */
-typedef enum { SADI_PREC_FP64 = 0, SADI_PREC_FP32 = 1, SADI_PREC_FP32_DENSE = 2 } sadi_prec;
+typedef enum {
+  SADI_PREC_AUTO = -1,    /* sadi_batch_create only: the autotuner's choice per N */
+  SADI_PREC_FP64 = 0, SADI_PREC_FP32 = 1, SADI_PREC_FP32_DENSE = 2
+} sadi_prec;
 
 /* Create a context for N interior points per direction, fractional order
  * alpha in (1, 2] (2 = the classical wave equation limit; the paper states
@@ -136,6 +139,52 @@ sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
  * queued on the other contexts' streams and before their later work (event
  * waits).  Results are identical to stepping each context alone. */
 sadi_status sadi_batch_step(sadi_ctx **ctxs, int count, int nsteps);
+
+/* A batch of independent instances behind one handle (the batched pattern:
+ * many problems of uneven N, alpha, kappa, tau advanced together; the paper
+ * solves one problem at a time, Sec. 6).  Member k is the problem
+ * sadi_create(N[k], alpha[k], kappa[k], tau[k], domains + 2k) would set up
+ * (domains NULL: every member on (-1, 1)^2), all with nonlinearity g, and
+ * the step form prec, or with prec = SADI_PREC_AUTO the form and tiles that
+ * sadi_autotune picks per N (FP32 or FP32_DENSE).  All members share one
+ * stream owned by the batch (sadi_batch_set_stream replaces it; NULL
+ * restores it).  On failure *out is NULL, nothing is left allocated, and
+ * sadi_batch_last_error(NULL) says which member failed and why. */
+typedef struct sadi_batch sadi_batch;
+sadi_status sadi_batch_create(int count, const int *N, const double *alpha, const double *kappa,
+                              const double *tau, const double *domains, int g, int prec,
+                              sadi_batch **out);
+
+/* Initial data of member k (0 <= k < count), as sadi_set_initial.  Members
+ * may be (re)initialised at any time between runs; a member at n = 0 takes
+ * the n = 0 step in the next sadi_batch_run. */
+sadi_status sadi_batch_set_initial(sadi_batch *batch, int k, const double *phi1, const double *phi2);
+
+/* Advance every member by nsteps >= 0 steps (asynchronous on the batch's
+ * stream): batched launches as sadi_batch_step makes them (one launch per
+ * kernel for each group of equal FFT length <= 1024), and once every member
+ * is past its n = 0 step, replays of a CUDA graph of one batched step
+ * (captured on first use; FP32 forms without source terms or profiling --
+ * otherwise the steps are launched directly).  Results are identical to
+ * stepping each member alone.  SADI_ESTATE if a member has no initial data. */
+sadi_status sadi_batch_run(sadi_batch *batch, int nsteps);
+
+/* u^n of member k to the host (N_k * N_k doubles) and its step count, as
+ * sadi_get (synchronous; the member's watchdog and wait errors surface
+ * here). */
+sadi_status sadi_batch_get(sadi_batch *batch, int k, double *u_out, long long *n_out);
+
+/* The context of member k (owned by the batch: do not destroy it), for the
+ * per-context calls (sadi_get_async, sadi_set_source, sadi_profile, ...).
+ * The batch captures its step graph anew after this call. */
+sadi_status sadi_batch_member(sadi_batch *batch, int k, sadi_ctx **ctx);
+sadi_status sadi_batch_count(const sadi_batch *batch, int *count);
+sadi_status sadi_batch_set_stream(sadi_batch *batch, void *cuda_stream);
+/* Last error of the batch ("" if none); NULL: the last failed
+ * sadi_batch_create on this thread. */
+const char *sadi_batch_last_error(const sadi_batch *batch);
+/* Waits for the batch's stream, then frees every member and the batch. */
+void sadi_batch_destroy(sadi_batch *batch);
 
 /* Checkpoint and resume (no paper counterpart).  sadi_save_state writes the
  * step state of an initialised context into buf (host memory of *bytes
@@ -273,6 +322,38 @@ sadi_status sadi_profile(sadi_ctx *ctx, int enable);
  * in *nsteps (may be NULL) the number of steps they cover; resets the
  * accumulators. */
 sadi_status sadi_get_phase_times(sadi_ctx *ctx, double ms[4], long long *nsteps);
+
+/* State watchdog (failure detection; no paper counterpart).  After every
+ * stepping call (sadi_step, sadi_batch_step, sadi_graph_launch,
+ * sadi_batch_run) in which the step counter n reaches or passes a multiple
+ * of `every`, one small kernel on the context's stream sums u_ij^2 of the
+ * state u^n over the grid in double (FP32 forms: the float hi part of u^n)
+ * and latches a flag if the sum is not finite (a NaN or an infinity in u^n,
+ * or a blow-up past ~1e154).  The next synchronising call (sadi_get,
+ * sadi_wait) then returns SADI_ENONFINITE, naming the step of the first
+ * check that saw it, and the context needs new data (sadi_set_initial or
+ * sadi_load_state, which clear the flag) before it steps again.
+ * every >= 0; 0 switches the checks off; a new context checks every 100
+ * steps.  The checks only read the state: results are unchanged. */
+sadi_status sadi_set_watchdog(sadi_ctx *ctx, int every);
+
+/* Result of the last watchdog check of ctx (waits for its stream): the
+ * discrete L2 norm h (sum_ij u_ij^2)^(1/2) of u^n (Sec. 4 norm) in *l2norm
+ * and its step n in *step (0 and 0 before the first check); either pointer
+ * may be NULL. */
+sadi_status sadi_get_watchdog(sadi_ctx *ctx, double *l2norm, long long *step);
+
+/* Test hook for the bounded device waits of the dense-inverse form (no paper
+ * counterpart).  The next step of ctx (SADI_PREC_FP32_DENSE only, else
+ * SADI_EUNSUPPORTED) launches its sweep GEMM with every bounded wait limited
+ * to wait_limit_ns (1e5 .. 1e9, else SADI_EINVAL) instead of 1 s, and with
+ * its y-sweep tiles waiting for an x-sweep panel count that no tile reaches.
+ * Those waits run out: the kernel's CTAs stop, wait (bounded) for their own
+ * copies and tensor-core work in flight, free their tensor memory and
+ * return, and the next sadi_get or sadi_wait returns SADI_ETIMEOUT; the
+ * context is then unusable (SADI_ESTATE), other contexts and the CUDA
+ * context are not affected.  One-shot: the hook applies to one step. */
+sadi_status sadi_debug_expire_waits(sadi_ctx *ctx, long long wait_limit_ns);
 
 /* Last error message of ctx ("" if none).  ctx may be NULL: then the message
  * of the last failed sadi_create on this thread is returned. */

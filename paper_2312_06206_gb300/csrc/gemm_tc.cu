@@ -33,8 +33,8 @@
 // problems precede those of the later ones in every CTA's walk, and such a
 // launch is cooperative, so every counter is raised by a resident CTA that
 // never waits itself.
-// Every mbarrier and counter wait is bounded (about 1 s of %globaltimer); on
-// expiry the CTA sets *err, the other roles stop at their next wait, the
+// Every mbarrier and counter wait is bounded (1 s of %globaltimer, or the
+// launch's TcBatch::wait_ns); on expiry the CTA sets *err, the other roles stop at their next wait, the
 // producer waits (bounded) for the copies it issued, all MMAs are waited for,
 // and the tensor memory is freed before the CTA returns.
 #include <cuda.h>
@@ -68,7 +68,7 @@ struct TileCfg {
   static constexpr int STAGES = BN == 256 ? 2 : 3;
   static constexpr int TMEM_COLS = BN;
 };
-constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull;   // default limit of every bounded wait
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
@@ -92,12 +92,12 @@ __device__ __forceinline__ uint64_t gtimer() {
   asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
   return t;
 }
-// Wait until the phase with the given parity has completed; false after the limit.
-__device__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+// Wait until the phase with the given parity has completed; false after limit ns.
+__device__ bool mbar_wait(uint32_t bar, uint32_t parity, uint64_t limit) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (!mbar_try(bar, parity))
-    if (gtimer() - t0 > WAIT_LIMIT_NS) return false;
+    if (gtimer() - t0 > limit) return false;
   return true;
 }
 
@@ -292,12 +292,12 @@ __device__ __forceinline__ void prefetch_epilogue(const TcEpi& e, int row, int c
 
 // Wait for a phase like mbar_wait, but give up at once when another role of
 // the CTA has aborted, and abort the CTA when the time limit runs out.
-__device__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag) {
+__device__ bool wait_or_abort(uint32_t bar, uint32_t parity, volatile int* abort_flag, uint64_t limit) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtimer();
   while (!mbar_try(bar, parity)) {
     if (*abort_flag) return false;
-    if (gtimer() - t0 > WAIT_LIMIT_NS) {
+    if (gtimer() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -312,12 +312,12 @@ __device__ __forceinline__ int ld_acquire(const int* p) {
   asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
   return v;
 }
-__device__ bool wait_count(const int* cnt, int need, volatile int* abort_flag) {
+__device__ bool wait_count(const int* cnt, int need, volatile int* abort_flag, uint64_t limit) {
   if (ld_acquire(cnt) >= need) return true;
   const uint64_t t0 = gtimer();
   while (ld_acquire(cnt) < need) {
     if (*abort_flag) return false;
-    if (gtimer() - t0 > WAIT_LIMIT_NS) {
+    if (gtimer() - t0 > limit) {
       *abort_flag = 1;
       return false;
     }
@@ -327,9 +327,9 @@ __device__ bool wait_count(const int* cnt, int need, volatile int* abort_flag) {
 }
 // Wait for every 128-column panel of the columns n0 .. n0 + BN - 1.
 template <int BN>
-__device__ bool wait_panels(const TcInst& in, int n0, volatile int* abort_flag) {
+__device__ bool wait_panels(const TcInst& in, int n0, volatile int* abort_flag, uint64_t limit) {
   for (int p = n0 / BOX; p < (n0 + BN) / BOX; ++p)
-    if (!wait_count(in.dep_wait + p, in.dep_need, abort_flag)) return false;
+    if (!wait_count(in.dep_wait + p, in.dep_need, abort_flag, limit)) return false;
   return true;
 }
 
@@ -394,6 +394,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
   const uint32_t tfull0 = su32(bars + 2 * STAGES), tempty0 = su32(bars + 2 * STAGES + 2);
   const uint32_t mdone = su32(bars + 2 * STAGES + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint64_t limit = bt.wait_ns ? bt.wait_ns : WAIT_LIMIT_NS;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -456,14 +457,14 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
         if (in.dep_wait) {
           // the B rows are written by an earlier problem of this launch with
           // generic stores: acquire them, then order them before the copies
-          if (!wait_panels<BN>(in, n0, abort_flag)) break;
+          if (!wait_panels<BN>(in, n0, abort_flag, limit)) break;
           asm volatile("fence.proxy.async.global;" ::: "memory");
         }
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
           const uint32_t use = (uint32_t)(it / STAGES);
           if constexpr (PF_LEAD > 0) prefetch_upto(it + STAGES + PF_LEAD);
-          if (it >= STAGES && !wait_or_abort(empty0 + 8 * s, (use - 1) & 1u, abort_flag)) break;
+          if (it >= STAGES && !wait_or_abort(empty0 + 8 * s, (use - 1) & 1u, abort_flag, limit)) break;
           uint8_t* st = base + s * STAGE_BYTES;
           mbar_expect_tx(full0 + 8 * s, STAGE_BYTES);
           tma_load_2d(su32(st), &in.a_hi, kb * BK, m0, full0 + 8 * s);
@@ -481,7 +482,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
       if (*abort_flag) {
         // the copies issued last must land before the CTA may exit
         for (int j = (it > STAGES ? it - STAGES : 0); j < it; ++j)
-          (void)mbar_wait(full0 + 8 * (j % STAGES), (uint32_t)(j / STAGES) & 1u);
+          (void)mbar_wait(full0 + 8 * (j % STAGES), (uint32_t)(j / STAGES) & 1u, limit);
       }
     }
   } else if (warp == 1) {
@@ -495,13 +496,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
         const int nk = bt.in[z].K / BK;
         const int b = tl & 1;
         const uint32_t ub = (uint32_t)(tl >> 1);
-        if (tl >= 2 && !wait_or_abort(tempty0 + 8 * b, (ub - 1) & 1u, abort_flag)) break;
+        if (tl >= 2 && !wait_or_abort(tempty0 + 8 * b, (ub - 1) & 1u, abort_flag, limit)) break;
         tc_fence_after();
         const uint32_t acc = tmem + (uint32_t)(b * TMEM_COLS);
         bool ok = true;
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const int s = it % STAGES;
-          if (!wait_or_abort(full0 + 8 * s, (uint32_t)(it / STAGES) & 1u, abort_flag)) {
+          if (!wait_or_abort(full0 + 8 * s, (uint32_t)(it / STAGES) & 1u, abort_flag, limit)) {
             ok = false;
             break;
           }
@@ -524,7 +525,7 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
       }
       // every MMA issued must have finished before the tensor memory is freed
       mma_commit(mdone);
-      (void)mbar_wait(mdone, 0);
+      (void)mbar_wait(mdone, 0, limit);
     }
   } else {
     // ---- epilogue warps: TMEM lane quarter = warp % 4, column half ----
@@ -538,13 +539,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
       const uint32_t ub = (uint32_t)(tl >> 1);
       const TcInst& in = bt.in[z];
       prefetch_epilogue<BN / 2>(in.e, m0 + quarter * 32 + lane, n0 + half * (BN / 2));
-      if (!wait_or_abort(tfull0 + 8 * b, ub & 1u, abort_flag) || *abort_flag) break;
+      if (!wait_or_abort(tfull0 + 8 * b, ub & 1u, abort_flag, limit) || *abort_flag) break;
       tc_fence_after();
       if (in.dep_wait) {
         // the epilogue reads W of the same panels (already complete: the
         // producer waited for them before this tile's loads)
         bool ok = true;
-        if (lane == 0) ok = wait_panels<BN>(in, n0, abort_flag);
+        if (lane == 0) ok = wait_panels<BN>(in, n0, abort_flag, limit);
         if (!__shfl_sync(0xffffffffu, ok ? 1 : 0, 0)) break;
       }
       const uint32_t acc = tmem + (uint32_t)(b * TMEM_COLS) + ((uint32_t)(quarter * 32) << 16);

@@ -34,6 +34,7 @@ sadi_status graph_check(sadi_ctx* const* ctxs, int count, bool launching) {
     if (c->n < 1) return fail(c, SADI_ESTATE, "take the n = 0 step before capturing or launching a graph");
     if (c->F) return fail(c, SADI_EUNSUPPORTED, "a source term changes every step; it cannot be replayed");
     if (c->profiling) return fail(c, SADI_ESTATE, "disable sadi_profile before capturing a graph");
+    if (c->dbg_expire_ns) return fail(c, SADI_ESTATE, "a sadi_debug_expire_waits step is pending; step it first");
     if (c->stream != s0) return fail(c, SADI_EINVAL, "all contexts of a graph must share one stream");
     if (!launching)
       for (int j = 0; j < k; ++j)
@@ -100,7 +101,12 @@ sadi_status sadi_graph_launch(sadi_graph* g, int reps) {
       return SADI_ECUDA;
     }
   }
-  for (sadi_ctx* c : g->ctxs) c->n += (long long)g->nsteps * reps;
+  for (sadi_ctx* c : g->ctxs) {
+    const long long n_before = c->n;
+    c->n += (long long)g->nsteps * reps;
+    st = watchdog_after(c, n_before, g->stream);
+    if (st != SADI_OK) return st;
+  }
   return SADI_OK;
 }
 

@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 
 #include <cmath>
+#include <cstddef>
 #include <cstdio>
 #include <cstring>
 #include <array>
@@ -55,7 +56,7 @@ void free_all(sadi_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   conv3_free(&c->c3);
-  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->tcdep, c->Chi, c->Clo};
+  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->tcdep, c->Chi, c->Clo, c->wd};
   for (void* p : dense)
     if (p) cudaFree(p);
   for (auto& a : c->ev_pool)
@@ -251,6 +252,7 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
       {(void**)&c->rlreg, sizeof(float) * nlpb},
       {(void**)&c->rlamc, sizeof(float2) * Np},
       {(void**)&c->rlams, sizeof(float2) * Np},
+      {(void**)&c->wd, sizeof(WdState)},
   };
   for (auto& al : allocs) {
     e = cudaMalloc(al.p, al.bytes);
@@ -260,6 +262,7 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
     }
   }
   cudaStream_t st = c->stream;
+  if ((e = cudaMemsetAsync(c->wd, 0, sizeof(WdState), st))) return bail(cuda_fail(c, e, "watchdog record"));
   if ((e = launch_twiddles(c->tw64, c->tw32, P, st))) return bail(cuda_fail(c, e, "twiddles"));
   if ((e = launch_stage_twiddles(c->stw64, c->stw32, g.logNp, st))) return bail(cuda_fail(c, e, "stage twiddles"));
   if ((e = launch_riesz1d(c->a1, Np, alpha, st))) return bail(cuda_fail(c, e, "riesz weights"));
@@ -391,6 +394,7 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   } else {
     CK(cudaMemsetAsync(c->phi2, 0, nn * esize(c->prec), st), "phi2 zero");
   }
+  CK(cudaMemsetAsync(c->wd, 0, sizeof(WdState), st), "watchdog record");
   CK(cudaStreamSynchronize(st), "set_initial");
   c->n = 0;
   c->initialized = true;
@@ -537,6 +541,7 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
   for (int k0 = 0; e == cudaSuccess && k0 < count; k0 += kPer) {
     const int m = count - k0 < kPer ? count - k0 : kPer;
     tb.count = 2 * m;
+    tb.wait_ns = 0;
     for (int k = 0; k < m && e == cudaSuccess; ++k) {
       const sadi_ctx* ck = cs[k0 + k];
       e = cudaMemsetAsync(ck->tcdep, 0, sizeof(int) * (ck->npad / kTcBox), st_);
@@ -567,9 +572,16 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
           in.dep_wait = ck->tcdep;
           in.dep_need = ck->tc_x->tiles_m;   // x-sweep tiles per column panel
           in.dep_signal = nullptr;
+          if (ck->dbg_expire_ns > 0) {
+            // sadi_debug_expire_waits: a panel count that no x-sweep tile
+            // reaches, and a short limit for every wait of the launch
+            in.dep_need = ck->tc_x->tiles_m + 1;
+            tb.wait_ns = (unsigned long long)ck->dbg_expire_ns;
+          }
         }
       }
     }
+    for (int k = 0; k < m; ++k) cs[k0 + k]->dbg_expire_ns = 0;
     if (e == cudaSuccess) e = launch_tc_gemm(tb, cs[k0]->tcerr, st_);
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[4], st_);
@@ -613,6 +625,7 @@ sadi_status sadi_step(sadi_ctx* c, int nsteps) {
   sadi_status st = check_steppable(c);
   if (st != SADI_OK) return st;
   if (nsteps < 0) return fail(c, SADI_EINVAL, "nsteps must be >= 0");
+  const long long n_before = c->n;
   for (int it = 0; it < nsteps; ++it) {
     if (is_dense(c)) {
       st = step_dense_group(&c, 1, c->stream);
@@ -625,7 +638,7 @@ sadi_status sadi_step(sadi_ctx* c, int nsteps) {
     }
     if (st != SADI_OK) return st;
   }
-  return SADI_OK;
+  return watchdog_after(c, n_before, c->stream);
 }
 
 }  // extern "C"
@@ -704,9 +717,32 @@ sadi_status zero_initial(sadi_ctx* c) {
   float* fb[] = {c->ulo, c->Chi, c->Clo};
   for (float* b : fb)
     if (b) CK(cudaMemsetAsync(b, 0, nn * sizeof(float), st), "zero state");
+  CK(cudaMemsetAsync(c->wd, 0, sizeof(WdState), st), "watchdog record");
   c->cur = 0;
   c->n = 0;
   c->initialized = true;
+  return SADI_OK;
+}
+
+sadi_status watchdog_after(sadi_ctx* c, long long n_before, cudaStream_t st) {
+  if (c->wd_every <= 0 || c->n / c->wd_every == n_before / c->wd_every) return SADI_OK;
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  const bool f64 = c->prec == SADI_PREC_FP64;
+  // FP64: u^n; FP32 forms: the hi part of the double-float pair, finite
+  // exactly when u^n is
+  CK(launch_watchdog(f64 ? c->ubuf[c->cur] : c->ubuf[0], f64, nn, c->wd, c->n, st), "watchdog");
+  return SADI_OK;
+}
+
+sadi_status check_watchdog(sadi_ctx* c) {
+  WdState h;
+  CK(cudaMemcpy(&h, c->wd, offsetof(WdState, ticket), cudaMemcpyDeviceToHost), "watchdog record");
+  if (h.nonfinite) {
+    c->initialized = false;
+    return fail(c, SADI_ENONFINITE,
+                "the watchdog found a non-finite value in u^n at step " + std::to_string(h.nonfinite_step) +
+                    "; set new initial data (sadi_set_initial or sadi_load_state) to continue");
+  }
   return SADI_OK;
 }
 
@@ -723,7 +759,14 @@ sadi_status sadi_batch_step(sadi_ctx** ctxs, int count, int nsteps) {
     sadi_status st = check_steppable(ctxs[k]);
     if (st != SADI_OK) return st;
   }
-  return batch_issue(ctxs, count, nsteps);
+  std::vector<long long> n_before(count);
+  for (int k = 0; k < count; ++k) n_before[k] = ctxs[k]->n;
+  sadi_status st = batch_issue(ctxs, count, nsteps);
+  for (int k = 0; k < count && st == SADI_OK; ++k) {
+    // on the stream of the context, after the batch (batch_issue ordered it)
+    st = watchdog_after(ctxs[k], n_before[k], ctxs[k]->stream);
+  }
+  return st;
 }
 
 sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {
@@ -741,7 +784,8 @@ sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {
     CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   }
   CK(cudaStreamSynchronize(st), "sadi_get");
-  const sadi_status es = check_gemm_flag(c);
+  sadi_status es = check_gemm_flag(c);
+  if (es == SADI_OK) es = check_watchdog(c);
   if (es != SADI_OK) return es;
   if (n_out) *n_out = c->n;
   return SADI_OK;
@@ -779,7 +823,8 @@ sadi_status sadi_wait(sadi_ctx* c) {
   if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
   CK(cudaStreamSynchronize(c->stream), "sadi_wait");
   if (c->copy_stream) CK(cudaStreamSynchronize(c->copy_stream), "sadi_wait (copies)");
-  return check_gemm_flag(c);
+  const sadi_status es = check_gemm_flag(c);
+  return es != SADI_OK || !c->initialized ? es : check_watchdog(c);
 }
 
 sadi_status sadi_get_device(sadi_ctx* c, void* dst, int dtype) {
@@ -899,6 +944,34 @@ sadi_status sadi_get_phase_times(sadi_ctx* c, double ms[4], long long* nsteps) {
   return SADI_OK;
 }
 
+sadi_status sadi_set_watchdog(sadi_ctx* c, int every) {
+  if (!c) return SADI_EINVAL;
+  if (every < 0) return fail(c, SADI_EINVAL, "sadi_set_watchdog: every must be >= 0");
+  c->wd_every = every;
+  return SADI_OK;
+}
+
+sadi_status sadi_get_watchdog(sadi_ctx* c, double* l2norm, long long* step) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  CK(cudaStreamSynchronize(c->stream), "sadi_get_watchdog");
+  WdState h;
+  CK(cudaMemcpy(&h, c->wd, offsetof(WdState, ticket), cudaMemcpyDeviceToHost), "watchdog record");
+  if (l2norm) *l2norm = c->h * std::sqrt(h.sumsq);
+  if (step) *step = h.step;
+  return SADI_OK;
+}
+
+sadi_status sadi_debug_expire_waits(sadi_ctx* c, long long wait_limit_ns) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (!is_dense(c)) return fail(c, SADI_EUNSUPPORTED, "sadi_debug_expire_waits: SADI_PREC_FP32_DENSE contexts only");
+  if (wait_limit_ns < 100000 || wait_limit_ns > 1000000000)
+    return fail(c, SADI_EINVAL, "sadi_debug_expire_waits: wait_limit_ns must be in [1e5, 1e9]");
+  c->dbg_expire_ns = wait_limit_ns;
+  return SADI_OK;
+}
+
 const char* sadi_last_error(const sadi_ctx* c) {
   if (!c) return g_create_err.c_str();
   return c->err.c_str();
@@ -917,7 +990,26 @@ void sadi_destroy(sadi_ctx* c) {
 
 namespace {
 
-sadi_status check_device_buffer(sadi_ctx* c, const void* p, const char* name) {
+// cuMemGetAddressRange of the driver API, looked up once through the runtime
+// (the library does not link libcuda directly)
+using AddressRangeFn = CUresult (*)(CUdeviceptr*, size_t*, CUdeviceptr);
+AddressRangeFn address_range_fn() {
+  static AddressRangeFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuMemGetAddressRange", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      return static_cast<AddressRangeFn>(nullptr);
+    }
+    return reinterpret_cast<AddressRangeFn>(f);
+  }();
+  return fn;
+}
+
+// p must be device (or managed) memory on the context's device, and the
+// allocation holding p must extend over all `bytes` bytes from p.
+sadi_status check_device_buffer(sadi_ctx* c, const void* p, size_t bytes, const char* name) {
   cudaPointerAttributes a{};
   const cudaError_t e = cudaPointerGetAttributes(&a, p);
   if (e != cudaSuccess) {
@@ -926,6 +1018,18 @@ sadi_status check_device_buffer(sadi_ctx* c, const void* p, const char* name) {
   }
   if ((a.type != cudaMemoryTypeDevice && a.type != cudaMemoryTypeManaged) || a.device != c->device)
     return fail(c, SADI_EINVAL, std::string(name) + " must be device memory on the context's device");
+  AddressRangeFn range = address_range_fn();
+  if (!range) return fail(c, SADI_EINVAL, std::string(name) + ": cannot query the size of its allocation");
+  CUdeviceptr base = 0;
+  size_t size = 0;
+  const CUdeviceptr q = reinterpret_cast<CUdeviceptr>(p);
+  if (range(&base, &size, q) != CUDA_SUCCESS)
+    return fail(c, SADI_EINVAL, std::string(name) + ": cannot query the size of its allocation");
+  if (q < base || q - base > size || size - (q - base) < bytes)
+    return fail(c, SADI_EINVAL,
+                std::string(name) + " is shorter than N*N doubles (" + std::to_string(bytes) + " bytes needed, " +
+                    std::to_string(base + size > q ? size_t(base + size - q) : size_t(0)) +
+                    " left in its allocation)");
   return SADI_OK;
 }
 
@@ -961,12 +1065,20 @@ extern "C" sadi_status sadi_step_noalloc(sadi_ctx* c, const double* u_prev, cons
   int dev = -1;
   CK(cudaGetDevice(&dev), "cudaGetDevice");
   if (dev != c->device) return fail(c, SADI_EINVAL, "sadi_step_noalloc: the context's device must be current");
-  sadi_status st = check_device_buffer(c, u_prev, "u_prev");
-  if (st == SADI_OK) st = check_device_buffer(c, u_cur, "u_cur");
-  if (st == SADI_OK) st = check_device_buffer(c, u_next, "u_next");
+  sadi_status st = check_device_buffer(c, u_prev, ub, "u_prev");
+  if (st == SADI_OK) st = check_device_buffer(c, u_cur, ub, "u_cur");
+  if (st == SADI_OK) st = check_device_buffer(c, u_next, ub, "u_next");
   if (st != SADI_OK) return st;
   void* scratch = nullptr;
-  CK(noalloc_scratch_address(dev, &scratch), "scratch address");
+  // a failed look-up (e.g. a first call made during a stream capture) is
+  // reported without marking the context unusable; a later call retries it
+  const cudaError_t se = noalloc_scratch_address(dev, &scratch);
+  if (se != cudaSuccess) {
+    cudaGetLastError();
+    return fail(c, SADI_ESTATE,
+                std::string("sadi_step_noalloc: looking up the scratch array's device address failed: ") +
+                    cudaGetErrorName(se) + " (make the first call on a device outside any stream capture)");
+  }
   RhsParams rp{c->tau, c->tau * c->tau, c->gkind, 0, c->F,
                c->F ? std::cos(c->f_omega * (double)n * c->tau + c->f_phase) : 0.0};
   StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
@@ -1076,6 +1188,7 @@ extern "C" sadi_status sadi_load_state(sadi_ctx* c, const void* buf, size_t byte
   const char* p = static_cast<const char*>(buf) + sizeof h;
   for (int k = 0; k < na; ++k, p += nn * es)
     CK(cudaMemcpyAsync(arr[k], p, nn * es, cudaMemcpyHostToDevice, c->stream), "copy state");
+  CK(cudaMemsetAsync(c->wd, 0, sizeof(WdState), c->stream), "watchdog record");
   CK(cudaStreamSynchronize(c->stream), "sadi_load_state");
   c->n = h.n;
   c->initialized = true;

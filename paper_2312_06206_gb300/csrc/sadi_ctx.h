@@ -12,6 +12,9 @@
 #include "../../include/sadi.h"
 #include "sadi_internal.h"
 
+// steps between watchdog checks of a new context
+constexpr int kWatchdogDefaultEvery = 100;
+
 struct sadi_ctx {
   using Geom = sadi::Geom;
   using Tiles = sadi::Tiles;
@@ -86,10 +89,15 @@ struct sadi_ctx {
   int npad = 0;
   unsigned short *Eh = nullptr, *El = nullptr, *Bh = nullptr, *Bl = nullptr, *WTh = nullptr, *WTl = nullptr;
   int* tcerr = nullptr;             // device flag: a bounded wait in a GEMM ran out
+  long long dbg_expire_ns = 0;      // sadi_debug_expire_waits: next dense step's waits run out (0: off)
   int* tcdep = nullptr;             // per 128-column panel: x-sweep tiles stored (zeroed each step)
   sadi::Conv3 c3;                   // FP32 forms, N' = 2048 .. 8192: three-pass column convolution
   std::unique_ptr<TcInst> tc_x, tc_y;
   std::string tune_log;             // choice of sadi_autotune
+  // state watchdog: after a stepping call in which n reaches a multiple of
+  // wd_every (0: off), sum u^2 on the device and latch non-finite results
+  int wd_every = kWatchdogDefaultEvery;
+  sadi::WdState* wd = nullptr;
 };
 
 namespace sadi_api {
@@ -114,5 +122,11 @@ sadi_status batch_issue(sadi_ctx** ctxs, int count, int nsteps);
 // zero state (u, increment, remainder, phi2) and n = 0: a context ready to
 // step, for timing runs that need no data
 sadi_status zero_initial(sadi_ctx* c);
+// queue a watchdog check of c's state if n crossed a multiple of its period
+// since n_before (the value before the stepping call)
+sadi_status watchdog_after(sadi_ctx* c, long long n_before, cudaStream_t st);
+// after the stream has been synchronised: SADI_ENONFINITE (and the state
+// marked as needing sadi_set_initial) if a check found a non-finite value
+sadi_status check_watchdog(sadi_ctx* c);
 
 }  // namespace sadi_api

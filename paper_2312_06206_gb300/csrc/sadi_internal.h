@@ -242,6 +242,7 @@ struct TcInst {
 // passed by value as a __grid_constant__ kernel parameter (about 10 KB)
 struct TcBatch {
   int count;
+  unsigned long long wait_ns;   // limit of every bounded wait of the launch (0: the default, 1 s)
   TcInst in[kTcMaxBatch];
 };
 // tensor map of a rows x kdim BF16 matrix (row-major) with box box_rows x 64
@@ -258,6 +259,22 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st);
 // FP32 rows x cols (ld src_ld) -> zero-padded prow x pcol BF16 hi / lo
 cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,
                              cudaStream_t st);
+
+// ---- state watchdog, watchdog.cu ----------------------------------------------
+// Device record of one context's watchdog: the last check's sum of u_ij^2
+// (double) and its step, and a latched non-finite flag with the step of the
+// first check that saw it (cleared by the host when the state is re-set).
+constexpr int kWdMaxBlocks = 304;
+struct WdState {
+  double sumsq;
+  long long step;
+  int nonfinite;
+  long long nonfinite_step;
+  unsigned int ticket;              // blocks finished in the running launch (0 between launches)
+  double partial[kWdMaxBlocks];
+};
+// sum of u[i]^2 over n elements (double or float) into wd, on stream st
+cudaError_t launch_watchdog(const void* u, bool fp64, size_t n, WdState* wd, long long step, cudaStream_t st);
 
 // ---- fixed scratch of sadi_step_noalloc, noalloc_scratch.cu ------------------
 constexpr size_t kNoallocScratchBytes = size_t(32) << 20;

@@ -21,6 +21,7 @@ STATUS_NAMES = {0: "SADI_OK", 1: "SADI_EINVAL", 2: "SADI_ENOMEM", 3: "SADI_ECUDA
                 5: "SADI_ESTATE", 6: "SADI_ETIMEOUT", 7: "SADI_ENONFINITE", 8: "SADI_EUNSUPPORTED"}
 SADI_G_ZERO, SADI_G_NEG_CUBE, SADI_G_NEG_SIN = 0, 1, 2
 SADI_PREC_FP64, SADI_PREC_FP32, SADI_PREC_FP32_DENSE = 0, 1, 2
+SADI_PREC_AUTO = -1
 
 # every symbol include/sadi.h declares, with its ctypes signature
 _SIGS = {
@@ -56,6 +57,19 @@ _SIGS = {
     "sadi_autotune": (C.c_int, [C.POINTER(C.c_void_p), C.c_int, C.c_int, C.c_int]),
     "sadi_tuning_log": (C.c_char_p, [C.c_void_p]),
     "sadi_step_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong]),
+    "sadi_set_watchdog": (C.c_int, [C.c_void_p, C.c_int]),
+    "sadi_get_watchdog": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
+    "sadi_debug_expire_waits": (C.c_int, [C.c_void_p, C.c_longlong]),
+    "sadi_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_int, C.c_int, C.POINTER(C.c_void_p)]),
+    "sadi_batch_set_initial": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p]),
+    "sadi_batch_run": (C.c_int, [C.c_void_p, C.c_int]),
+    "sadi_batch_get": (C.c_int, [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_longlong)]),
+    "sadi_batch_member": (C.c_int, [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]),
+    "sadi_batch_count": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
+    "sadi_batch_set_stream": (C.c_int, [C.c_void_p, C.c_void_p]),
+    "sadi_batch_last_error": (C.c_char_p, [C.c_void_p]),
+    "sadi_batch_destroy": (None, [C.c_void_p]),
 }
 
 
@@ -174,6 +188,86 @@ def sadi_batch_step(instances, nsteps: int = 1):
         raise SadiError(st, "; ".join(m for m in msgs if m) or "invalid batch")
 
 
+class SadiBatch:
+    """Independent instances behind one sadi_batch* handle (sadi_batch_create)."""
+
+    def __init__(self, Ns, alphas, kappas, taus, domains=None, g: int = SADI_G_ZERO, prec: int = SADI_PREC_AUTO):
+        n = len(Ns)
+        self.Ns = [int(x) for x in Ns]
+        arr_i = (C.c_int * n)(*self.Ns)
+        arr = [(C.c_double * n)(*[float(x) for x in v]) for v in (alphas, kappas, taus)]
+        dom = None if domains is None else (C.c_double * (2 * n))(*[float(x) for d in domains for x in d])
+        out = C.c_void_p()
+        st = lib().sadi_batch_create(n, arr_i, arr[0], arr[1], arr[2], dom, int(g), int(prec), C.byref(out))
+        if st != SADI_OK:
+            msg = lib().sadi_batch_last_error(None)
+            raise SadiError(st, msg.decode() if msg else "sadi_batch_create failed")
+        self.handle = out.value
+
+    def _check(self, st):
+        if st != SADI_OK:
+            msg = lib().sadi_batch_last_error(self.handle)
+            raise SadiError(st, msg.decode() if msg else "")
+
+    def _n_of(self, k, arr=None):
+        # an out-of-range k goes to the library, which rejects it
+        if 0 <= k < len(self.Ns):
+            return self.Ns[k]
+        return np.asarray(arr).shape[0] if arr is not None else 1
+
+    def sadi_batch_set_initial(self, k: int, phi1, phi2=None):
+        N = self._n_of(k, phi1)
+        p1 = _f64(phi1, N)
+        p2 = None if phi2 is None else _f64(phi2, N)
+        self._check(lib().sadi_batch_set_initial(self.handle, int(k), p1.ctypes.data,
+                                                 None if p2 is None else p2.ctypes.data))
+
+    def sadi_batch_run(self, nsteps: int = 1):
+        self._check(lib().sadi_batch_run(self.handle, int(nsteps)))
+
+    def sadi_batch_get(self, k: int):
+        N = self._n_of(k)
+        out = np.empty((N, N), dtype=np.float64)
+        n = C.c_longlong()
+        self._check(lib().sadi_batch_get(self.handle, int(k), out.ctypes.data, C.byref(n)))
+        return out, n.value
+
+    def sadi_batch_member(self, k: int) -> int:
+        out = C.c_void_p()
+        self._check(lib().sadi_batch_member(self.handle, int(k), C.byref(out)))
+        return out.value
+
+    def sadi_batch_count(self) -> int:
+        c = C.c_int()
+        self._check(lib().sadi_batch_count(self.handle, C.byref(c)))
+        return c.value
+
+    def sadi_batch_set_stream(self, stream_handle):
+        self._check(lib().sadi_batch_set_stream(self.handle, C.c_void_p(stream_handle or 0)))
+
+    def sadi_batch_destroy(self):
+        if getattr(self, "handle", None):
+            lib().sadi_batch_destroy(self.handle)
+            self.handle = None
+
+    set_initial = sadi_batch_set_initial
+    run = sadi_batch_run
+    get = sadi_batch_get
+    close = sadi_batch_destroy
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.sadi_batch_destroy()
+
+    def __del__(self):
+        try:
+            self.sadi_batch_destroy()
+        except Exception:
+            pass
+
+
 class Sadi:
     """One S-ADI instance (wraps a sadi_ctx*)."""
 
@@ -265,6 +359,18 @@ class Sadi:
         """One step on caller-owned device buffers (N*N doubles each); no allocation."""
         _check(lib().sadi_step_noalloc(self.ctx, C.c_void_p(u_prev_ptr), C.c_void_p(u_cur_ptr),
                                        C.c_void_p(u_next_ptr), int(n)), self.ctx)
+
+    def sadi_set_watchdog(self, every: int):
+        _check(lib().sadi_set_watchdog(self.ctx, int(every)), self.ctx)
+
+    def sadi_get_watchdog(self):
+        """(discrete L2 norm of u^n at the last check, its step n)."""
+        v, n = C.c_double(), C.c_longlong()
+        _check(lib().sadi_get_watchdog(self.ctx, C.byref(v), C.byref(n)), self.ctx)
+        return v.value, n.value
+
+    def sadi_debug_expire_waits(self, wait_limit_ns: int):
+        _check(lib().sadi_debug_expire_waits(self.ctx, int(wait_limit_ns)), self.ctx)
 
     def sadi_save_state(self) -> bytes:
         n = C.c_size_t(0)

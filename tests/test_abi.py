@@ -67,3 +67,14 @@ def test_null_out_pointer_rejected(lib):
 
 def test_noalloc_step_rejects_null_context_without_a_gpu(lib):
     assert lib.sadi_step_noalloc(None, None, None, None, 1) == 1
+
+
+def test_batch_create_validates_before_any_device_call(lib):
+    out = ctypes.c_void_p()
+    n = (ctypes.c_int * 1)(63)
+    d = (ctypes.c_double * 1)(1.5)
+    assert lib.sadi_batch_create(0, n, d, d, d, None, 0, 1, ctypes.byref(out)) == 1      # count < 1
+    assert out.value is None
+    assert lib.sadi_batch_create(1, n, d, d, d, None, 0, 7, ctypes.byref(out)) == 1      # prec
+    assert lib.sadi_batch_create(1, None, d, d, d, None, 0, 1, ctypes.byref(out)) == 1   # arrays
+    assert b"prec" in lib.sadi_batch_last_error(None) or b"arrays" in lib.sadi_batch_last_error(None)
