@@ -18,6 +18,11 @@ sadi     -- the discrete operators L_h, delta_x, delta_y (Sec. 2), the ADI facto
             Gohberg-Semencul solve (Proposition 1, Algorithm 1), the discrete
             energy of the stability theorem (Sec. 4) and the Error_1/Error_2
             estimators of Sec. 6.
+diffusion -- S-ADI for the fractional Laplacian diffusion equation, the further
+            application the conclusion (Sec. 7) names without a scheme: the
+            splitting of Secs. 2-3 with Crank-Nicolson on the Riesz parts, the
+            remainder and g extrapolated to t_{n+1/2}, and the factorisation
+            term on the second difference (the reading is in its docstring).
 
 Every function is plain FP64 numpy/scipy and cites the passage it follows.
 Parity status of each function is listed in its docstring; every function

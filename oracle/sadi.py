@@ -42,17 +42,22 @@ import scipy.linalg
 
 from . import weights as W
 
-G_ZERO, G_NEG_CUBE, G_NEG_SIN = 0, 1, 2
+G_ZERO, G_NEG_CUBE, G_NEG_SIN, G_GENERAL = 0, 1, 2, 3
 
 
-def g_eval(kind: int, u: np.ndarray) -> np.ndarray:
-    """Nonlinearity g(u): 0, -u^3 (Klein-Gordon, Sec. 6 Ex. 2), -sin u (sine-Gordon, Ex. 1)."""
+def g_eval(kind: int, u: np.ndarray, coef=(0.0, 0.0, 0.0)) -> np.ndarray:
+    """Nonlinearity g(u) of the problem statement (Sec. 1): 0, -u^3
+    (Klein-Gordon, Sec. 6 Ex. 2), -sin u (sine-Gordon, Ex. 1), or the general
+    form c1 u + c3 u^3 + cs sin u with coef = (c1, c3, cs)."""
     if kind == G_ZERO:
         return np.zeros_like(u)
     if kind == G_NEG_CUBE:
         return -u * u * u
     if kind == G_NEG_SIN:
         return -np.sin(u)
+    if kind == G_GENERAL:
+        c1, c3, cs = coef
+        return c1 * u + c3 * (u * u * u) + cs * np.sin(u)
     raise ValueError(f"unknown g kind {kind}")
 
 
@@ -77,6 +82,7 @@ class Problem:
     a1: np.ndarray | None = field(default=None, repr=False)   # a_i, 0<=i<N
     fft_size: int | None = None      # circulant size Q >= 2N - 1 of the fft tier (default 2N)
     fft_workers: int | None = None   # threads of its transforms (default 1)
+    gc: tuple = (0.0, 0.0, 0.0)      # coefficients of the general g (kind 3)
 
     def __post_init__(self):
         self.h, self.x = grid(self.N, self.a, self.b)
@@ -177,7 +183,7 @@ def solve_y(P: Problem, W_: np.ndarray) -> np.ndarray:
 def rhs(P: Problem, u: np.ndarray, Lu: np.ndarray, first: bool, phi2=None, f=None) -> np.ndarray:
     """B^n of eq. "ADI scheme equivalent" (optionally with a source f^n added
     to g, for the manufactured-solution tests)."""
-    gu = g_eval(P.g, u)
+    gu = g_eval(P.g, u, P.gc)
     if f is not None:
         gu = gu + f
     if first:
@@ -247,7 +253,7 @@ def step_literal(P: Problem, ops, u_prev, u_cur, first: bool, phi2=None):
     I = np.eye(N2)
     k, t = P.kappa, P.tau
     un = u_cur.reshape(-1)
-    gn = g_eval(P.g, un)
+    gn = g_eval(P.g, un, P.gc)
     R = L - Dx - Dy                                  # the explicit remainder
     S = Dx + Dy
     DxDy = Dx @ Dy

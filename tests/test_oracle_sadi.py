@@ -222,6 +222,52 @@ def test_alpha2_single_sine_mode_recursion():
         assert np.abs(u_end - c[30] * mode).max() < 1e-12 * abs(c[30])
 
 
+def test_general_g_reduces_to_the_named_kinds():
+    # g(u) = c1 u + c3 u^3 + cs sin u: (0, -1, 0) is the Klein-Gordon term and
+    # (0, 0, -1) the sine-Gordon term of Sec. 6, exactly
+    u = _rng(3).uniform(-3, 3, (7, 5))
+    assert np.array_equal(S.g_eval(S.G_GENERAL, u, (0.0, -1.0, 0.0)), S.g_eval(S.G_NEG_CUBE, u))
+    assert np.array_equal(S.g_eval(S.G_GENERAL, u, (0.0, 0.0, -1.0)), S.g_eval(S.G_NEG_SIN, u))
+    assert np.array_equal(S.g_eval(S.G_GENERAL, u, (0.0, 0.0, 0.0)), np.zeros_like(u))
+    assert np.array_equal(S.g_eval(S.G_GENERAL, u, (2.0, 0.0, 0.0)), 2.0 * u)
+
+
+def test_alpha2_sine_mode_with_linear_g():
+    # g(u) = c1 u keeps a Dirichlet sine mode a mode at alpha = 2: B^n gains
+    # tau^2 c1 c_n, so (1+t^2 k mu_k/2)(1+t^2 k mu_l/2)(c_{n+1}-2c_n+c_{n-1})
+    # = t^2 (c1 - k (mu_k + mu_l)) c_n, and the start step carries t^2/2 c1 c_0
+    N, kap, tau, c1 = 15, 0.8, 0.05, -2.5
+    P = S.Problem(N, 2.0, kap, tau, g=S.G_GENERAL, gc=(c1, 0.0, 0.0))
+    h = P.h
+    for (k, l) in [(1, 2), (5, 3)]:
+        X, Y = WL.coords(N, -1.0, 1.0)
+        mode = np.sin(k * np.pi * (X + 1) / 2) * np.sin(l * np.pi * (Y + 1) / 2)
+        mu = lambda m: 4 / h ** 2 * math.sin(m * math.pi / (2 * (N + 1))) ** 2
+        fac = (1 + tau ** 2 * kap * mu(k) / 2) * (1 + tau ** 2 * kap * mu(l) / 2)
+        lam = kap * (mu(k) + mu(l)) - c1
+        c0, d0 = 0.7, -0.4
+        u_end = S.run(P, c0 * mode, d0 * mode, 30)
+        c = [c0, c0 + (tau * d0 - 0.5 * tau ** 2 * lam * c0) / fac]
+        for n in range(1, 30):
+            c.append(2 * c[n] - c[n - 1] - tau ** 2 * lam * c[n] / fac)
+        assert np.abs(u_end - c[30] * mode).max() < 1e-12 * abs(c[30])
+
+
+@pytest.mark.parametrize("N,alpha", [(3, 1.5), (6, 1.7)])
+def test_factored_step_equals_literal_scheme_general_g(N, alpha):
+    P = S.Problem(N, alpha, 0.7, 0.3, -1.0, 1.0, S.G_GENERAL, gc=(-1.3, -0.4, 0.8))
+    ops = S.dense_operators(P)
+    rng = _rng(20 + N)
+    u0 = rng.uniform(-1, 1, (N, N))
+    phi2 = rng.uniform(-1, 1, (N, N))
+    u1f = S.step(P, None, u0, True, phi2)
+    u1l = S.step_literal(P, ops, None, u0, True, phi2)
+    assert np.abs(u1f - u1l).max() < 1e-12 * np.abs(u1l).max()
+    u2f = S.step(P, u0, u1f, False)
+    u2l = S.step_literal(P, ops, u0, u1f, False)
+    assert np.abs(u2f - u2l).max() < 1e-12 * np.abs(u2l).max()
+
+
 def test_fft_tier_equals_direct_tier():
     P = S.Problem(31, 1.6, 1.0, 0.02, g=S.G_NEG_SIN)
     phi1 = WL.gaussian_bumps(31, 4, 7)
