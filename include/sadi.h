@@ -50,8 +50,11 @@ typedef enum {
   SADI_EUNSUPPORTED = 8   /* valid request this library version does not implement */
 } sadi_status;
 
-/* Nonlinearity g(u) of Sec. 1 (Sec. 6 uses -sin u and -u^3). */
-typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2 } sadi_g;
+/* Nonlinearity g(u) of Sec. 1 (Sec. 6 uses -sin u and -u^3).
+ * SADI_G_GENERAL: g(u) = c1 u + c3 u^3 + cs sin u with the coefficients of
+ * sadi_set_nonlinearity (all 0 until set), e.g. the linear Klein-Gordon term
+ * -u, the phi^4 term -u - u^3, or a scaled sine-Gordon term. */
+typedef enum { SADI_G_ZERO = 0, SADI_G_NEG_CUBE = 1, SADI_G_NEG_SIN = 2, SADI_G_GENERAL = 3 } sadi_g;
 
 /* Arithmetic of the per-step path.  Setup (weights, generator, spectra, the
  * dense inverse) is always FP64.
@@ -92,9 +95,42 @@ typedef enum {
 sadi_status sadi_create(int N, double alpha, double kappa, double tau,
                         const double domain[2], sadi_ctx **out);
 
+/* A context for the fractional Laplacian diffusion equation
+ *     u_t = -kappa (-Delta)^{alpha/2} u + g(u) + f on Omega, u = 0 outside,
+ *     u(., 0) = phi1,
+ * the further application of the S-ADI idea that the paper names in its
+ * conclusion (Sec. 7) without giving a scheme.  This library takes the
+ * splitting of Secs. 2-3 with the Riesz parts delta_x + delta_y by
+ * Crank-Nicolson, the remainder L_h - delta_x - delta_y and g explicit at
+ * t_{n+1/2} by the extrapolation u~ = u^n + (u^n - u^{n-1})/2, and the
+ * factorisation term (kappa^2 tau/4) delta_x delta_y on the second
+ * difference, so that each step is
+ *     (I + kappa tau/2 delta_x)(I + kappa tau/2 delta_y) Delta
+ *         = tau (-kappa L_h u~ + g(u~) + f^{n+1/2}) - (u^n - u^{n-1}),
+ *     u^{n+1} = 2u^n - u^{n-1} + Delta      (n = 0: u~ = u^0, u^1 = u^0 + Delta),
+ * second order in tau, with the same operators, Gohberg-Semencul sweeps and
+ * step forms as the wave equation (tau in place of tau^2 in the ADI factor
+ * and the symbol).  Arguments, set-up and every other call as sadi_create;
+ * sadi_set_initial takes phi2 = NULL (SADI_EINVAL otherwise); sources are
+ * sampled at the step midpoints t_{n+1/2} (sadi_set_source) or given for
+ * them (sadi_step_source).  The dense-inverse form's accuracy limit applies
+ * with s = kappa tau / (2 h^alpha), usually far larger than the wave's. */
+sadi_status sadi_create_diffusion(int N, double alpha, double kappa, double tau,
+                                  const double domain[2], sadi_ctx **out);
+
+/* *eq = 0 for a context of sadi_create (wave), 1 for sadi_create_diffusion. */
+sadi_status sadi_get_equation(const sadi_ctx *ctx, int *eq);
+
 /* Choose g and the step precision.  Must be called before sadi_set_initial
  * (SADI_ESTATE otherwise). */
 sadi_status sadi_set_options(sadi_ctx *ctx, int g, int prec);
+
+/* g(u) = c1 u + c3 u^3 + cs sin u (finite coefficients, else SADI_EINVAL):
+ * selects SADI_G_GENERAL with these coefficients; the nonlinear term enters
+ * B^n as the paper's g does (Sec. 3), evaluated in the step's precision (the
+ * FP32 register path uses the hardware sine, whose error is scaled by
+ * tau^2).  Must precede sadi_set_initial (SADI_ESTATE otherwise). */
+sadi_status sadi_set_nonlinearity(sadi_ctx *ctx, double c1, double c3, double cs);
 
 /* Current g and precision of ctx (either pointer may be NULL). */
 sadi_status sadi_get_options(const sadi_ctx *ctx, int *g, int *prec);
@@ -108,6 +144,20 @@ sadi_status sadi_get_options(const sadi_ctx *ctx, int *g, int *prec);
  * to remove the source.  Call after sadi_set_options; changing the precision
  * afterwards returns SADI_ESTATE. */
 sadi_status sadi_set_source(sadi_ctx *ctx, const double *F, double omega, double phase);
+
+/* One time step (as sadi_step(ctx, 1)) with a source term given as a grid
+ * function for this step: the equation u_tt = -kappa (-Delta)^{alpha/2} u +
+ * g(u) + f (an extension beyond the paper's problem statement, e.g. for
+ * manufactured solutions or driven problems), f^n = f at t_n = n tau
+ * entering B^n as g(u^n) does: tau^2 f^n for n >= 1, tau^2/2 f^0 at n = 0,
+ * fused into the B^n epilogue.  f: device memory on the context's device,
+ * N*N elements (layout above) of dtype 0 = double or 1 = float, owned by the
+ * caller and read by the step on the context's stream (keep it unchanged
+ * until the step has run).  A dtype other than the step's precision is
+ * converted into a buffer of the context (allocated on first use) first.
+ * SADI_EINVAL if f is not such a buffer; SADI_ESTATE while a separable source
+ * (sadi_set_source) is set or before sadi_set_initial. */
+sadi_status sadi_step_source(sadi_ctx *ctx, const void *f, int dtype);
 
 /* Issue all further device work on cuda_stream (a cudaStream_t, e.g. a torch
  * stream's handle); NULL selects the context's own stream.  The caller keeps

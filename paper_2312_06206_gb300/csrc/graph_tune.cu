@@ -208,7 +208,7 @@ sadi_status sadi_autotune(sadi_ctx** ctxs, int count, int g, int flags) {
     for (int j = 0; j < k; ++j)
       if (ctxs[j] == c) return fail(c, SADI_EINVAL, "a context appears twice");
   }
-  if (g < SADI_G_ZERO || g > SADI_G_NEG_SIN) return fail(ctxs[0], SADI_EINVAL, "g must be 0, 1 or 2");
+  if (g < SADI_G_ZERO || g > SADI_G_GENERAL) return fail(ctxs[0], SADI_EINVAL, "g must be 0, 1, 2 or 3");
   // groups of equal N (they share a choice), at most one register-path batch each
   std::map<int, std::vector<sadi_ctx*>> by_n;
   for (int k = 0; k < count; ++k) by_n[ctxs[k]->g.N].push_back(ctxs[k]);

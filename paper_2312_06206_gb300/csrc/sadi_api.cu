@@ -56,7 +56,7 @@ void free_all(sadi_ctx* c) {
   for (void* p : ptrs)
     if (p) cudaFree(p);
   conv3_free(&c->c3);
-  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->tcdep, c->Chi, c->Clo, c->wd};
+  void* dense[] = {c->Eh, c->El, c->Bh, c->Bl, c->WTh, c->WTl, c->tcerr, c->tcdep, c->Chi, c->Clo, c->wd, c->Fconv};
   for (void* p : dense)
     if (p) cudaFree(p);
   for (auto& a : c->ev_pool)
@@ -180,9 +180,12 @@ sadi_status setup_dense(sadi_ctx* c) {
 
 using namespace sadi_api;
 
-extern "C" {
+namespace sadi_api {
 
-sadi_status sadi_create(int N, double alpha, double kappa, double tau, const double domain[2], sadi_ctx** out) {
+// sadi_create and sadi_create_diffusion: eq 0 (wave) scales the ADI factor
+// and the symbol by tau^2, eq 1 (diffusion) by tau.
+sadi_status create_impl(int eq, int N, double alpha, double kappa, double tau, const double domain[2],
+                        sadi_ctx** out) {
   if (!out) {
     g_create_err = "sadi_create: out is NULL";
     return SADI_EINVAL;
@@ -208,13 +211,15 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
     delete c;
     return st;
   };
+  c->eq = eq;
   c->alpha = alpha;
   c->kappa = kappa;
   c->tau = tau;
   c->a = domain[0];
   c->b = domain[1];
   c->h = (c->b - c->a) / (N + 1);
-  c->s = kappa * tau * tau / (2.0 * std::pow(c->h, alpha));
+  const double tp = eq == 0 ? tau * tau : tau;   // tau^2 (wave) or tau (diffusion)
+  c->s = kappa * tp / (2.0 * std::pow(c->h, alpha));
   Geom& g = c->g;
   g.N = N;
   g.logNp = log2i(N < 8 ? 8 : N);
@@ -268,7 +273,7 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
   if ((e = launch_riesz1d(c->a1, Np, alpha, st))) return bail(cuda_fail(c, e, "riesz weights"));
   const int M = (8 * Np > 1024) ? 8 * Np : 1024;
   if ((e = run_weights2d(c->a2d, g, alpha, M, c->stw64, st))) return bail(cuda_fail(c, e, "2D weights"));
-  const double scale = -kappa * tau * tau * std::pow(c->h, -alpha) / ((double)P * (double)Np);
+  const double scale = -kappa * tp * std::pow(c->h, -alpha) / ((double)P * (double)Np);
   if ((e = run_lambda(c->a2d, g, c->stw64, c->tw64, scale, c->lnat, c->lpb64, c->lpb32, st)))
     return bail(cuda_fail(c, e, "symbol"));
   int gstat = 1;
@@ -293,11 +298,30 @@ sadi_status sadi_create(int N, double alpha, double kappa, double tau, const dou
   return SADI_OK;
 }
 
+}  // namespace sadi_api
+
+extern "C" {
+
+sadi_status sadi_create(int N, double alpha, double kappa, double tau, const double domain[2], sadi_ctx** out) {
+  return create_impl(0, N, alpha, kappa, tau, domain, out);
+}
+
+sadi_status sadi_create_diffusion(int N, double alpha, double kappa, double tau, const double domain[2],
+                                  sadi_ctx** out) {
+  return create_impl(1, N, alpha, kappa, tau, domain, out);
+}
+
+sadi_status sadi_get_equation(const sadi_ctx* c, int* eq) {
+  if (!c || !eq) return SADI_EINVAL;
+  *eq = c->eq;
+  return SADI_OK;
+}
+
 sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
   if (!c) return SADI_EINVAL;
   if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
   if (c->initialized) return fail(c, SADI_ESTATE, "sadi_set_options must precede sadi_set_initial");
-  if (g < SADI_G_ZERO || g > SADI_G_NEG_SIN) return fail(c, SADI_EINVAL, "g must be 0, 1 or 2");
+  if (g < SADI_G_ZERO || g > SADI_G_GENERAL) return fail(c, SADI_EINVAL, "g must be 0, 1, 2 or 3");
   if (prec != SADI_PREC_FP64 && prec != SADI_PREC_FP32 && prec != SADI_PREC_FP32_DENSE)
     return fail(c, SADI_EINVAL, "prec must be 0, 1 or 2");
   if (prec == SADI_PREC_FP64 && c->g.N > 4096)
@@ -313,8 +337,23 @@ sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
   if (prec != c->prec) {
     if (c->F) return fail(c, SADI_ESTATE, "set the precision before sadi_set_source");
     c->prec = prec;
+    if (c->Fconv) cudaFree(c->Fconv);
+    c->Fconv = nullptr;
     return alloc_state(c);
   }
+  return SADI_OK;
+}
+
+sadi_status sadi_set_nonlinearity(sadi_ctx* c, double c1, double c3, double cs) {
+  if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
+  if (c->initialized) return fail(c, SADI_ESTATE, "sadi_set_nonlinearity must precede sadi_set_initial");
+  if (!std::isfinite(c1) || !std::isfinite(c3) || !std::isfinite(cs))
+    return fail(c, SADI_EINVAL, "the coefficients of g must be finite");
+  c->gc[0] = c1;
+  c->gc[1] = c3;
+  c->gc[2] = cs;
+  c->gkind = SADI_G_GENERAL;
   return SADI_OK;
 }
 
@@ -360,6 +399,7 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   if (!c) return SADI_EINVAL;
   if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
   if (!phi1) return fail(c, SADI_EINVAL, "phi1 is NULL");
+  if (c->eq == 1 && phi2) return fail(c, SADI_EINVAL, "the diffusion equation has no phi2 (pass NULL)");
   if (c->prec == SADI_PREC_FP64 && c->g.N > 4096)
     return fail(c, SADI_EUNSUPPORTED, "the FP64 step path supports N <= 4096; select SADI_PREC_FP32");
   const size_t nn = (size_t)c->g.N * c->g.N;
@@ -421,6 +461,30 @@ sadi_status next_events(sadi_ctx* c, cudaEvent_t** out) {
   return SADI_OK;
 }
 
+// B^n scalars of the next step of c (time level n): g, the source term (the
+// field of sadi_step_source, else the separable one) and the n = 0 switch
+RhsParams rhs_of(const sadi_ctx* c, long long n) {
+  RhsParams rp{};
+  rp.eq = c->eq;
+  rp.tau = c->tau;
+  rp.tau2 = c->eq == 0 ? c->tau * c->tau : c->tau;
+  rp.g = c->gkind;
+  rp.first = n == 0 ? 1 : 0;
+  if (c->F_step) {
+    rp.F = c->F_step;
+    rp.fsc = 1.0;
+  } else if (c->F) {
+    // the wave step samples f at t_n, the diffusion step at t_{n+1/2}
+    const double t = ((double)n + (c->eq == 0 ? 0.0 : 0.5)) * c->tau;
+    rp.F = c->F;
+    rp.fsc = std::cos(c->f_omega * t + c->f_phase);
+  }
+  rp.gc1 = c->gc[0];
+  rp.gc3 = c->gc[1];
+  rp.gcs = c->gc[2];
+  return rp;
+}
+
 RegInst reg_inst(const sadi_ctx* c) {
   RegInst r{};
   r.tw1 = c->rtw1;
@@ -438,11 +502,16 @@ RegInst reg_inst(const sadi_ctx* c) {
   r.N = c->g.N;
   r.r = c->g.r;
   r.tau = (float)c->tau;
-  r.tau2 = (float)(c->tau * c->tau);
+  r.tau2 = (float)(c->eq == 0 ? c->tau * c->tau : c->tau);
+  r.eq = c->eq;
   r.gkind = c->gkind;
   r.first = c->n == 0 ? 1 : 0;
-  r.F = static_cast<const float*>(c->F);
-  r.fsc = c->F ? (float)std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.f;
+  const RhsParams rp = rhs_of(c, c->n);
+  r.F = static_cast<const float*>(rp.F);
+  r.fsc = (float)rp.fsc;
+  r.gc1 = (float)c->gc[0];
+  r.gc3 = (float)c->gc[1];
+  r.gcs = (float)c->gc[2];
   r.C_hi = c->Chi;
   r.C_lo = c->Clo;
   r.Bh = c->Bh;
@@ -457,8 +526,7 @@ bool is_dense(const sadi_ctx* c) { return c->prec == SADI_PREC_FP32_DENSE; }
 // One step of a context on the shared-memory engine (FP64, or FP32 N' > 1024),
 // on stream st.
 sadi_status step_smem(sadi_ctx* c, cudaEvent_t* ev, cudaStream_t st) {
-  RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0, c->F,
-               c->F ? std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.0};
+  const RhsParams rp = rhs_of(c, c->n);
   cudaError_t e;
   if (c->prec == SADI_PREC_FP64) {
     void* ucur = c->ubuf[c->cur];
@@ -523,8 +591,7 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
     e = launch_step_reg(b, c->g.logNp, max_n, st_, ev, true);
   } else {
     if (count != 1) return fail(c, SADI_EINVAL, "internal: shared-memory dense group of more than one");
-    RhsParams rp{c->tau, c->tau * c->tau, c->gkind, c->n == 0 ? 1 : 0, c->F,
-                 c->F ? std::cos(c->f_omega * (double)c->n * c->tau + c->f_phase) : 0.0};
+    const RhsParams rp = rhs_of(c, c->n);
     StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32, c3_of(c)};
     e = launch_dense_rows(c->g, tb, c->tiles32, rp, static_cast<const float*>(c->ubuf[0]),
                           static_cast<const float*>(c->ubuf[1]), static_cast<const float*>(c->phi2), c->S,
@@ -1079,8 +1146,7 @@ extern "C" sadi_status sadi_step_noalloc(sadi_ctx* c, const double* u_prev, cons
                 std::string("sadi_step_noalloc: looking up the scratch array's device address failed: ") +
                     cudaGetErrorName(se) + " (make the first call on a device outside any stream capture)");
   }
-  RhsParams rp{c->tau, c->tau * c->tau, c->gkind, 0, c->F,
-               c->F ? std::cos(c->f_omega * (double)n * c->tau + c->f_phase) : 0.0};
+  const RhsParams rp = rhs_of(c, n);
   StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
   double* W = reinterpret_cast<double*>(static_cast<char*>(scratch) + w_off);
   // u_prev is only read by the plain (uncompensated) leapfrog form
@@ -1090,15 +1156,46 @@ extern "C" sadi_status sadi_step_noalloc(sadi_ctx* c, const double* u_prev, cons
   return SADI_OK;
 }
 
+// ---- sadi_step_source: one step with a per-step source field ---------------
+
+extern "C" sadi_status sadi_step_source(sadi_ctx* c, const void* f, int dtype) {
+  if (!c) return SADI_EINVAL;
+  sadi_status st = check_steppable(c);
+  if (st != SADI_OK) return st;
+  if (!f) return fail(c, SADI_EINVAL, "sadi_step_source: f is NULL");
+  if (dtype != 0 && dtype != 1) return fail(c, SADI_EINVAL, "sadi_step_source: dtype must be 0 (double) or 1 (float)");
+  if (c->F) return fail(c, SADI_ESTATE, "sadi_step_source: remove the separable source (sadi_set_source NULL) first");
+  const size_t nn = (size_t)c->g.N * c->g.N;
+  st = check_device_buffer(c, f, nn * (dtype == 0 ? sizeof(double) : sizeof(float)), "f");
+  if (st != SADI_OK) return st;
+  const bool f64 = c->prec == SADI_PREC_FP64;
+  const void* field = f;
+  if ((dtype == 0) != f64) {
+    if (!c->Fconv) CK(cudaMalloc(&c->Fconv, nn * esize(c->prec)), "cudaMalloc(source conversion)");
+    if (f64)
+      CK(launch_convert_f2d(static_cast<const float*>(f), static_cast<double*>(c->Fconv), nn, c->stream),
+         "source convert");
+    else
+      CK(launch_convert_d2f(static_cast<const double*>(f), static_cast<float*>(c->Fconv), nn, c->stream),
+         "source convert");
+    field = c->Fconv;
+  }
+  c->F_step = field;
+  st = sadi_step(c, 1);
+  c->F_step = nullptr;
+  return st;
+}
+
 // ---- checkpoint / resume -----------------------------------------------------
 
 namespace {
 
 struct StateHeader {
-  char magic[8];          // "SADIST01"
-  int N, Np, prec, gkind, cur, initialized;
+  char magic[8];          // "SADIST02"
+  int N, Np, prec, gkind, cur, initialized, eq;
   long long n;
   double alpha, kappa, tau, a, b;
+  double gc[3];           // coefficients of SADI_G_GENERAL
   int narrays;            // arrays of N*N elements that follow
   int esz;                // bytes per element of the state arrays
 };
@@ -1141,11 +1238,13 @@ extern "C" sadi_status sadi_save_state(sadi_ctx* c, void* buf, size_t* bytes) {
     return fail(c, SADI_EINVAL, "sadi_save_state: buffer too small (size returned in *bytes)");
   }
   StateHeader h{};
-  std::memcpy(h.magic, "SADIST01", 8);
+  std::memcpy(h.magic, "SADIST02", 8);
+  for (int k = 0; k < 3; ++k) h.gc[k] = c->gc[k];
   h.N = c->g.N;
   h.Np = c->g.Np;
   h.prec = c->prec;
   h.gkind = c->gkind;
+  h.eq = c->eq;
   h.cur = 0;
   h.initialized = 1;
   h.n = c->n;
@@ -1171,9 +1270,11 @@ extern "C" sadi_status sadi_load_state(sadi_ctx* c, const void* buf, size_t byte
   StateHeader h;
   if (bytes < sizeof h) return fail(c, SADI_EINVAL, "sadi_load_state: blob too small");
   std::memcpy(&h, buf, sizeof h);
-  if (std::memcmp(h.magic, "SADIST01", 8) != 0) return fail(c, SADI_EINVAL, "sadi_load_state: not a state blob");
-  if (h.N != c->g.N || h.prec != c->prec || h.gkind != c->gkind || h.alpha != c->alpha || h.kappa != c->kappa ||
-      h.tau != c->tau || h.a != c->a || h.b != c->b)
+  if (std::memcmp(h.magic, "SADIST02", 8) != 0) return fail(c, SADI_EINVAL, "sadi_load_state: not a state blob");
+  if (h.N != c->g.N || h.prec != c->prec || h.gkind != c->gkind || h.eq != c->eq || h.alpha != c->alpha ||
+      h.kappa != c->kappa ||
+      h.tau != c->tau || h.a != c->a || h.b != c->b || h.gc[0] != c->gc[0] || h.gc[1] != c->gc[1] ||
+      h.gc[2] != c->gc[2])
     return fail(c, SADI_EINVAL,
                 "sadi_load_state: the blob was saved by a context with another N, alpha, kappa, tau, domain, g or "
                 "precision");

@@ -21,7 +21,9 @@ struct sadi_ctx {
   using TcInst = sadi::TcInst;
   Geom g{};
   double alpha = 0, kappa = 0, tau = 0, a = 0, b = 0, h = 0, s = 0;
+  int eq = 0;                       // 0 the wave equation, 1 the diffusion equation
   int gkind = SADI_G_ZERO;
+  double gc[3] = {0.0, 0.0, 0.0};   // coefficients of SADI_G_GENERAL (u, u^3, sin u)
   int prec = SADI_PREC_FP64;
   int device = 0;
   cudaStream_t own_stream = nullptr;
@@ -84,6 +86,10 @@ struct sadi_ctx {
   // optional source term f^n = cos(omega t_n + phase) F(x)
   void* F = nullptr;                // T, N x N
   double f_omega = 0.0, f_phase = 0.0;
+  // sadi_step_source: the source field of the step being issued (T, N x N;
+  // the caller's buffer or Fconv, its conversion to T), nullptr otherwise
+  const void* F_step = nullptr;
+  void* Fconv = nullptr;
   // dense-inverse form (SADI_PREC_FP32_DENSE): BF16 pairs, npad x npad,
   // zero-padded: E = H^-1 - I, B^n rows, W^T rows; tensor maps of the two GEMMs
   int npad = 0;

@@ -20,12 +20,18 @@ struct Geom {
 };
 
 // Scalars of the right-hand side B^n (Sec. 3): tau, tau^2, g kind, n == 0.
+// g kinds: 0 none, 1 -u^3, 2 -sin u, 3 gc1 u + gc3 u^3 + gcs sin u.
+// eq 0: the wave equation (tau2 = tau^2); eq 1: the diffusion equation
+// (tau2 = tau), B = tau (-kappa L_h u~ + g(u~) + f) - d with d = u^n - u^{n-1}
+// and u~ = u^n + d/2 (d = 0 at n = 0).
 struct RhsParams {
+  int eq;
   double tau, tau2;
   int g;
   int first;
   const void* F;   // optional source field (T, N x N) or nullptr
   double fsc;      // its time factor cos(omega t_n + phase) for this step
+  double gc1, gc3, gcs;   // coefficients of g kind 3
 };
 
 // ---- setup (FP64), setup_kernels.cu ----------------------------------------
@@ -146,6 +152,8 @@ struct RegInst {
   float tau, tau2;
   float fsc;            // time factor of the source for this step
   int gkind, first;
+  float gc1, gc3, gcs;  // coefficients of g kind 3 (gc1 u + gc3 u^3 + gcs sin u)
+  int eq;               // 0 wave, 1 diffusion (RhsParams::eq); tau2 = tau^2 or tau
 };
 constexpr int kMaxBatch = 32;
 // passed by value as a __grid_constant__ kernel parameter (about 4 KB)

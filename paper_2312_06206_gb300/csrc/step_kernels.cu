@@ -35,9 +35,10 @@ constexpr int kThreads = 256;
 constexpr int kMaxPairs = 16;
 
 template <typename T>
-__device__ __forceinline__ T g_of(int kind, T u) {
-  if (kind == 1) return -u * u * u;
-  if (kind == 2) return -sin(u);
+__device__ __forceinline__ T g_of(const RhsParams& rp, T u) {
+  if (rp.g == 1) return -u * u * u;
+  if (rp.g == 2) return -sin(u);
+  if (rp.g == 3) return (T(rp.gc1) + T(rp.gc3) * u * u) * u + T(rp.gcs) * sin(u);
   return T(0);
 }
 
@@ -145,10 +146,12 @@ __device__ __forceinline__ T gs_out(const cx<T>* vh, int k, const Geom& g, const
 // length P = 2Np, via a complex FFT of length Np of z[n] = x[2n] + i x[2n+1].
 // Slot s >= 1 holds X[brev(s)]; slot 0 holds X[0] + i X[Np] (both real).
 // ---------------------------------------------------------------------------
+// With u2 (the diffusion step, FP64) the transformed rows are those of
+// u + beta (u - u2): the extrapolation u~ = u^n + (u^n - u^{n-1})/2.
 template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw,
-           const cx<T>* __restrict__ tw, int NR) {
+           const cx<T>* __restrict__ tw, int NR, const T* __restrict__ u2 = nullptr, T beta = T(0)) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
@@ -162,6 +165,11 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
       const T* row = u + (size_t)(row0 + v) * N;
       if (2 * n < N) a = row[2 * n];
       if (2 * n + 1 < N) b = row[2 * n + 1];
+      if (u2) {
+        const T* row2 = u2 + (size_t)(row0 + v) * N;
+        if (2 * n < N) a += beta * (a - row2[2 * n]);
+        if (2 * n + 1 < N) b += beta * (b - row2[2 * n + 1]);
+      }
     }
     buf[v * vs + sidx<T>(n)] = mkc(a, b);
   }
@@ -333,6 +341,32 @@ k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ 
 }
 
 // ---------------------------------------------------------------------------
+// B^n at grid index idx (row element k, convolution read from the row vector
+// e).  Wave (Sec. 3): conv + tau^2 (g(u^n) + f^n), or at n = 0
+// tau phi2 + (conv + tau^2 (g + f))/2, conv = -kappa tau^2 L_h u^n.
+// Diffusion: tau (g(u~) + f) - d + conv, with conv = -kappa tau L_h u~ (the
+// plain form transforms u~ itself), or in the compensated form (Ch: the
+// increment d is what was transformed, and C accumulates -kappa tau L_h u^n)
+// C + conv/2 = -kappa tau L_h (u^n + d/2).  uaux is u^{n-1} in the plain form
+// and d in the compensated one.
+template <typename T>
+__device__ __forceinline__ T rhs_at(const RhsParams& rp, const cx<T>* e, int k, size_t idx, const T* u,
+                                    const T* uaux, const T* phi2, float* Ch, float* Cl) {
+  const T cd = real_view<T>(e, k);
+  const T conv = Ch ? acc_remainder<T>(Ch, Cl, idx, cd) : cd;
+  const T uu = u[idx];
+  T fsrc = rp.F ? T(rp.fsc) * static_cast<const T*>(rp.F)[idx] : T(0);
+  if (rp.eq == 0) {
+    const T gg = T(rp.tau2) * (g_of<T>(rp, uu) + fsrc);
+    return rp.first ? T(rp.tau) * phi2[idx] + T(0.5) * (conv + gg) : conv + gg;
+  }
+  const T d = rp.first ? T(0) : (Ch ? uaux[idx] : uu - uaux[idx]);
+  const T ut = uu + T(0.5) * d;
+  const T b = conv + T(rp.tau2) * (g_of<T>(rp, ut) + fsrc) - d;
+  return Ch ? b + T(0.5) * cd : b;
+}
+
+// ---------------------------------------------------------------------------
 // k_rows_solve: per row j: inverse real FFT of the convolved half spectrum
 // (gives -kappa tau^2 L_h u^n, the scale being folded into the symbol),
 // B^n epilogue with g(u^n) (and phi2 when n = 0), then the x sweep W_j = H^-1 B_j.
@@ -341,7 +375,8 @@ k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ 
 // split into BF16 pairs, to Bh / Bl (ld ldp).
 template <typename T, bool DENSE = false, int NT = kThreads>
 __global__ void __launch_bounds__(NT)
-k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ phi2, T* __restrict__ W,
+k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ uaux,
+             const T* __restrict__ phi2, T* __restrict__ W,
              Geom g, RhsParams rp, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
              const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR,
              float* Ch, float* Cl, unsigned short* Bh = nullptr, unsigned short* Bl = nullptr, int ldp = 0) {
@@ -368,24 +403,8 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
       if (v < nrows) {
         const int row = row0 + v;
         const cx<T>* e = buf + v * vs;
-        if (k < N) {
-          T conv = real_view<T>(e, k);
-          if (Ch) conv = acc_remainder<T>(Ch, Cl, (size_t)row * N + k, conv);
-          const T uu = u[(size_t)row * N + k];
-          T gsrc = g_of<T>(rp.g, uu);
-          if (rp.F) gsrc += T(rp.fsc) * static_cast<const T*>(rp.F)[(size_t)row * N + k];
-          const T gg = T(rp.tau2) * gsrc;
-          ra[it] = rp.first ? T(rp.tau) * phi2[(size_t)row * N + k] + half * (conv + gg) : conv + gg;
-        }
-        if (k2 < N) {
-          T conv = real_view<T>(e, k2);
-          if (Ch) conv = acc_remainder<T>(Ch, Cl, (size_t)row * N + k2, conv);
-          const T uu = u[(size_t)row * N + k2];
-          T gsrc = g_of<T>(rp.g, uu);
-          if (rp.F) gsrc += T(rp.fsc) * static_cast<const T*>(rp.F)[(size_t)row * N + k2];
-          const T gg = T(rp.tau2) * gsrc;
-          rb[it] = rp.first ? T(rp.tau) * phi2[(size_t)row * N + k2] + half * (conv + gg) : conv + gg;
-        }
+        if (k < N) ra[it] = rhs_at<T>(rp, e, k, (size_t)row * N + k, u, uaux, phi2, Ch, Cl);
+        if (k2 < N) rb[it] = rhs_at<T>(rp, e, k2, (size_t)row * N + k2, u, uaux, phi2, Ch, Cl);
       }
     }
   }
@@ -652,13 +671,16 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   const int rblocks = (g.N + NR - 1) / NR;
   if (ev) cudaEventRecord(ev[0], st);
   // incremental remainder (Ch != nullptr): transform the increment d = u_prev
-  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(Ch ? u_prev : u_cur, S, g, stw, tw, NR);
+  // FP64 diffusion step (n >= 1): transform u~ = u^n + (u^n - u^{n-1})/2
+  const bool extrap = !Ch && rp.eq == 1 && !rp.first;
+  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(Ch ? u_prev : u_cur, S, g, stw, tw, NR,
+                                                        extrap ? u_prev : nullptr, T(0.5));
   if (ev) cudaEventRecord(ev[1], st);
   cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
   if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
-  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch,
-                                                          Cl);
+  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, u_prev, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
+                                                          NR, Ch, Cl);
   if (ev) cudaEventRecord(ev[3], st);
   if (transposed_y_sweep<T>(u_lo)) {
     // FP32 compensated form: the y sweep on rows of W^T (S is free scratch)
@@ -735,10 +757,10 @@ cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const 
   if (ev) cudaEventRecord(ev[2], st);
   if (wide_rows<T>(g))
     k_rows_solve<T, true, 2 * kThreads><<<rblocks, 2 * kThreads, NR * vbytes, st>>>(
-        S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
+        S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
   else
-    k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR,
-                                                                   Ch, Cl, Bh, Bl, ldp);
+    k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
+                                                                   NR, Ch, Cl, Bh, Bl, ldp);
   return cudaGetLastError();
 }
 

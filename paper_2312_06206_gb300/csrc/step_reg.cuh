@@ -25,9 +25,10 @@ using rf::static_for;
 // g(u) of the FP32 register path.  -sin u uses the hardware approximation:
 // its absolute error (about 2^-21 on [-pi, pi], growing slowly with |u|) is
 // scaled by tau^2 in B^n, far below the FP32 rounding of B^n itself.
-__device__ __forceinline__ float g_of_r(int kind, float u) {
-  if (kind == 1) return -u * u * u;
-  if (kind == 2) return -__sinf(u);
+__device__ __forceinline__ float g_of_r(const RegInst& I, float u) {
+  if (I.gkind == 1) return -u * u * u;
+  if (I.gkind == 2) return -__sinf(u);
+  if (I.gkind == 3) return (I.gc1 + I.gc3 * u * u) * u + I.gcs * __sinf(u);
   return 0.f;
 }
 
@@ -403,12 +404,17 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   __syncwarp();
   // B^n in place: sm[n] holds the convolution at 2n, 2n+1 (real view).  The
   // remainder pairs of four q are loaded before any of them is stored (the
-  // loads overlap instead of waiting one after another).
+  // loads overlap instead of waiting one after another).  The convolution is
+  // that of the increment d^n; the wave step takes B = C + tau^2 (g(u) + f)
+  // (n = 0: tau phi2 + (C + tau^2 (g + f))/2) with C <- C + conv, the
+  // diffusion step B = C + conv/2 + tau (g(u~) + f) - d, u~ = u + d/2
+  // (C + conv/2 = -kappa tau L_h u~; d = 0 at n = 0).
   const float tau = I.tau, tau2 = I.tau2;
+  const bool diff = I.eq == 1;
   const size_t rbase = (size_t)rrow * N;
 #pragma unroll 1
   for (int q0 = 0; q0 < F::E; q0 += 4) {
-    float ch[8], cl[8], uv[8];
+    float ch[8], cl[8], uv[8], dv[8];
 #pragma unroll
     for (int j = 0; j < 8; ++j) {
       const int x = 2 * (t + F::TT * (q0 + (j >> 1))) + (j & 1);
@@ -416,6 +422,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
       ch[j] = ok ? I.C_hi[rbase + x] : 0.f;
       cl[j] = ok ? I.C_lo[rbase + x] : 0.f;
       uv[j] = ok ? I.u_hi[rbase + x] : 0.f;
+      dv[j] = (ok && diff && !I.first) ? I.u_d[rbase + x] : 0.f;
     }
 #pragma unroll
     for (int j2 = 0; j2 < 4; ++j2) {
@@ -435,10 +442,14 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
           const float c = s + l2;
           I.C_hi[rbase + x] = c;
           I.C_lo[rbase + x] = l2 - (c - s);
-          float gs = g_of_r(I.gkind, uv[2 * j2 + e]);
-          if (I.F) gs += I.fsc * I.F[rbase + x];
-          const float gg = tau2 * gs;
-          b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
+          const float fs = I.F ? I.fsc * I.F[rbase + x] : 0.f;
+          if (!diff) {
+            const float gg = tau2 * (g_of_r(I, uv[2 * j2 + e]) + fs);
+            b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
+          } else {
+            const float d = dv[2 * j2 + e];
+            b[e] = (c + 0.5f * cx) + tau2 * (g_of_r(I, uv[2 * j2 + e] + 0.5f * d) + fs) - d;
+          }
         }
       }
       sm[pad32(n)] = make_float2(b[0], b[1]);

@@ -19,7 +19,7 @@ SADI_OK, SADI_EINVAL, SADI_ENOMEM, SADI_ECUDA, SADI_ENOTSPD, SADI_ESTATE, SADI_E
     SADI_ENONFINITE, SADI_EUNSUPPORTED = range(9)
 STATUS_NAMES = {0: "SADI_OK", 1: "SADI_EINVAL", 2: "SADI_ENOMEM", 3: "SADI_ECUDA", 4: "SADI_ENOTSPD",
                 5: "SADI_ESTATE", 6: "SADI_ETIMEOUT", 7: "SADI_ENONFINITE", 8: "SADI_EUNSUPPORTED"}
-SADI_G_ZERO, SADI_G_NEG_CUBE, SADI_G_NEG_SIN = 0, 1, 2
+SADI_G_ZERO, SADI_G_NEG_CUBE, SADI_G_NEG_SIN, SADI_G_GENERAL = 0, 1, 2, 3
 SADI_PREC_FP64, SADI_PREC_FP32, SADI_PREC_FP32_DENSE = 0, 1, 2
 SADI_PREC_AUTO = -1
 
@@ -27,6 +27,9 @@ SADI_PREC_AUTO = -1
 _SIGS = {
     "sadi_create": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
                               C.POINTER(C.c_void_p)]),
+    "sadi_create_diffusion": (C.c_int, [C.c_int, C.c_double, C.c_double, C.c_double, C.POINTER(C.c_double),
+                                        C.POINTER(C.c_void_p)]),
+    "sadi_get_equation": (C.c_int, [C.c_void_p, C.POINTER(C.c_int)]),
     "sadi_set_options": (C.c_int, [C.c_void_p, C.c_int, C.c_int]),
     "sadi_get_options": (C.c_int, [C.c_void_p, C.POINTER(C.c_int), C.POINTER(C.c_int)]),
     "sadi_set_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_double, C.c_double]),
@@ -58,6 +61,8 @@ _SIGS = {
     "sadi_tuning_log": (C.c_char_p, [C.c_void_p]),
     "sadi_step_noalloc": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_longlong]),
     "sadi_set_watchdog": (C.c_int, [C.c_void_p, C.c_int]),
+    "sadi_set_nonlinearity": (C.c_int, [C.c_void_p, C.c_double, C.c_double, C.c_double]),
+    "sadi_step_source": (C.c_int, [C.c_void_p, C.c_void_p, C.c_int]),
     "sadi_get_watchdog": (C.c_int, [C.c_void_p, C.POINTER(C.c_double), C.POINTER(C.c_longlong)]),
     "sadi_debug_expire_waits": (C.c_int, [C.c_void_p, C.c_longlong]),
     "sadi_batch_create": (C.c_int, [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
@@ -271,17 +276,27 @@ class SadiBatch:
 class Sadi:
     """One S-ADI instance (wraps a sadi_ctx*)."""
 
-    def __init__(self, N: int, alpha: float, kappa: float, tau: float, domain=(-1.0, 1.0)):
+    def __init__(self, N: int, alpha: float, kappa: float, tau: float, domain=(-1.0, 1.0),
+                 equation: str = "wave"):
+        """equation: "wave" (sadi_create) or "diffusion" (sadi_create_diffusion)."""
         self.N = int(N)
         dom = (C.c_double * 2)(float(domain[0]), float(domain[1]))
         out = C.c_void_p()
-        st = lib().sadi_create(self.N, float(alpha), float(kappa), float(tau), dom, C.byref(out))
+        if equation not in ("wave", "diffusion"):
+            raise ValueError(f"unknown equation {equation!r}")
+        create = lib().sadi_create if equation == "wave" else lib().sadi_create_diffusion
+        st = create(self.N, float(alpha), float(kappa), float(tau), dom, C.byref(out))
         _check(st, None)
         self.ctx = out.value
 
     # -- C ABI calls, same names -------------------------------------------
     def sadi_set_options(self, g: int = SADI_G_ZERO, prec: int = SADI_PREC_FP64):
         _check(lib().sadi_set_options(self.ctx, int(g), int(prec)), self.ctx)
+
+    def sadi_get_equation(self) -> int:
+        e = C.c_int()
+        _check(lib().sadi_get_equation(self.ctx, C.byref(e)), self.ctx)
+        return e.value
 
     def sadi_get_options(self):
         g, p = C.c_int(), C.c_int()
@@ -359,6 +374,13 @@ class Sadi:
         """One step on caller-owned device buffers (N*N doubles each); no allocation."""
         _check(lib().sadi_step_noalloc(self.ctx, C.c_void_p(u_prev_ptr), C.c_void_p(u_cur_ptr),
                                        C.c_void_p(u_next_ptr), int(n)), self.ctx)
+
+    def sadi_set_nonlinearity(self, c1: float, c3: float, cs: float):
+        _check(lib().sadi_set_nonlinearity(self.ctx, float(c1), float(c3), float(cs)), self.ctx)
+
+    def sadi_step_source(self, f_ptr: int, dtype: int = 0):
+        """One step with the source field at device address f_ptr (N*N of dtype 0 double / 1 float)."""
+        _check(lib().sadi_step_source(self.ctx, C.c_void_p(f_ptr), int(dtype)), self.ctx)
 
     def sadi_set_watchdog(self, every: int):
         _check(lib().sadi_set_watchdog(self.ctx, int(every)), self.ctx)
