@@ -395,6 +395,9 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
   const uint32_t mdone = su32(bars + 2 * STAGES + 4);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t limit = bt.wait_ns ? bt.wait_ns : WAIT_LIMIT_NS;
+  // the next step's first kernel (a programmatic dependent) may be scheduled
+  // onto SMs as these CTAs exit; it waits for this grid before reading
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {

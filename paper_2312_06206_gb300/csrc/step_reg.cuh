@@ -11,6 +11,7 @@
 // X[0] + i X[N']); all spectral tables are natural-order copies of the FP64
 // setup products.
 #pragma once
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "bf16split.cuh"
@@ -113,6 +114,15 @@ __device__ __forceinline__ void cp_async16(void* dst, const void* src, bool pred
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
+// Programmatic dependent launch.  The step's kernels are launched with
+// programmatic stream serialisation: a kernel may start once every block of
+// the kernel before it has started (each signals that at its beginning),
+// stages its constant tables, and waits for the earlier kernel to have
+// completed, its writes visible, before it reads anything that kernel (or an
+// earlier one) writes.  Launched without that attribute both are no-ops.
+__device__ __forceinline__ void pdl_allow_dependents() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+__device__ __forceinline__ void pdl_wait_prerequisites() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
 // The twiddle tables tw1 (two-level FFT) and tw[0 .. L) staged into shared
 // memory (one cp.async group): the transforms read them in their inner
 // stages, where global (L1) loads would stall the few resident warps.
@@ -200,6 +210,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   using F = rf::RegFFT<float, LOGL>;
   using C = RowCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_allow_dependents();
   const RegInst& I = B.in[blockIdx.y];
   const int N = I.N;
   if ((int)blockIdx.x * C::VB >= N) return;
@@ -211,6 +222,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   float2* s_tw = s_tw1 + F::L;
   stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
   cp_async_commit();
+  pdl_wait_prerequisites();
   // the increment d^n = u^n - u^{n-1} (zero before the first step): the
   // remainder is advanced incrementally
   const float* ur = I.u_d + (size_t)(valid ? row : 0) * N;
@@ -255,6 +267,7 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   using F = rf::RegFFT<float, LOGL>;
   using C = ConvCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_allow_dependents();
   const RegInst& I = B.in[blockIdx.y];
   const int N = I.N, Np = F::L;
   const int c = threadIdx.x / F::TT, t = threadIdx.x % F::TT;
@@ -278,6 +291,7 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   // each item's column, rows 0 .. N-1 (zero-filled to L), once, into the
   // buffer of its even-half vector: thread -> (item, row) with the items
   // fastest, so that a warp's copies cover whole row segments
+  pdl_wait_prerequisites();
   constexpr int NI = C::CT / 2;
   for (int e = threadIdx.x; e < NI * F::L; e += BLOCK) {
     const int ci = e % NI, j = e / NI, it = item_of(2 * ci);
@@ -340,6 +354,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   using F = rf::RegFFT<float, LOGL>;
   using C = RowCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_allow_dependents();
   const RegInst& I = B.in[blockIdx.y];
   const int N = I.N, Np = F::L;
   if ((int)blockIdx.x * C::VB >= N) return;
@@ -351,6 +366,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   float2* s_tw1 = reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV;
   float2* s_tw = s_tw1 + F::L;
   stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
+  pdl_wait_prerequisites();
   // stage the spectrum row (u^n, and phi2 on the first step, are read in the
   // B^n epilogue together with the remainder)
   const float2* srow = I.S + (size_t)rrow * Np;
@@ -410,51 +426,60 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   // diffusion step B = C + conv/2 + tau (g(u~) + f) - d, u~ = u + d/2
   // (C + conv/2 = -kappa tau L_h u~; d = 0 at n = 0).
   const float tau = I.tau, tau2 = I.tau2;
-  const bool diff = I.eq == 1;
   const size_t rbase = (size_t)rrow * N;
+  // the equation is uniform over the launch: one loop per equation, so the
+  // wave step's loop carries nothing of the diffusion step's
+  auto bn_loop = [&](auto diff_c) {
+    constexpr bool DIFF = decltype(diff_c)::value;
 #pragma unroll 1
-  for (int q0 = 0; q0 < F::E; q0 += 4) {
-    float ch[8], cl[8], uv[8], dv[8];
+    for (int q0 = 0; q0 < F::E; q0 += 4) {
+      float ch[8], cl[8], uv[8], dv[8];
 #pragma unroll
-    for (int j = 0; j < 8; ++j) {
-      const int x = 2 * (t + F::TT * (q0 + (j >> 1))) + (j & 1);
-      const bool ok = valid && x < N;
-      ch[j] = ok ? I.C_hi[rbase + x] : 0.f;
-      cl[j] = ok ? I.C_lo[rbase + x] : 0.f;
-      uv[j] = ok ? I.u_hi[rbase + x] : 0.f;
-      dv[j] = (ok && diff && !I.first) ? I.u_d[rbase + x] : 0.f;
-    }
+      for (int j = 0; j < 8; ++j) {
+        const int x = 2 * (t + F::TT * (q0 + (j >> 1))) + (j & 1);
+        const bool ok = valid && x < N;
+        ch[j] = ok ? I.C_hi[rbase + x] : 0.f;
+        cl[j] = ok ? I.C_lo[rbase + x] : 0.f;
+        uv[j] = ok ? I.u_hi[rbase + x] : 0.f;
+        if constexpr (DIFF) dv[j] = (ok && !I.first) ? I.u_d[rbase + x] : 0.f;
+      }
 #pragma unroll
-    for (int j2 = 0; j2 < 4; ++j2) {
-      const int n = t + F::TT * (q0 + j2);
-      const float2 cv = sm[pad32(n)];
-      float b[2] = {0.f, 0.f};
+      for (int j2 = 0; j2 < 4; ++j2) {
+        const int n = t + F::TT * (q0 + j2);
+        const float2 cv = sm[pad32(n)];
+        float b[2] = {0.f, 0.f};
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const int x = 2 * n + e;
-        if (valid && x < N) {
-          // C <- C + conv (two-sum into the double-float pair)
-          const float hi = ch[2 * j2 + e], lo = cl[2 * j2 + e], cx = e ? cv.y : cv.x;
-          const float s = hi + cx;
-          const float bb = s - hi;
-          const float err = (hi - (s - bb)) + (cx - bb);
-          const float l2 = lo + err;
-          const float c = s + l2;
-          I.C_hi[rbase + x] = c;
-          I.C_lo[rbase + x] = l2 - (c - s);
-          const float fs = I.F ? I.fsc * I.F[rbase + x] : 0.f;
-          if (!diff) {
-            const float gg = tau2 * (g_of_r(I, uv[2 * j2 + e]) + fs);
-            b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
-          } else {
-            const float d = dv[2 * j2 + e];
-            b[e] = (c + 0.5f * cx) + tau2 * (g_of_r(I, uv[2 * j2 + e] + 0.5f * d) + fs) - d;
+        for (int e = 0; e < 2; ++e) {
+          const int x = 2 * n + e;
+          if (valid && x < N) {
+            // C <- C + conv (two-sum into the double-float pair)
+            const float hi = ch[2 * j2 + e], lo = cl[2 * j2 + e], cx = e ? cv.y : cv.x;
+            const float s = hi + cx;
+            const float bb = s - hi;
+            const float err = (hi - (s - bb)) + (cx - bb);
+            const float l2 = lo + err;
+            const float c = s + l2;
+            I.C_hi[rbase + x] = c;
+            I.C_lo[rbase + x] = l2 - (c - s);
+            if constexpr (!DIFF) {
+              float gs = g_of_r(I, uv[2 * j2 + e]);
+              if (I.F) gs += I.fsc * I.F[rbase + x];
+              const float gg = tau2 * gs;
+              b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
+            } else {
+              const float d = dv[2 * j2 + e];
+              float gs = g_of_r(I, uv[2 * j2 + e] + 0.5f * d);
+              if (I.F) gs += I.fsc * I.F[rbase + x];
+              b[e] = (c + 0.5f * cx) + tau2 * gs - d;
+            }
           }
         }
+        sm[pad32(n)] = make_float2(b[0], b[1]);
       }
-      sm[pad32(n)] = make_float2(b[0], b[1]);
     }
-  }
+  };
+  if (I.eq == 1) bn_loop(std::integral_constant<bool, true>{});
+  else bn_loop(std::integral_constant<bool, false>{});
   __syncwarp();
   if constexpr (DENSE) {
     if (!valid) return;
@@ -513,6 +538,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
   using F = rf::RegFFT<float, LOGL>;
   using C = ColCfg<LOGL, BLOCK>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_allow_dependents();
   const RegInst& I = B.in[blockIdx.y];
   const int N = I.N, Np = F::L;
   if ((int)blockIdx.x * C::CT >= N) return;
@@ -531,6 +557,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
   float2* s_tw = s_tw1 + F::L;
   stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
   cp_async_commit();
+  pdl_wait_prerequisites();
   // the state column (needed at the end) is staged asynchronously; the W
   // column (needed now) is loaded straight into registers, all loads in flight
   static_for<0, F::E>([&](auto qc) {
@@ -677,23 +704,40 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
     for (int k = 0; k < 3; ++k)
       wide[k] = fewer_waves(shape[k][dev].load(std::memory_order_relaxed), b.count, max_n, RC::VB, RW::VB);
   const dim3 wgrid((max_n + RW::VB - 1) / RW::VB, b.count);
+  // every kernel of the step is a programmatic dependent of the one before it
+  // in the stream (see pdl_wait_prerequisites)
+  cudaLaunchAttribute pdl[1];
+  pdl[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  pdl[0].val.programmaticStreamSerializationAllowed = 1;
+  auto launch = [&](auto kernel, dim3 grid, int block, size_t smem) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(block);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cfg.attrs = pdl;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, b);
+  };
+  cudaError_t e;
   if (ev) cudaEventRecord(ev[0], st);
-  if (wide[0]) kr_rows_r2c<LOGL, kRowBlockWide><<<wgrid, kRowBlockWide, RW::bytes_r2c, st>>>(b);
-  else kr_rows_r2c<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_r2c, st>>>(b);
+  if (wide[0]) e = launch(kr_rows_r2c<LOGL, kRowBlockWide>, wgrid, kRowBlockWide, RW::bytes_r2c);
+  else e = launch(kr_rows_r2c<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_r2c);
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], st);
-  kr_cols_conv<LOGL, kConvBlock><<<cgrid, kConvBlock, VC::bytes, st>>>(b);
+  if ((e = launch(kr_cols_conv<LOGL, kConvBlock>, cgrid, kConvBlock, VC::bytes))) return e;
   if (ev) cudaEventRecord(ev[2], st);
   if (dense) {
-    if (wide[2]) kr_rows_solve<LOGL, kRowBlockWide, true><<<wgrid, kRowBlockWide, RW::bytes_solve, st>>>(b);
-    else kr_rows_solve<LOGL, kRowBlock, true><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
-    return cudaGetLastError();
+    if (wide[2]) return launch(kr_rows_solve<LOGL, kRowBlockWide, true>, wgrid, kRowBlockWide, RW::bytes_solve);
+    return launch(kr_rows_solve<LOGL, kRowBlock, true>, rgrid, kRowBlock, RC::bytes_solve);
   }
-  if (wide[1]) kr_rows_solve<LOGL, kRowBlockWide><<<wgrid, kRowBlockWide, RW::bytes_solve, st>>>(b);
-  else kr_rows_solve<LOGL, kRowBlock><<<rgrid, kRowBlock, RC::bytes_solve, st>>>(b);
+  if (wide[1]) e = launch(kr_rows_solve<LOGL, kRowBlockWide>, wgrid, kRowBlockWide, RW::bytes_solve);
+  else e = launch(kr_rows_solve<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_solve);
+  if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[3], st);
-  kr_cols_solve<LOGL, kColBlock><<<sgrid, kColBlock, CC::bytes_solve, st>>>(b);
+  if ((e = launch(kr_cols_solve<LOGL, kColBlock>, sgrid, kColBlock, CC::bytes_solve))) return e;
   if (ev) cudaEventRecord(ev[4], st);
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 }  // namespace regk
