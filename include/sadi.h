@@ -258,9 +258,12 @@ sadi_status sadi_load_state(sadi_ctx *ctx, const void *buf, size_t bytes);
  * CUDA graph on the first context's stream; nothing runs at capture time and
  * the contexts' step counters are unchanged.  Requirements (SADI_ESTATE /
  * SADI_EINVAL / SADI_EUNSUPPORTED otherwise): every context initialised and
- * past its n = 0 step (n >= 1), FP32 or FP32_DENSE precision (their state is
- * updated in place, so one captured step fits every later step), no source
- * term, profiling off, all contexts on one stream, distinct.
+ * past its n = 0 step (n >= 1), no source term, profiling off, all contexts
+ * on one stream, distinct.  FP32 and FP32_DENSE contexts update their state
+ * in place, so one captured step fits every later step; FP64 contexts keep
+ * u^n and u^{n-1} in two buffers that swap every step, so they need an even
+ * nsteps, and a launch after an odd number of other steps since the capture
+ * returns SADI_ESTATE.
  * sadi_graph_launch replays the graph reps >= 0 times (asynchronous) and
  * advances every context's n by nsteps * reps; it re-checks the requirements
  * first.  The graph holds the contexts' device pointers: destroy it before

@@ -4,9 +4,10 @@
 //
 // The members are ordinary contexts on one stream.  sadi_batch_run advances
 // them with the batched launches of sadi_batch_step and, once every member
-// is past its n = 0 step and the members allow it (FP32 forms, no source
-// term, no profiling), by replaying a CUDA graph of one batched step that is
-// captured on first use and kept until a member's set-up changes.
+// is past its n = 0 step and the members allow it (no source term, no
+// profiling), by replaying a CUDA graph of one batched step (two when a
+// member is FP64) that is captured on first use and kept until a member's
+// set-up changes.
 #include <cuda_runtime.h>
 
 #include <string>
@@ -20,7 +21,8 @@ using namespace sadi_api;
 struct sadi_batch {
   std::vector<sadi_ctx*> ctxs;
   cudaStream_t own_stream = nullptr;
-  sadi_graph* graph = nullptr;      // one batched step, captured on first use
+  sadi_graph* graph = nullptr;      // gsteps batched steps, captured on first use
+  int gsteps = 1;                   // 2 when a member is FP64 (its buffers swap every step)
   bool graph_failed = false;        // the members cannot be replayed: launch directly
   std::string err;
 };
@@ -131,8 +133,17 @@ sadi_status sadi_batch_run(sadi_batch* b, int nsteps) {
   while (nsteps > 0) {
     bool fresh = false;   // a member still takes its n = 0 step
     for (int k = 0; k < count; ++k) fresh = fresh || cs[k]->n == 0;
-    if (fresh || b->graph_failed) {
+    bool fp64 = false;
+    for (int k = 0; k < count; ++k) fp64 = fp64 || cs[k]->prec == SADI_PREC_FP64;
+    const int gsteps = fp64 ? 2 : 1;
+    if (fresh || b->graph_failed || nsteps < gsteps) {
       const int m = fresh ? 1 : nsteps;
+      // a direct step swaps FP64 buffers: a graph captured before is replayed
+      // only after an even number of them, so capture anew
+      if (fp64 && (m % 2) != 0 && b->graph) {
+        sadi_graph_destroy(b->graph);
+        b->graph = nullptr;
+      }
       const sadi_status st = sadi_batch_step(cs, count, m);
       if (st != SADI_OK) {
         for (int k = 0; k < count; ++k)
@@ -142,8 +153,10 @@ sadi_status sadi_batch_run(sadi_batch* b, int nsteps) {
       nsteps -= m;
       continue;
     }
+    if (b->graph && b->gsteps != gsteps) drop_graph(b);
     if (!b->graph) {
-      const sadi_status st = sadi_graph_create(cs, count, 1, &b->graph);
+      b->gsteps = gsteps;
+      const sadi_status st = sadi_graph_create(cs, count, gsteps, &b->graph);
       if (st == SADI_EUNSUPPORTED || st == SADI_ESTATE) {
         // FP64 members, a source term or profiling: direct launches
         b->graph = nullptr;
@@ -153,14 +166,14 @@ sadi_status sadi_batch_run(sadi_batch* b, int nsteps) {
       }
       if (st != SADI_OK) return bfail(b, st, "sadi_batch_run: graph capture failed");
     }
-    const sadi_status st = sadi_graph_launch(b->graph, nsteps);
+    const sadi_status st = sadi_graph_launch(b->graph, nsteps / gsteps);
     if (st != SADI_OK) {
       drop_graph(b);
       for (int k = 0; k < count; ++k)
         if (*sadi_last_error(cs[k])) return member_fail(b, k, st);
       return bfail(b, st, "sadi_batch_run: graph launch failed");
     }
-    nsteps = 0;
+    nsteps %= gsteps;   // an odd last step of FP64 members: directly, above
   }
   return SADI_OK;
 }

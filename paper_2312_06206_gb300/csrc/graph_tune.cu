@@ -16,6 +16,7 @@ using namespace sadi_api;
 
 struct sadi_graph {
   std::vector<sadi_ctx*> ctxs;
+  std::vector<int> cur;   // FP64 contexts: which ping-pong buffer held u^n at capture
   int nsteps = 0;
   cudaStream_t stream = nullptr;
   cudaGraph_t graph = nullptr;
@@ -24,13 +25,20 @@ struct sadi_graph {
 
 namespace {
 
-sadi_status graph_check(sadi_ctx* const* ctxs, int count, bool launching) {
+// nsteps: steps per replay.  An FP64 context keeps u^n and u^{n-1} in two
+// buffers that swap every step, so it replays only in graphs of an even
+// number of steps, launched with the buffers as they were at capture (cur,
+// when launching).
+sadi_status graph_check(sadi_ctx* const* ctxs, int count, bool launching, int nsteps, const int* cur = nullptr) {
   cudaStream_t s0 = ctxs[0]->stream;
   for (int k = 0; k < count; ++k) {
     sadi_ctx* c = ctxs[k];
     sadi_status st = check_steppable(c);
     if (st != SADI_OK) return st;
-    if (c->prec == SADI_PREC_FP64) return fail(c, SADI_EUNSUPPORTED, "graphs replay the FP32 forms only");
+    if (c->prec == SADI_PREC_FP64 && nsteps % 2 != 0)
+      return fail(c, SADI_EUNSUPPORTED, "FP64 contexts replay in graphs of an even number of steps only");
+    if (c->prec == SADI_PREC_FP64 && cur && c->cur != cur[k])
+      return fail(c, SADI_ESTATE, "an odd number of steps since the capture: the FP64 buffers are swapped");
     if (c->n < 1) return fail(c, SADI_ESTATE, "take the n = 0 step before capturing or launching a graph");
     if (c->F) return fail(c, SADI_EUNSUPPORTED, "a source term changes every step; it cannot be replayed");
     if (c->profiling) return fail(c, SADI_ESTATE, "disable sadi_profile before capturing a graph");
@@ -59,15 +67,18 @@ sadi_status sadi_graph_create(sadi_ctx** ctxs, int count, int nsteps, sadi_graph
   if (!ctxs || count < 1 || nsteps < 1) return SADI_EINVAL;
   for (int k = 0; k < count; ++k)
     if (!ctxs[k]) return SADI_EINVAL;
-  sadi_status st = graph_check(ctxs, count, false);
+  sadi_status st = graph_check(ctxs, count, false, nsteps);
   if (st != SADI_OK) return st;
   sadi_graph* g = new (std::nothrow) sadi_graph();
   if (!g) return fail(ctxs[0], SADI_ENOMEM, "host allocation failed");
   g->ctxs.assign(ctxs, ctxs + count);
+  for (int k = 0; k < count; ++k) g->cur.push_back(ctxs[k]->cur);
   g->nsteps = nsteps;
   g->stream = ctxs[0]->stream;
   std::vector<long long> n0(count);
   for (int k = 0; k < count; ++k) n0[k] = ctxs[k]->n;
+  // the capture issues the steps without running them: the FP64 buffer swaps
+  // it makes are undone below, with the step counters
   cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
   if (e != cudaSuccess) {
     delete g;
@@ -75,7 +86,10 @@ sadi_status sadi_graph_create(sadi_ctx** ctxs, int count, int nsteps, sadi_graph
   }
   st = batch_issue(ctxs, count, nsteps);
   e = cudaStreamEndCapture(g->stream, &g->graph);
-  for (int k = 0; k < count; ++k) ctxs[k]->n = n0[k];
+  for (int k = 0; k < count; ++k) {
+    ctxs[k]->n = n0[k];
+    ctxs[k]->cur = g->cur[k];
+  }
   if (st == SADI_OK && e != cudaSuccess) st = cuda_fail(ctxs[0], e, "cudaStreamEndCapture");
   if (st == SADI_OK) {
     e = cudaGraphInstantiate(&g->exec, g->graph, 0);
@@ -92,7 +106,7 @@ sadi_status sadi_graph_create(sadi_ctx** ctxs, int count, int nsteps, sadi_graph
 
 sadi_status sadi_graph_launch(sadi_graph* g, int reps) {
   if (!g || reps < 0) return SADI_EINVAL;
-  sadi_status st = graph_check(g->ctxs.data(), (int)g->ctxs.size(), true);
+  sadi_status st = graph_check(g->ctxs.data(), (int)g->ctxs.size(), true, g->nsteps, g->cur.data());
   if (st != SADI_OK) return st;
   for (int r = 0; r < reps; ++r) {
     const cudaError_t e = cudaGraphLaunch(g->exec, g->stream);

@@ -289,8 +289,8 @@ sadi_status create_impl(int eq, int N, double alpha, double kappa, double tau, c
     return bail(cuda_fail(c, e, "register-path tables"));
   if ((e = step_setup_attributes<float>())) return bail(cuda_fail(c, e, "kernel attributes"));
   if ((e = step_setup_attributes<double>())) return bail(cuda_fail(c, e, "kernel attributes"));
-  c->tiles64 = default_tiles<double>(Np);
-  c->tiles32 = default_tiles<float>(Np);
+  c->tiles64 = default_tiles<double>(Np, N);
+  c->tiles32 = default_tiles<float>(Np, N);
   sadi_status sst = alloc_state(c);
   if (sst != SADI_OK) return bail(sst);
   if ((e = cudaStreamSynchronize(st))) return bail(cuda_fail(c, e, "setup"));
@@ -416,11 +416,11 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
     // engine applies (N' <= 4096), else FP32 from the hi part
     if (c->g.Np <= 4096) {
       StepTables<double> tb{c->stw64, c->tw64, c->lpb64, c->lams64, c->lamc64, c->G64};
-      CK(launch_remainder<double>(c->g, tb, default_tiles<double>(c->g.Np), c->stage, c->S, c->Chi, c->Clo, st),
+      CK(launch_remainder<double>(c->g, tb, default_tiles<double>(c->g.Np, c->g.N), c->stage, c->S, c->Chi, c->Clo, st),
          "starting remainder");
     } else {
       StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32, c3_of(c)};
-      CK(launch_remainder<float>(c->g, tb, default_tiles<float>(c->g.Np), static_cast<const float*>(c->ubuf[0]),
+      CK(launch_remainder<float>(c->g, tb, default_tiles<float>(c->g.Np, c->g.N), static_cast<const float*>(c->ubuf[0]),
                                  c->S, c->Chi, c->Clo, st),
          "starting remainder");
     }
@@ -964,7 +964,7 @@ sadi_status sadi_set_tiles(sadi_ctx* c, int rows, int conv_cols, int solve_cols)
   Tiles t{rows, conv_cols, solve_cols};
   const bool f64 = c->prec == SADI_PREC_FP64;
   if (rows == 0 && conv_cols == 0 && solve_cols == 0)
-    t = f64 ? default_tiles<double>(c->g.Np) : default_tiles<float>(c->g.Np);
+    t = f64 ? default_tiles<double>(c->g.Np, c->g.N) : default_tiles<float>(c->g.Np, c->g.N);
   const bool ok = f64 ? tiles_valid<double>(c->g, t) : tiles_valid<float>(c->g, t);
   if (!ok) return fail(c, SADI_EINVAL, "tile sizes invalid for this N and precision");
   if (!f64 && t.conv_cols == kConvThreePass) {

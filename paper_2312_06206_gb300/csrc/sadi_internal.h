@@ -119,8 +119,13 @@ struct Tiles {
 // conv_cols value selecting the three-pass column convolution (conv3.cu)
 constexpr int kConvThreePass = -1;
 
+// Default work decomposition for FFT length Np; with N (the grid size) the
+// row and column tiles are also capped so that a launch has about
+// kSmallTileBlocks blocks or more where N allows it (small problems are
+// latency-bound: spread them over the SMs).
+constexpr int kSmallTileBlocks = 128;
 template <typename T>
-Tiles default_tiles(int Np);
+Tiles default_tiles(int Np, int N = 0);
 template <typename T>
 bool tiles_valid(const Geom& g, const Tiles& t);
 

@@ -589,7 +589,7 @@ cudaError_t step_setup_attributes() {
 }
 
 template <typename T>
-Tiles default_tiles(int Np) {
+Tiles default_tiles(int Np, int N) {
   // rows per block of the row kernels and slots/columns per block of the
   // column kernels: about two resident blocks of 256 threads per SM at N' = 1024
   const int es = (int)sizeof(T) / 4;   // 1 (float) or 2 (double)
@@ -602,6 +602,13 @@ Tiles default_tiles(int Np) {
   if (t.solve_cols < 1) t.solve_cols = 1;
   if (t.conv_cols > 8) t.conv_cols = 8;
   if (t.solve_cols > 16) t.solve_cols = 16;
+  if (N > 0) {
+    const int cap = (N + kSmallTileBlocks - 1) / kSmallTileBlocks;   // rows or columns per block
+    if (t.rows > cap) t.rows = cap;
+    if (t.solve_cols > cap) t.solve_cols = cap;
+    const int ccap = Np / kSmallTileBlocks > 1 ? Np / kSmallTileBlocks : 1;   // a power of two
+    if (t.conv_cols > ccap) t.conv_cols = ccap;
+  }
   // FP32 at N' = 8192: the three-pass column convolution (conv_cols = -1)
   if (sizeof(T) == 4 && Np == 8192) t.conv_cols = kConvThreePass;
   return t;
@@ -703,8 +710,8 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
 
 template cudaError_t step_setup_attributes<float>();
 template cudaError_t step_setup_attributes<double>();
-template Tiles default_tiles<float>(int);
-template Tiles default_tiles<double>(int);
+template Tiles default_tiles<float>(int, int);
+template Tiles default_tiles<double>(int, int);
 template bool tiles_valid<float>(const Geom&, const Tiles&);
 template bool tiles_valid<double>(const Geom&, const Tiles&);
 template cudaError_t launch_step<float>(const Geom&, const StepTables<float>&, const Tiles&, const RhsParams&,

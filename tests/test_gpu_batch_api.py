@@ -88,3 +88,51 @@ def test_batch_argument_errors(S):
         with pytest.raises(S.SadiError) as ei:
             b.get(0)
         assert ei.value.status == S.SADI_ESTATE
+
+
+def test_fp64_graph_replays_even_step_counts(S):
+    # FP64 buffers swap every step: graphs of an even number of steps replay
+    # bitwise what direct steps give; odd counts are refused, and so is a
+    # launch after an odd number of direct steps since the capture
+    import torch
+    N = 127
+    phi1 = WL.gaussian_bumps(N, 4, WL.SEED_BASE + 75)
+    stream = torch.cuda.Stream()
+
+    def ctx():
+        s = S.Sadi(N, 1.6, 1.0, 1.0 / (N + 1))
+        s.set_stream(stream.cuda_stream)
+        s.set_options(1, S.SADI_PREC_FP64)
+        s.set_initial(phi1)
+        s.step(1)
+        return s
+    with ctx() as a, ctx() as b:
+        with pytest.raises(S.SadiError) as ei:
+            S.SadiGraph([a], 3)
+        assert ei.value.status == S.SADI_EUNSUPPORTED
+        g = S.SadiGraph([a], 2)
+        g.launch(5)
+        b.step(10)
+        ua, na = a.get()
+        ub, nb = b.get()
+        assert na == nb == 11 and np.array_equal(ua, ub)
+        a.step(1)
+        with pytest.raises(S.SadiError) as ei:
+            g.launch(1)
+        assert ei.value.status == S.SADI_ESTATE
+        a.step(1)
+        g.launch(1)
+        b.step(4)
+        assert np.array_equal(a.get()[0], b.get()[0])
+        g.close()
+    # the batch handle replays FP64 members in two-step graphs, an odd tail directly
+    with S.SadiBatch([63, 127], [1.4, 1.6], [1.0, 1.0], [1 / 64, 1 / 128], g=1, prec=S.SADI_PREC_FP64) as bt:
+        for k, n in enumerate((63, 127)):
+            bt.set_initial(k, WL.gaussian_bumps(n, 3, WL.SEED_BASE + 76 + k))
+        bt.run(7)
+        bt.run(4)
+        for k, n in enumerate((63, 127)):
+            ref, _ = _alone(S, n, [1.4, 1.6][k], 1.0, [1 / 64, 1 / 128][k], 1, S.SADI_PREC_FP64, None,
+                            WL.gaussian_bumps(n, 3, WL.SEED_BASE + 76 + k), 11)
+            u, m = bt.get(k)
+            assert m == 11 and np.array_equal(u, ref), k
