@@ -145,7 +145,7 @@ struct RegInst {
   float* u_lo;
   float* u_d;
   const float* phi2;
-  float2* S;            // N x N' spectrum scratch
+  float2* S;            // spectrum scratch, slot-major: N' slots x N rows (S[k * N + row])
   float* W;             // N x N sweep scratch
   const float* F;       // optional source field (N x N) or nullptr
   float* C_hi;          // incremental remainder -kappa tau^2 L_h u^n (double-float)

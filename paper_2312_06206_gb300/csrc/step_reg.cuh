@@ -50,7 +50,12 @@ template <int LOGL, int BLOCK>
 struct RowCfg {
   using F = rf::RegFFT<float, LOGL>;
   static constexpr int VB = BLOCK / F::TT;                    // vectors (rows) per block
-  static constexpr int SMV = vec_smem<LOGL>(F::TT & 15);      // transform buffer (float2)
+  // transform buffer (float2).  The spectrum moves between global and shared
+  // memory with the block's rows fastest (slot-major spectrum): 16 threads
+  // then cover 16/VB slots x VB rows (narrow blocks) or 16 consecutive rows of
+  // one slot, and a vector stride of 16/VB resp. 1 (mod 16) float2 gives them
+  // 16 distinct bank pairs
+  static constexpr int SMV = vec_smem<LOGL>(VB < 16 ? (16 / VB) & 15 : 1);
   static constexpr size_t tw_bytes = 2 * (size_t)F::L * sizeof(float2);   // tw1 and tw[0 .. L) staged
   static constexpr size_t bytes_r2c = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
   static constexpr size_t bytes_solve = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
@@ -239,17 +244,20 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   // a row vector belongs to TT threads of one warp: warp barriers from here
   F::template fwd<true>(x, sm, t, s_tw1);
   store_freq<LOGL>(x, sm, t);
-  __syncwarp();
-  if (!valid) return;
-  float2* srow = I.S + (size_t)row * F::L;
-#pragma unroll 2
-  for (int q = 0; q < F::E; ++q) {
-    const int k = t + F::TT * q;
-    const float2 Z = sm[pad32(k)];
-    const float2 Zc = cconj(sm[pad32((F::L - k) & (F::L - 1))]);
+  __syncthreads();
+  // the spectrum is slot-major, S[k * N + row]: the block writes slot by slot,
+  // its rows fastest (runs of VB rows), reading every vector's buffer
+  const float2* base = reinterpret_cast<const float2*>(smem_raw);
+  const int row0 = blockIdx.x * C::VB;
+  for (int e = threadIdx.x; e < C::VB * F::L; e += BLOCK) {
+    const int vv = e % C::VB, k = e / C::VB;
+    if (row0 + vv >= N) continue;
+    const float2* smv = base + vv * C::SMV;
+    const float2 Z = smv[pad32(k)];
+    const float2 Zc = cconj(smv[pad32((F::L - k) & (F::L - 1))]);
     const float2 Ev = cscale(cadd(Z, Zc), 0.5f);
     const float2 Ov = cscale(cmul_mi(csub(Z, Zc)), 0.5f);
-    srow[k] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(s_tw[k], Ov));
+    I.S[(size_t)k * N + row0 + vv] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(s_tw[k], Ov));
   }
 }
 
@@ -289,14 +297,15 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
     cp_async16(s_lam + cc * F::L + 4 * p, src, true);
   }
   // each item's column, rows 0 .. N-1 (zero-filled to L), once, into the
-  // buffer of its even-half vector: thread -> (item, row) with the items
-  // fastest, so that a warp's copies cover whole row segments
+  // buffer of its even-half vector: the spectrum is slot-major (S[k * N + j]),
+  // so a column is contiguous; thread -> (item, row) with the rows fastest
   pdl_wait_prerequisites();
   constexpr int NI = C::CT / 2;
   for (int e = threadIdx.x; e < NI * F::L; e += BLOCK) {
-    const int ci = e % NI, j = e / NI, it = item_of(2 * ci);
+    const int j = e % F::L, ci = e / F::L, it = item_of(2 * ci);
     float2* dst = reinterpret_cast<float2*>(smem_raw) + 2 * ci * C::SMV + pad32(j);
-    cp_async8(dst, I.S + (size_t)(j < N ? j : 0) * Np + slot_of(it), it <= Np && j < N);
+    const bool ok = it <= Np && j < N;
+    cp_async8(dst, I.S + (size_t)(ok ? slot_of(it) : 0) * N + (ok ? j : 0), ok);
   }
   cp_async_commit();
   cp_async_wait_all();
@@ -327,21 +336,22 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   F::template inv<true>(x, sm, t, s_tw1);
   store_nat<LOGL>(x, sm, t);
   __syncthreads();
-  // even + conj-twiddled odd half -> rows 0 .. N-1 of each item's column; the
-  // threads walk (item, row) with the items fastest.  Item 0 also holds the
-  // x-frequency N' result (item 1's pair) in the imaginary part of slot 0.
+  // even + conj-twiddled odd half -> rows 0 .. N-1 of each item's column
+  // (contiguous in the slot-major spectrum); the threads walk (item, row)
+  // with the rows fastest.  Item 0 also holds the x-frequency N' result (item
+  // 1's pair) in the imaginary part of slot 0.
   const float2* base = reinterpret_cast<const float2*>(smem_raw);
   for (int e = threadIdx.x; e < (C::CT / 2) * N; e += BLOCK) {
-    const int i = e % (C::CT / 2), j = e / (C::CT / 2), it = item_of(2 * i);
+    const int j = e % N, i = e / N, it = item_of(2 * i);
     if (it > Np || it == 1) continue;
     const float2 w = twh[j];
     const float2* se = base + (2 * i) * C::SMV;
     const float2 y = cadd(se[pad32(j)], cmulc(se[C::SMV + pad32(j)], w));
     if (it == 0) {
       const float2 yn = cadd(se[2 * C::SMV + pad32(j)], cmulc(se[3 * C::SMV + pad32(j)], w));
-      I.S[(size_t)j * Np] = make_float2(y.x, yn.x);
+      I.S[j] = make_float2(y.x, yn.x);
     } else {
-      I.S[(size_t)j * Np + slot_of(it)] = y;
+      I.S[(size_t)slot_of(it) * N + j] = y;
     }
   }
 }
@@ -367,14 +377,18 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   float2* s_tw = s_tw1 + F::L;
   stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
   pdl_wait_prerequisites();
-  // stage the spectrum row (u^n, and phi2 on the first step, are read in the
-  // B^n epilogue together with the remainder)
-  const float2* srow = I.S + (size_t)rrow * Np;
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    const int k = t + F::TT * q;
-    cp_async8(&sm[pad32(k)], srow + k, valid);
-  });
+  // stage the block's spectrum rows from the slot-major spectrum S[k * N + row]
+  // (slot by slot, rows fastest: runs of VB rows); u^n, and phi2 on the
+  // first step, are read in the B^n epilogue together with the remainder
+  {
+    float2* base = reinterpret_cast<float2*>(smem_raw);
+    const int row0 = blockIdx.x * C::VB;
+    for (int e = threadIdx.x; e < C::VB * F::L; e += BLOCK) {
+      const int vv = e % C::VB, k = e / C::VB;
+      const bool ok = row0 + vv < N;
+      cp_async8(&base[vv * C::SMV + pad32(k)], I.S + (size_t)k * N + (ok ? row0 + vv : 0), ok);
+    }
+  }
   cp_async_commit();
   // the rows the B^n epilogue reads (remainder pair, u^n) into L2 while the
   // transform runs: one request per 128-byte line, valid elements only
