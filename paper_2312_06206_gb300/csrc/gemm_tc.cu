@@ -366,11 +366,12 @@ __device__ __forceinline__ void tile_coords(const TcBatch& bt, int t, int* z, in
 // tmem_empty.  The ring and the accumulator pair carry over from tile to
 // tile.
 constexpr int EPI_WARPS = 8;
+constexpr int TQ = 4;   // slots of the tile-index ring (the producer runs at most three tiles ahead)
 constexpr int GEMM_THREADS = 64 + 32 * EPI_WARPS;
 constexpr size_t EPI_BYTES = (size_t)EPI_WARPS * 32 * EPI_LD * sizeof(float);
 template <int BN>
 constexpr size_t psmem_bytes() {
-  return (size_t)TileCfg<BN>::STAGES * TileCfg<BN>::STAGE_BYTES + EPI_BYTES + 1024 + 128;
+  return (size_t)TileCfg<BN>::STAGES * TileCfg<BN>::STAGE_BYTES + EPI_BYTES + 1024 + 256;
 }
 static_assert(psmem_bytes<256>() <= 232448 && psmem_bytes<128>() <= 232448, "shared memory per CTA");
 
@@ -386,13 +387,23 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   float* epi = reinterpret_cast<float*>(base + STAGES * STAGE_BYTES);
   uint64_t* bars = reinterpret_cast<uint64_t*>(base + STAGES * STAGE_BYTES + EPI_BYTES);
-  // bars: full[STAGES], empty[STAGES], tmem_full[2], tmem_empty[2], mma_done
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  // bars: full[STAGES], empty[STAGES], tmem_full[2], tmem_empty[2], mma_done,
+  // tile_full[TQ], tile_empty[TQ]
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5 + 2 * TQ);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   int* epi_arrive = reinterpret_cast<int*>(tmem_slot + 2);   // per accumulator
+  volatile int* tile_ring = reinterpret_cast<volatile int*>(tmem_slot + 4);   // TQ tile indices
   const uint32_t full0 = su32(bars), empty0 = su32(bars + STAGES);
   const uint32_t tfull0 = su32(bars + 2 * STAGES), tempty0 = su32(bars + 2 * STAGES + 2);
   const uint32_t mdone = su32(bars + 2 * STAGES + 4);
+  const uint32_t qfull0 = su32(bars + 2 * STAGES + 5), qempty0 = su32(bars + 2 * STAGES + 5 + TQ);
+  // Dynamic tile order (narrow tiles with a tile counter): the producer takes
+  // the next tile from the launch's counter and passes its index to the MMA
+  // thread and the epilogue warps through tile_ring (slot tl % TQ for the
+  // CTA's tl-th tile, -1 when there are no more), guarded by tile_full (the
+  // producer's arrival) and tile_empty (the MMA thread and every epilogue warp
+  // have read it).  Otherwise the static order blockIdx.x + tl * gridDim.x.
+  int* const tile_next = BN == 128 ? bt.tile_next : nullptr;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const uint64_t limit = bt.wait_ns ? bt.wait_ns : WAIT_LIMIT_NS;
   // the next step's first kernel (a programmatic dependent) may be scheduled
@@ -409,6 +420,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
       mbar_init(tempty0 + 8 * b, EPI_WARPS);
     }
     mbar_init(mdone, 1);
+    for (int q = 0; q < TQ; ++q) {
+      mbar_init(qfull0 + 8 * q, 1);
+      mbar_init(qempty0 + 8 * q, 1 + EPI_WARPS);
+    }
     *abort_flag = 0;
     epi_arrive[0] = epi_arrive[1] = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
@@ -452,7 +467,15 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
         }
       };
       int it = 0;
-      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x) {
+      for (int tl = 0; !*abort_flag; ++tl) {
+        // the next tile: publish its index (or -1) in the ring for the others
+        const int q = tl % TQ;
+        if (tl >= TQ && !wait_or_abort(qempty0 + 8 * q, (uint32_t)(tl / TQ - 1) & 1u, abort_flag, limit)) break;
+        int t = tile_next ? atomicAdd(tile_next, 1) : blockIdx.x + tl * gridDim.x;
+        if (t >= total) t = -1;
+        tile_ring[q] = t;
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(qfull0 + 8 * q) : "memory");
+        if (t < 0) break;
         int z, m0, n0;
         tile_coords<BN>(bt, t, &z, &m0, &n0);
         const TcInst& in = bt.in[z];
@@ -492,8 +515,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
     if (lane == 0) {
       // ---- MMA issuer ----
       constexpr uint32_t idesc = idesc_bf16(BM, BN);
-      int it = 0, tl = 0;
-      for (int t = blockIdx.x; t < total && !*abort_flag; t += gridDim.x, ++tl) {
+      int it = 0;
+      for (int tl = 0; !*abort_flag; ++tl) {
+        const int q = tl % TQ;
+        if (!wait_or_abort(qfull0 + 8 * q, (uint32_t)(tl / TQ) & 1u, abort_flag, limit)) break;
+        const int t = tile_ring[q];
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(qempty0 + 8 * q) : "memory");
+        if (t < 0) break;
         int z, m0, n0;
         tile_coords<BN>(bt, t, &z, &m0, &n0);
         const int nk = bt.in[z].K / BK;
@@ -534,8 +562,13 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
     // ---- epilogue warps: TMEM lane quarter = warp % 4, column half ----
     const int quarter = warp & 3, half = (warp - 2) >> 2;
     float* tile = epi + (warp - 2) * 32 * EPI_LD;
-    int tl = 0;
-    for (int t = blockIdx.x; t < total; t += gridDim.x, ++tl) {
+    for (int tl = 0;; ++tl) {
+      const int q = tl % TQ;
+      if (!wait_or_abort(qfull0 + 8 * q, (uint32_t)(tl / TQ) & 1u, abort_flag, limit)) break;
+      const int t = tile_ring[q];
+      __syncwarp();
+      if (lane == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(qempty0 + 8 * q) : "memory");
+      if (t < 0) break;
       int z, m0, n0;
       tile_coords<BN>(bt, t, &z, &m0, &n0);
       const int b = tl & 1;

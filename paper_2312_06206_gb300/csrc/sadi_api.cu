@@ -158,7 +158,8 @@ sadi_status setup_dense(sadi_ctx* c) {
       return fail(c, SADI_ENOMEM, "cudaMalloc(dense-inverse buffers) failed");
   }
   CK(cudaMalloc(&c->tcerr, sizeof(int)), "cudaMalloc(error flag)");
-  CK(cudaMalloc(&c->tcdep, sizeof(int) * (np / kTcBox)), "cudaMalloc(panel counters)");
+  // the per-panel counters and, after them, the GEMM launch's tile counter
+  CK(cudaMalloc(&c->tcdep, sizeof(int) * (np / kTcBox + 1)), "cudaMalloc(panel counters)");
   cudaStream_t st = c->stream;
   CK(cudaMemsetAsync(c->tcerr, 0, sizeof(int), st), "error flag");
   for (int k = 2; k < 6; ++k) CK(cudaMemsetAsync(*bufs[k], 0, bytes, st), "dense padding");
@@ -609,9 +610,10 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
     const int m = count - k0 < kPer ? count - k0 : kPer;
     tb.count = 2 * m;
     tb.wait_ns = 0;
+    tb.tile_next = cs[k0]->tcdep + cs[k0]->npad / kTcBox;
     for (int k = 0; k < m && e == cudaSuccess; ++k) {
       const sadi_ctx* ck = cs[k0 + k];
-      e = cudaMemsetAsync(ck->tcdep, 0, sizeof(int) * (ck->npad / kTcBox), st_);
+      e = cudaMemsetAsync(ck->tcdep, 0, sizeof(int) * (ck->npad / kTcBox + 1), st_);
       for (int pass = 0; pass < 2; ++pass) {
         TcInst& in = tb.in[pass * m + k];
         in = pass == 0 ? *ck->tc_x : *ck->tc_y;

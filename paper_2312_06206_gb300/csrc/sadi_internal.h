@@ -256,6 +256,10 @@ struct TcInst {
 struct TcBatch {
   int count;
   unsigned long long wait_ns;   // limit of every bounded wait of the launch (0: the default, 1 s)
+  // zeroed int: with it the CTAs of a launch with 128-wide tiles take tiles
+  // in order from this counter as they become free (nullptr: the static
+  // order, CTA c taking tiles c, c + grid, ...)
+  int* tile_next;
   TcInst in[kTcMaxBatch];
 };
 // tensor map of a rows x kdim BF16 matrix (row-major) with box box_rows x 64
