@@ -24,7 +24,10 @@
 //     32x32b; a warp takes the lane quarter 32 (w % 4) .. +31 and one column
 //     half), transpose 32 x 32 blocks through shared memory and run the
 //     epilogue of the launch (plain store, or the two fused sweep epilogues of
-//     the dense S-ADI step) with coalesced global accesses.
+//     the dense S-ADI step) with coalesced global accesses: 4-byte accesses
+//     of 128-byte row segments, or, when every row of the launch's arrays
+//     starts on a 16-byte boundary, 16-byte vectors (4 rows x 128 B per warp
+//     access; a separate instantiation of the kernel).
 // Problems of one launch may depend on earlier ones by 128-column panels (the
 // two sweeps of the dense step: the y sweep reads the W that the x sweep
 // stores): the last epilogue warp of a tile raises the panel counters of its
@@ -263,6 +266,156 @@ __device__ __forceinline__ void epilogue_block(const TcEpi& e, int rowbase, int 
   __syncwarp();
 }
 
+// The same epilogue with 16-byte accesses, for arrays whose rows start on
+// 16-byte boundaries (TcEpi::vec).  The warp's tile holds the 32 x 32 block
+// unpadded, in 4-float granules XOR-swizzled per row: element (r, c) sits at
+// r * 32 + 4 * ((c / 4) ^ vsw(r)) + c % 4.  The swizzle makes the three
+// access patterns free of bank conflicts: a lane's row of granules from
+// tcgen05.ld (8 lanes of a phase: 8 rows, one granule each), the row-major
+// vectors of the global arrays (8 lanes: one row, 8 granules) and the
+// column reads of the transposed split (32 lanes: 8 columns x 4 row octets,
+// vsw mixes the octet into the granule).
+__device__ __forceinline__ int vsw(int r) { return (r ^ ((r >> 3) << 1)) & 7; }
+__device__ __forceinline__ int vpos(int r, int g) { return r * 32 + ((g ^ vsw(r)) << 2); }
+
+// a row segment of nv valid floats (0..4) starting at p: one 16-byte access
+// when all four are valid
+__device__ __forceinline__ float4 ld4(const float* p, int nv) {
+  if (nv >= 4) return *reinterpret_cast<const float4*>(p);
+  float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (nv > 0) v.x = p[0];
+  if (nv > 1) v.y = p[1];
+  if (nv > 2) v.z = p[2];
+  return v;
+}
+__device__ __forceinline__ void st4(float* p, float4 v, int nv) {
+  if (nv >= 4) {
+    *reinterpret_cast<float4*>(p) = v;
+    return;
+  }
+  if (nv > 0) p[0] = v.x;
+  if (nv > 1) p[1] = v.y;
+  if (nv > 2) p[2] = v.z;
+}
+
+// one element of the compensated leapfrog: d^{n+1} = d^n + uhat and
+// u^{n+1} = (hi + lo) + d^{n+1} by a two-sum, renormalised
+__device__ __forceinline__ void leapfrog2(float uh, float dv, float hi, float lo, float* h_out, float* l_out,
+                                          float* d_out) {
+  const float d = dv + uh;
+  const float s = hi + d;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (d - bb);
+  const float l2 = lo + err;
+  const float h2 = s + l2;
+  *h_out = h2;
+  *l_out = l2 - (h2 - s);
+  *d_out = d;
+}
+
+__device__ __forceinline__ void epilogue_block_vec(const TcEpi& e, int rowbase, int col0, const uint32_t* r,
+                                                   float* tile, int lane) {
+#pragma unroll
+  for (int g = 0; g < 8; ++g)
+    *reinterpret_cast<float4*>(tile + vpos(lane, g)) =
+        make_float4(__uint_as_float(r[4 * g]), __uint_as_float(r[4 * g + 1]), __uint_as_float(r[4 * g + 2]),
+                    __uint_as_float(r[4 * g + 3]));
+  __syncwarp();
+  // lane -> row rr of each group of 4 rows (rows 4 i + rr, i = 0..7),
+  // granule gg (columns col0 + 4 gg ..): a warp access covers 4 rows x 128 B
+  const int rr = lane >> 3, gg = lane & 7;
+  const int c4 = col0 + 4 * gg;
+  const int ncol = min(max(e.n_valid - c4, 0), 4);
+  auto nv_of = [&](int i) { return rowbase + 4 * i + rr < e.m_valid ? ncol : 0; };
+  auto tile4 = [&](int i) -> float4* { return reinterpret_cast<float4*>(tile + vpos(4 * i + rr, gg)); };
+  if (e.mode == kTcStore) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int nv = nv_of(i);
+      if (nv) st4(e.C + (size_t)(rowbase + 4 * i + rr) * e.ldc + c4, *tile4(i), nv);
+    }
+  } else if (e.mode == kTcSweepX) {
+    // W = B + B E (in place over B), then the transposed BF16 split of W
+    float4 bv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int nv = nv_of(i);
+      bv[i] = ld4(e.C + (size_t)(nv ? rowbase + 4 * i + rr : 0) * e.ldc + (nv ? c4 : 0), nv);
+    }
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const int nv = nv_of(i);
+      float4* tp = tile4(i);
+      const float4 a = *tp;
+      const float4 w = make_float4(bv[i].x + a.x, bv[i].y + a.y, bv[i].z + a.z, bv[i].w + a.w);
+      *tp = w;
+      if (nv) st4(e.C + (size_t)(rowbase + 4 * i + rr) * e.ldc + c4, w, nv);
+    }
+    __syncwarp();
+    // lane -> row octet oc (rows 8 oc .. 8 oc + 7), column cl of each group
+    // of 8 columns: the octet as one 16-byte store each of hi and lo.  Rows
+    // beyond m_valid (padding up to the GEMM tile) hold W = 0 there (their B
+    // rows were loaded as 0 and their accumulator rows are zero), so the
+    // octets are stored whole.
+    const int oc = lane >> 3, cl = lane & 7;
+#pragma unroll
+    for (int jb = 0; jb < 4; ++jb) {
+      const int c = 8 * jb + cl;
+      if (col0 + c < e.n_valid) {
+        unsigned hi[4], lo[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int ra = 8 * oc + 2 * q;
+          split_bf16x2(tile[vpos(ra, c >> 2) + (c & 3)], tile[vpos(ra + 1, c >> 2) + (c & 3)], &hi[q], &lo[q]);
+        }
+        const size_t t = (size_t)(col0 + c) * e.ldt + rowbase + 8 * oc;
+        *reinterpret_cast<uint4*>(e.t_hi + t) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
+        *reinterpret_cast<uint4*>(e.t_lo + t) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      }
+    }
+  } else {
+    // uhat = W + E W; compensated leapfrog as in epilogue_block.  Four
+    // groups of two row quads; the loads of the next group are issued
+    // before the current one is computed and stored (different rows).
+    float4 wv[2][2], dv[2][2], hv[2][2], lv[2][2];
+#pragma unroll
+    for (int gi = 0; gi <= 4; ++gi) {
+      if (gi < 4) {
+        const int nb = gi & 1;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int i = 2 * gi + q, nv = nv_of(i);
+          const size_t rowc = (size_t)(nv ? rowbase + 4 * i + rr : 0), cc = nv ? c4 : 0;
+          wv[nb][q] = ld4(e.C + rowc * e.ldc + cc, nv);
+          dv[nb][q] = ld4(e.u_d + rowc * e.ldu + cc, e.first ? 0 : nv);
+          hv[nb][q] = ld4(e.u_hi + rowc * e.ldu + cc, nv);
+          lv[nb][q] = ld4(e.u_lo + rowc * e.ldu + cc, nv);
+        }
+      }
+      if (gi > 0) {
+        const int g = gi - 1, cb = g & 1;
+#pragma unroll
+        for (int q = 0; q < 2; ++q) {
+          const int i = 2 * g + q, nv = nv_of(i);
+          if (!nv) continue;
+          const float4 a = *tile4(i);
+          const float4 w = wv[cb][q], dd = dv[cb][q], hh = hv[cb][q], ll = lv[cb][q];
+          float4 h, l, d;
+          leapfrog2(w.x + a.x, dd.x, hh.x, ll.x, &h.x, &l.x, &d.x);
+          leapfrog2(w.y + a.y, dd.y, hh.y, ll.y, &h.y, &l.y, &d.y);
+          leapfrog2(w.z + a.z, dd.z, hh.z, ll.z, &h.z, &l.z, &d.z);
+          leapfrog2(w.w + a.w, dd.w, hh.w, ll.w, &h.w, &l.w, &d.w);
+          const size_t idx = (size_t)(rowbase + 4 * i + rr) * e.ldu + c4;
+          st4(e.u_hi + idx, h, nv);
+          st4(e.u_lo + idx, l, nv);
+          st4(e.u_d + idx, d, nv);
+        }
+      }
+    }
+  }
+  __syncwarp();
+}
+
 // Pull the global inputs of a warp's epilogue share into L2 while the tile's
 // MMAs still run: the lane's row, columns c0 .. c0 + W - 1 (clipped to the
 // valid columns) of each array the epilogue reads.  Only addresses of valid
@@ -375,7 +528,10 @@ constexpr size_t psmem_bytes() {
 }
 static_assert(psmem_bytes<256>() <= 232448 && psmem_bytes<128>() <= 232448, "shared memory per CTA");
 
-template <int BN>
+// VEC: every problem of the launch has TcEpi::vec set (16-byte epilogue
+// accesses); the two epilogues are separate instantiations, so that neither
+// carries the other's registers.
+template <int BN, bool VEC>
 __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_constant__ TcBatch bt, int total, int* err) {
   constexpr int STAGES = TileCfg<BN>::STAGES, STAGE_BYTES = TileCfg<BN>::STAGE_BYTES;
   constexpr int B_TILE = TileCfg<BN>::B_TILE, TMEM_COLS = TileCfg<BN>::TMEM_COLS;
@@ -590,7 +746,10 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
         const int cc = half * (BN / 64) + c;
         uint32_t r[32];
         tmem_ld32(acc + (uint32_t)(cc * 32), r);
-        epilogue_block(in.e, m0 + quarter * 32, n0 + cc * 32, r, tile, lane);
+        if constexpr (VEC)
+          epilogue_block_vec(in.e, m0 + quarter * 32, n0 + cc * 32, r, tile, lane);
+        else
+          epilogue_block(in.e, m0 + quarter * 32, n0 + cc * 32, r, tile, lane);
       }
       if (in.dep_signal) {
         // publish the tile: every warp's stores, then the last of the
@@ -690,12 +849,13 @@ cudaError_t tc_set_operands(TcInst* in, const void* a_hi, const void* a_lo, cons
 cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
   if (b.count < 1 || b.count > kTcMaxBatch) return cudaErrorInvalidValue;
   int boxes = 0;
-  bool even = true;
+  bool even = true, vec = true;
   for (int k = 0; k < b.count; ++k) {
     const TcInst& in = b.in[k];
     if (in.K <= 0 || in.K % BK || in.tiles_m < 1 || in.boxes_n < 1) return cudaErrorInvalidValue;
     boxes += in.tiles_m * in.boxes_n;
     even = even && in.boxes_n % 2 == 0;
+    vec = vec && in.e.vec;
   }
   static LaunchCache sms_of[kLauncherDevices];
   const int dev = device_slot();
@@ -704,9 +864,17 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
   if (!sms) {
     cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tc_gemm<256>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<256>());
+      e = cudaFuncSetAttribute(k_tc_gemm<256, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem_bytes<256>());
     if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(k_tc_gemm<128>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem_bytes<128>());
+      e = cudaFuncSetAttribute(k_tc_gemm<256, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem_bytes<256>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_gemm<128, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem_bytes<128>());
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(k_tc_gemm<128, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)psmem_bytes<128>());
     if (e != cudaSuccess) return e;
     sms_of[dev].store(sms, std::memory_order_release);
   }
@@ -732,12 +900,14 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
     const int total = boxes / 2;
     cfg.gridDim = dim3(sms);
     cfg.dynamicSmemBytes = psmem_bytes<256>();
-    return cudaLaunchKernelEx(&cfg, k_tc_gemm<256>, b, total, err);
+    return vec ? cudaLaunchKernelEx(&cfg, k_tc_gemm<256, true>, b, total, err)
+               : cudaLaunchKernelEx(&cfg, k_tc_gemm<256, false>, b, total, err);
   }
   const int total = boxes;
   cfg.gridDim = dim3(total < sms ? total : sms);
   cfg.dynamicSmemBytes = psmem_bytes<128>();
-  return cudaLaunchKernelEx(&cfg, k_tc_gemm<128>, b, total, err);
+  return vec ? cudaLaunchKernelEx(&cfg, k_tc_gemm<128, true>, b, total, err)
+             : cudaLaunchKernelEx(&cfg, k_tc_gemm<128, false>, b, total, err);
 }
 
 cudaError_t launch_split_pad(const float* src, int rows, int cols, int src_ld, void* hi, void* lo, int prow, int pcol,
@@ -782,6 +952,7 @@ extern "C" sadi_status sadi_gemm_split_bf16(const float* A, const float* B, floa
   e.n_valid = N;
   e.C = C;
   e.ldc = N;
+  e.vec = tc_vec_ok(e) ? 1 : 0;
   sadi_status rs = SADI_OK;
   int herr = 0;
   if (cudaMemsetAsync(err, 0, sizeof(int), st) != cudaSuccess ||

@@ -99,7 +99,12 @@ int log2i(int v) {
 size_t esize(int prec) { return prec == SADI_PREC_FP64 ? sizeof(double) : sizeof(float); }
 
 sadi_status alloc_state(sadi_ctx* c) {
-  const size_t nn = (size_t)c->g.N * c->g.N;
+  // row pitch of the N x N arrays: the FP32 forms on the register path pad
+  // their rows to 128 bytes (16-byte vector accesses in the sweep GEMM's
+  // epilogue and the row kernels), everything else keeps rows of N
+  c->g.ld = (c->prec != SADI_PREC_FP64 && c->reg_path) ? (c->g.N + kPitchAlign - 1) / kPitchAlign * kPitchAlign
+                                                        : c->g.N;
+  const size_t nn = (size_t)c->g.ld * c->g.N;
   const size_t es = esize(c->prec);
   cudaError_t e;
   for (int k = 0; k < 2; ++k) {
@@ -123,6 +128,13 @@ sadi_status alloc_state(sadi_ctx* c) {
   const size_t ses = (c->prec != SADI_PREC_FP64 && c->g.Np <= 4096) ? sizeof(double) : es;
   CK(cudaMalloc(&c->S, (size_t)c->g.N * c->g.Np * 2 * ses), "cudaMalloc(spectrum)");
   CK(cudaMalloc(&c->W, nn * es), "cudaMalloc(sweep)");
+  if (c->g.ld != c->g.N) {
+    // the padding columns stay zero: no kernel writes them, and the state
+    // watchdog sums whole padded arrays
+    void* pbufs[] = {c->ubuf[0], c->ubuf[1], c->ulo, c->Chi, c->Clo, c->phi2, c->W};
+    for (void* b : pbufs) CK(cudaMemsetAsync(b, 0, nn * es, c->stream), "zero state");
+    CK(cudaStreamSynchronize(c->stream), "zero state");
+  }
   // FP32 forms whose tiles select the three-pass column convolution (the
   // default at N' = 8192): its buffers and tables (kept once allocated)
   if (c->prec != SADI_PREC_FP64 && c->tiles32.conv_cols == kConvThreePass) {
@@ -223,6 +235,7 @@ sadi_status create_impl(int eq, int N, double alpha, double kappa, double tau, c
   c->s = kappa * tp / (2.0 * std::pow(c->h, alpha));
   Geom& g = c->g;
   g.N = N;
+  g.ld = N;
   g.logNp = log2i(N < 8 ? 8 : N);
   g.Np = 1 << g.logNp;
   g.P = 2 * g.Np;
@@ -375,15 +388,16 @@ sadi_status sadi_set_source(sadi_ctx* c, const double* F, double omega, double p
     c->F = nullptr;
   }
   if (!F) return SADI_OK;
-  const size_t nn = (size_t)c->g.N * c->g.N;
-  CK(cudaMalloc(&c->F, nn * esize(c->prec)), "cudaMalloc(source)");
+  const int N = c->g.N, ld = c->g.ld;
+  const size_t nn = (size_t)N * N;
+  CK(cudaMalloc(&c->F, (size_t)ld * N * esize(c->prec)), "cudaMalloc(source)");
   cudaStream_t st = c->stream;
   CK(stage_acquire(c), "order after the last asynchronous read");
   CK(cudaMemcpyAsync(c->stage, F, nn * sizeof(double), cudaMemcpyHostToDevice, st), "copy source");
   if (c->prec == SADI_PREC_FP64)
     CK(cudaMemcpyAsync(c->F, c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "source");
   else
-    CK(launch_convert_d2f(c->stage, static_cast<float*>(c->F), nn, st), "source convert");
+    CK(launch_convert_d2f(c->stage, static_cast<float*>(c->F), N, N, N, ld, st), "source convert");
   CK(cudaStreamSynchronize(st), "sadi_set_source");
   c->f_omega = omega;
   c->f_phase = phase;
@@ -403,7 +417,8 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   if (c->eq == 1 && phi2) return fail(c, SADI_EINVAL, "the diffusion equation has no phi2 (pass NULL)");
   if (c->prec == SADI_PREC_FP64 && c->g.N > 4096)
     return fail(c, SADI_EUNSUPPORTED, "the FP64 step path supports N <= 4096; select SADI_PREC_FP32");
-  const size_t nn = (size_t)c->g.N * c->g.N;
+  const int N = c->g.N, ld = c->g.ld;
+  const size_t nn = (size_t)N * N;
   cudaStream_t st = c->stream;
   c->cur = 0;
   CK(stage_acquire(c), "order after the last asynchronous read");
@@ -411,8 +426,8 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
   if (c->prec == SADI_PREC_FP64) {
     CK(cudaMemcpyAsync(c->ubuf[0], c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "phi1");
   } else {
-    CK(launch_split_d2ff(c->stage, static_cast<float*>(c->ubuf[0]), c->ulo, nn, st), "phi1 split");
-    CK(cudaMemsetAsync(c->ubuf[1], 0, nn * sizeof(float), st), "increment zero");
+    CK(launch_split_d2ff(c->stage, static_cast<float*>(c->ubuf[0]), c->ulo, N, N, N, ld, st), "phi1 split");
+    CK(cudaMemsetAsync(c->ubuf[1], 0, (size_t)ld * N * sizeof(float), st), "increment zero");
     // starting remainder C^0 = -kappa tau^2 L_h phi1: FP64 where the FP64
     // engine applies (N' <= 4096), else FP32 from the hi part
     if (c->g.Np <= 4096) {
@@ -431,9 +446,9 @@ sadi_status sadi_set_initial(sadi_ctx* c, const double* phi1, const double* phi2
     if (c->prec == SADI_PREC_FP64)
       CK(cudaMemcpyAsync(c->phi2, c->stage, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "phi2");
     else
-      CK(launch_convert_d2f(c->stage, static_cast<float*>(c->phi2), nn, st), "phi2 convert");
+      CK(launch_convert_d2f(c->stage, static_cast<float*>(c->phi2), N, N, N, ld, st), "phi2 convert");
   } else {
-    CK(cudaMemsetAsync(c->phi2, 0, nn * esize(c->prec), st), "phi2 zero");
+    CK(cudaMemsetAsync(c->phi2, 0, (size_t)ld * N * esize(c->prec), st), "phi2 zero");
   }
   CK(cudaMemsetAsync(c->wd, 0, sizeof(WdState), st), "watchdog record");
   CK(cudaStreamSynchronize(st), "set_initial");
@@ -501,6 +516,7 @@ RegInst reg_inst(const sadi_ctx* c) {
   r.S = static_cast<float2*>(c->S);
   r.W = static_cast<float*>(c->W);
   r.N = c->g.N;
+  r.ld = c->g.ld;
   r.r = c->g.r;
   r.tau = (float)c->tau;
   r.tau2 = (float)(c->eq == 0 ? c->tau * c->tau : c->tau);
@@ -621,7 +637,7 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
         ep = TcEpi{};
         ep.m_valid = ep.n_valid = ck->g.N;
         ep.C = static_cast<float*>(ck->W);
-        ep.ldc = ck->g.N;
+        ep.ldc = ck->g.ld;
         ep.err = ck->tcerr;
         if (pass == 0) {
           ep.mode = kTcSweepX;
@@ -636,7 +652,7 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
           ep.u_hi = static_cast<float*>(ck->ubuf[0]);
           ep.u_lo = ck->ulo;
           ep.u_d = static_cast<float*>(ck->ubuf[1]);
-          ep.ldu = ck->g.N;
+          ep.ldu = ck->g.ld;
           ep.first = ck->n == 0 ? 1 : 0;
           in.dep_wait = ck->tcdep;
           in.dep_need = ck->tc_x->tiles_m;   // x-sweep tiles per column panel
@@ -650,6 +666,7 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
         }
       }
     }
+    for (int k = 0; k < 2 * m; ++k) tb.in[k].e.vec = tc_vec_ok(tb.in[k].e) ? 1 : 0;
     for (int k = 0; k < m; ++k) cs[k0 + k]->dbg_expire_ns = 0;
     if (e == cudaSuccess) e = launch_tc_gemm(tb, cs[k0]->tcerr, st_);
   }
@@ -777,7 +794,7 @@ sadi_status batch_issue(sadi_ctx** ctxs, int count, int nsteps) {
 }
 
 sadi_status zero_initial(sadi_ctx* c) {
-  const size_t nn = (size_t)c->g.N * c->g.N;
+  const size_t nn = (size_t)c->g.ld * c->g.N;
   const size_t es = esize(c->prec);
   cudaStream_t st = c->stream;
   void* bufs[] = {c->ubuf[0], c->ubuf[1], c->phi2};
@@ -795,7 +812,7 @@ sadi_status zero_initial(sadi_ctx* c) {
 
 sadi_status watchdog_after(sadi_ctx* c, long long n_before, cudaStream_t st) {
   if (c->wd_every <= 0 || c->n / c->wd_every == n_before / c->wd_every) return SADI_OK;
-  const size_t nn = (size_t)c->g.N * c->g.N;
+  const size_t nn = (size_t)c->g.ld * c->g.N;   // padding columns (zero) included
   const bool f64 = c->prec == SADI_PREC_FP64;
   // FP64: u^n; FP32 forms: the hi part of the double-float pair, finite
   // exactly when u^n is
@@ -849,7 +866,9 @@ sadi_status sadi_get(sadi_ctx* c, double* u_out, long long* n_out) {
     CK(cudaMemcpyAsync(u_out, c->ubuf[c->cur], nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   } else {
     CK(stage_acquire(c), "order after the last asynchronous read");
-    CK(launch_join_ff2d(static_cast<const float*>(c->ubuf[0]), c->ulo, c->stage, nn, st), "u join");
+    CK(launch_join_ff2d(static_cast<const float*>(c->ubuf[0]), c->ulo, c->stage, c->g.N, c->g.N, c->g.ld, c->g.N,
+                        st),
+       "u join");
     CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, st), "copy u");
   }
   CK(cudaStreamSynchronize(st), "sadi_get");
@@ -879,7 +898,9 @@ sadi_status sadi_get_async(sadi_ctx* c, double* u_out) {
   if (c->prec == SADI_PREC_FP64)
     CK(cudaMemcpyAsync(c->stage, c->ubuf[c->cur], nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "stage u");
   else
-    CK(launch_join_ff2d(static_cast<const float*>(c->ubuf[0]), c->ulo, c->stage, nn, st), "u join");
+    CK(launch_join_ff2d(static_cast<const float*>(c->ubuf[0]), c->ulo, c->stage, c->g.N, c->g.N, c->g.ld, c->g.N,
+                        st),
+       "u join");
   CK(cudaEventRecord(c->ev_staged, st), "cudaEventRecord");
   CK(cudaStreamWaitEvent(c->copy_stream, c->ev_staged, 0), "cudaStreamWaitEvent");
   CK(cudaMemcpyAsync(u_out, c->stage, nn * sizeof(double), cudaMemcpyDeviceToHost, c->copy_stream), "copy u");
@@ -902,16 +923,19 @@ sadi_status sadi_get_device(sadi_ctx* c, void* dst, int dtype) {
   if (!c->initialized) return fail(c, SADI_ESTATE, "sadi_get_device before sadi_set_initial");
   if (!dst) return fail(c, SADI_EINVAL, "dst is NULL");
   if (dtype != 0 && dtype != 1) return fail(c, SADI_EINVAL, "dtype must be 0 (double) or 1 (float)");
-  const size_t nn = (size_t)c->g.N * c->g.N;
+  const int N = c->g.N;
+  const size_t nn = (size_t)N * N;
   cudaStream_t st = c->stream;
   const void* src = c->ubuf[c->cur];
   if (c->prec == SADI_PREC_FP64) {
     if (dtype == 0) CK(cudaMemcpyAsync(dst, src, nn * sizeof(double), cudaMemcpyDeviceToDevice, st), "copy");
-    else CK(launch_convert_d2f(static_cast<const double*>(src), static_cast<float*>(dst), nn, st), "convert");
+    else
+      CK(launch_convert_d2f(static_cast<const double*>(src), static_cast<float*>(dst), N, N, N, N, st), "convert");
   } else {
     const float* hi = static_cast<const float*>(c->ubuf[0]);
-    if (dtype == 1) CK(launch_join_ff2f(hi, c->ulo, static_cast<float*>(dst), nn, st), "join");
-    else CK(launch_join_ff2d(hi, c->ulo, static_cast<double*>(dst), nn, st), "join");
+    const int ld = c->g.ld;
+    if (dtype == 1) CK(launch_join_ff2f(hi, c->ulo, static_cast<float*>(dst), N, N, ld, N, st), "join");
+    else CK(launch_join_ff2d(hi, c->ulo, static_cast<double*>(dst), N, N, ld, N, st), "join");
   }
   return SADI_OK;
 }
@@ -1171,15 +1195,22 @@ extern "C" sadi_status sadi_step_source(sadi_ctx* c, const void* f, int dtype) {
   st = check_device_buffer(c, f, nn * (dtype == 0 ? sizeof(double) : sizeof(float)), "f");
   if (st != SADI_OK) return st;
   const bool f64 = c->prec == SADI_PREC_FP64;
+  const int N = c->g.N, ld = c->g.ld;
   const void* field = f;
-  if ((dtype == 0) != f64) {
-    if (!c->Fconv) CK(cudaMalloc(&c->Fconv, nn * esize(c->prec)), "cudaMalloc(source conversion)");
+  // the caller's field is used in place when its type and row pitch are the
+  // context's; else it is converted (and its rows spread to the padded pitch)
+  if ((dtype == 0) != f64 || ld != N) {
+    if (!c->Fconv) CK(cudaMalloc(&c->Fconv, (size_t)ld * N * esize(c->prec)), "cudaMalloc(source conversion)");
     if (f64)
-      CK(launch_convert_f2d(static_cast<const float*>(f), static_cast<double*>(c->Fconv), nn, c->stream),
+      CK(launch_convert_f2d(static_cast<const float*>(f), static_cast<double*>(c->Fconv), N, N, N, ld, c->stream),
+         "source convert");
+    else if (dtype == 0)
+      CK(launch_convert_d2f(static_cast<const double*>(f), static_cast<float*>(c->Fconv), N, N, N, ld, c->stream),
          "source convert");
     else
-      CK(launch_convert_d2f(static_cast<const double*>(f), static_cast<float*>(c->Fconv), nn, c->stream),
-         "source convert");
+      CK(cudaMemcpy2DAsync(c->Fconv, (size_t)ld * sizeof(float), f, (size_t)N * sizeof(float), (size_t)N * sizeof(float),
+                           N, cudaMemcpyDeviceToDevice, c->stream),
+         "source copy");
     field = c->Fconv;
   }
   c->F_step = field;
@@ -1259,8 +1290,9 @@ extern "C" sadi_status sadi_save_state(sadi_ctx* c, void* buf, size_t* bytes) {
   h.esz = (int)es;
   std::memcpy(buf, &h, sizeof h);
   char* p = static_cast<char*>(buf) + sizeof h;
+  const size_t row = (size_t)c->g.N * es, pitch = (size_t)c->g.ld * es;
   for (int k = 0; k < na; ++k, p += nn * es)
-    CK(cudaMemcpyAsync(p, arr[k], nn * es, cudaMemcpyDeviceToHost, c->stream), "copy state");
+    CK(cudaMemcpy2DAsync(p, row, arr[k], pitch, row, c->g.N, cudaMemcpyDeviceToHost, c->stream), "copy state");
   CK(cudaStreamSynchronize(c->stream), "sadi_save_state");
   *bytes = need;
   return SADI_OK;
@@ -1289,8 +1321,9 @@ extern "C" sadi_status sadi_load_state(sadi_ctx* c, const void* buf, size_t byte
   c->cur = 0;   // saved in canonical order: arr[0] = u^n
   state_arrays(c, arr);
   const char* p = static_cast<const char*>(buf) + sizeof h;
+  const size_t row = (size_t)c->g.N * es, pitch = (size_t)c->g.ld * es;
   for (int k = 0; k < na; ++k, p += nn * es)
-    CK(cudaMemcpyAsync(arr[k], p, nn * es, cudaMemcpyHostToDevice, c->stream), "copy state");
+    CK(cudaMemcpy2DAsync(arr[k], pitch, p, row, row, c->g.N, cudaMemcpyHostToDevice, c->stream), "copy state");
   CK(cudaMemsetAsync(c->wd, 0, sizeof(WdState), c->stream), "watchdog record");
   CK(cudaStreamSynchronize(c->stream), "sadi_load_state");
   c->n = h.n;

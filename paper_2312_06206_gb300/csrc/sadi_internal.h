@@ -5,6 +5,7 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
+#include <stdint.h>
 
 #include <atomic>
 
@@ -17,7 +18,12 @@ namespace sadi {
 // border rank r = Np - N.
 struct Geom {
   int N, Np, logNp, P, logP, r;
+  // row pitch (elements) of the context's N x N arrays (state, sweep scratch,
+  // phi2, source, remainder pair): N for FP64, N rounded up to a multiple of
+  // kPitchAlign for the FP32 forms (aligned rows for vector accesses)
+  int ld;
 };
+constexpr int kPitchAlign = 32;
 
 // Scalars of the right-hand side B^n (Sec. 3): tau, tau^2, g kind, n == 0.
 // g kinds: 0 none, 1 -u^3, 2 -sin u, 3 gc1 u + gc3 u^3 + gcs sin u.
@@ -55,12 +61,17 @@ cudaError_t run_generator(const double* a1, const Geom& g, double s, const doubl
                           double* cgen,
                           double2* lamc64, double2* lams64, float2* lamc32, float2* lams32, double* G64,
                           float* G32, int* status_host, cudaStream_t st);
-cudaError_t launch_convert_d2f(const double* src, float* dst, size_t n, cudaStream_t st);
-cudaError_t launch_convert_f2d(const float* src, double* dst, size_t n, cudaStream_t st);
-// double -> (hi, lo) float pair; (hi, lo) -> double hi + lo (optionally also a float copy)
-cudaError_t launch_split_d2ff(const double* src, float* hi, float* lo, size_t n, cudaStream_t st);
-cudaError_t launch_join_ff2d(const float* hi, const float* lo, double* dst, size_t n, cudaStream_t st);
-cudaError_t launch_join_ff2f(const float* hi, const float* lo, float* dst, size_t n, cudaStream_t st);
+// Element-wise conversions of a rows x cols array, source rows sld elements
+// apart, destination rows dld apart (padding elements are not touched).
+cudaError_t launch_convert_d2f(const double* src, float* dst, int rows, int cols, int sld, int dld, cudaStream_t st);
+cudaError_t launch_convert_f2d(const float* src, double* dst, int rows, int cols, int sld, int dld, cudaStream_t st);
+// double -> (hi, lo) float pair; (hi, lo) -> double hi + lo, or float hi + lo
+cudaError_t launch_split_d2ff(const double* src, float* hi, float* lo, int rows, int cols, int sld, int dld,
+                              cudaStream_t st);
+cudaError_t launch_join_ff2d(const float* hi, const float* lo, double* dst, int rows, int cols, int sld, int dld,
+                             cudaStream_t st);
+cudaError_t launch_join_ff2f(const float* hi, const float* lo, float* dst, int rows, int cols, int sld, int dld,
+                             cudaStream_t st);
 
 // ---- per-step kernels, step_kernels.cu --------------------------------------
 template <typename T>
@@ -154,6 +165,7 @@ struct RegInst {
   unsigned short* Bl;
   int ldp;
   int N, r;
+  int ld;               // row pitch (elements) of the N x N arrays: u_hi, u_lo, u_d, phi2, W, F, C_hi, C_lo
   float tau, tau2;
   float fsc;            // time factor of the source for this step
   int gkind, first;
@@ -235,7 +247,19 @@ struct TcEpi {
   int ldu;
   int first;
   int* err;                   // set to 1 if a bounded wait of this problem's CTAs ran out (or nullptr)
+  // 1: every row of C and of the state starts on a 16-byte boundary (ldc and
+  // ldu multiples of 4, pointers 16-byte aligned) and the rows of the W^T
+  // pair too (ldt a multiple of 8): the epilogue moves 16-byte vectors
+  int vec;
 };
+// whether the epilogue of e may use 16-byte accesses (TcEpi::vec)
+inline bool tc_vec_ok(const TcEpi& e) {
+  auto al = [](const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; };
+  bool ok = e.ldc % 4 == 0 && al(e.C);
+  if (e.mode == kTcSweepX) ok = ok && e.ldt % 8 == 0 && al(e.t_hi) && al(e.t_lo);
+  if (e.mode == kTcSweepY) ok = ok && e.ldu % 4 == 0 && al(e.u_hi) && al(e.u_lo) && al(e.u_d);
+  return ok;
+}
 struct TcInst {
   CUtensorMap a_hi, a_lo;     // A operand (M rows), box 128 x 64
   CUtensorMap b_hi, b_lo;     // B operand (N rows), box 128 x 64

@@ -386,32 +386,62 @@ __global__ void k_reg_tables(Geom g, const double* __restrict__ lnat, double sca
   }
 }
 
-__global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, size_t n) {
+// Element-wise conversions over a rows x cols array (source rows sld apart,
+// destination rows dld apart); one thread per element.
+struct Pitch2 {
+  int cols, sld, dld;
+  __device__ void at(size_t k, size_t* si, size_t* di) const {
+    const size_t r = k / (size_t)cols, c = k % (size_t)cols;
+    *si = r * sld + c;
+    *di = r * dld + c;
+  }
+};
+__global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, size_t n, Pitch2 p) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (k < n) d[k] = (float)s[k];
+  size_t si, di;
+  if (k < n) {
+    p.at(k, &si, &di);
+    d[di] = (float)s[si];
+  }
 }
-__global__ void k_f2d(const float* __restrict__ s, double* __restrict__ d, size_t n) {
+__global__ void k_f2d(const float* __restrict__ s, double* __restrict__ d, size_t n, Pitch2 p) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (k < n) d[k] = (double)s[k];
+  size_t si, di;
+  if (k < n) {
+    p.at(k, &si, &di);
+    d[di] = (double)s[si];
+  }
 }
 
-__global__ void k_split_d2ff(const double* __restrict__ s, float* __restrict__ hi, float* __restrict__ lo, size_t n) {
+__global__ void k_split_d2ff(const double* __restrict__ s, float* __restrict__ hi, float* __restrict__ lo, size_t n,
+                             Pitch2 p) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
+  size_t si, di;
   if (k < n) {
-    const float h = (float)s[k];
-    hi[k] = h;
-    lo[k] = (float)(s[k] - (double)h);
+    p.at(k, &si, &di);
+    const double v = s[si];
+    const float h = (float)v;
+    hi[di] = h;
+    lo[di] = (float)(v - (double)h);
   }
 }
 __global__ void k_join_ff2d(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ d,
-                            size_t n) {
+                            size_t n, Pitch2 p) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (k < n) d[k] = (double)hi[k] + (double)lo[k];
+  size_t si, di;
+  if (k < n) {
+    p.at(k, &si, &di);
+    d[di] = (double)hi[si] + (double)lo[si];
+  }
 }
 __global__ void k_join_ff2f(const float* __restrict__ hi, const float* __restrict__ lo, float* __restrict__ d,
-                            size_t n) {
+                            size_t n, Pitch2 p) {
   const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  if (k < n) d[k] = hi[k] + lo[k];
+  size_t si, di;
+  if (k < n) {
+    p.at(k, &si, &di);
+    d[di] = hi[si] + lo[si];
+  }
 }
 
 inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -442,30 +472,38 @@ cudaError_t launch_riesz1d(double* a, int n, double alpha, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert_d2f(const double* s, float* d, size_t n, cudaStream_t st) {
+cudaError_t launch_convert_d2f(const double* s, float* d, int rows, int cols, int sld, int dld, cudaStream_t st) {
+  const size_t n = (size_t)rows * cols;
   if (n == 0) return cudaSuccess;
-  k_d2f<<<nblk(n, 256), 256, 0, st>>>(s, d, n);
+  k_d2f<<<nblk(n, 256), 256, 0, st>>>(s, d, n, Pitch2{cols, sld, dld});
   return cudaGetLastError();
 }
-cudaError_t launch_split_d2ff(const double* s, float* hi, float* lo, size_t n, cudaStream_t st) {
+cudaError_t launch_split_d2ff(const double* s, float* hi, float* lo, int rows, int cols, int sld, int dld,
+                              cudaStream_t st) {
+  const size_t n = (size_t)rows * cols;
   if (n == 0) return cudaSuccess;
-  k_split_d2ff<<<nblk(n, 256), 256, 0, st>>>(s, hi, lo, n);
+  k_split_d2ff<<<nblk(n, 256), 256, 0, st>>>(s, hi, lo, n, Pitch2{cols, sld, dld});
   return cudaGetLastError();
 }
-cudaError_t launch_join_ff2d(const float* hi, const float* lo, double* d, size_t n, cudaStream_t st) {
+cudaError_t launch_join_ff2d(const float* hi, const float* lo, double* d, int rows, int cols, int sld, int dld,
+                             cudaStream_t st) {
+  const size_t n = (size_t)rows * cols;
   if (n == 0) return cudaSuccess;
-  k_join_ff2d<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n);
+  k_join_ff2d<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n, Pitch2{cols, sld, dld});
   return cudaGetLastError();
 }
-cudaError_t launch_join_ff2f(const float* hi, const float* lo, float* d, size_t n, cudaStream_t st) {
+cudaError_t launch_join_ff2f(const float* hi, const float* lo, float* d, int rows, int cols, int sld, int dld,
+                             cudaStream_t st) {
+  const size_t n = (size_t)rows * cols;
   if (n == 0) return cudaSuccess;
-  k_join_ff2f<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n);
+  k_join_ff2f<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n, Pitch2{cols, sld, dld});
   return cudaGetLastError();
 }
 
-cudaError_t launch_convert_f2d(const float* s, double* d, size_t n, cudaStream_t st) {
+cudaError_t launch_convert_f2d(const float* s, double* d, int rows, int cols, int sld, int dld, cudaStream_t st) {
+  const size_t n = (size_t)rows * cols;
   if (n == 0) return cudaSuccess;
-  k_f2d<<<nblk(n, 256), 256, 0, st>>>(s, d, n);
+  k_f2d<<<nblk(n, 256), 256, 0, st>>>(s, d, n, Pitch2{cols, sld, dld});
   return cudaGetLastError();
 }
 

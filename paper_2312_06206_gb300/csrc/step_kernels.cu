@@ -334,7 +334,7 @@ k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ 
     const int v = t / N, k = t % N;
     const T c = real_view<T>(buf + v * vs, k);
     const float hi = (float)c;
-    const size_t idx = (size_t)(row0 + v) * N + k;
+    const size_t idx = (size_t)(row0 + v) * g.ld + k;
     Ch[idx] = hi;
     Cl[idx] = (float)(c - (T)hi);
   }

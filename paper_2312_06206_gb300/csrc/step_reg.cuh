@@ -230,7 +230,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   pdl_wait_prerequisites();
   // the increment d^n = u^n - u^{n-1} (zero before the first step): the
   // remainder is advanced incrementally
-  const float* ur = I.u_d + (size_t)(valid ? row : 0) * N;
+  const float* ur = I.u_d + (size_t)(valid ? row : 0) * I.ld;
   float2 x[F::E];
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   // the rows the B^n epilogue reads (remainder pair, u^n) into L2 while the
   // transform runs: one request per 128-byte line, valid elements only
   if (valid) {
-    const size_t rb = (size_t)row * N;
+    const size_t rb = (size_t)row * I.ld;
     for (int c0 = 32 * t; c0 < N; c0 += 32 * F::TT) {
       asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_hi + rb + c0));
       asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_lo + rb + c0));
@@ -440,7 +440,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   // diffusion step B = C + conv/2 + tau (g(u~) + f) - d, u~ = u + d/2
   // (C + conv/2 = -kappa tau L_h u~; d = 0 at n = 0).
   const float tau = I.tau, tau2 = I.tau2;
-  const size_t rbase = (size_t)rrow * N;
+  const size_t rbase = (size_t)rrow * I.ld;
   // the equation is uniform over the launch: one loop per equation, so the
   // wave step's loop carries nothing of the diffusion step's
   auto bn_loop = [&](auto diff_c) {
@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   __syncwarp();
   if constexpr (DENSE) {
     if (!valid) return;
-    float* wrow = I.W + (size_t)row * N;
+    float* wrow = I.W + (size_t)row * I.ld;
     unsigned short* bh = I.Bh + (size_t)row * I.ldp;
     unsigned short* bl = I.Bl + (size_t)row * I.ldp;
     // B^n at x = 2m and 2m + 1 (one float2 of the buffer) per lane: the BF16
@@ -533,7 +533,7 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   // (H^-1 B)[k] = Re vhat[k] + Im vhat[Np-1-k] + sum_q G[k,q] ybot[q],
   // ybot[q] = Re vhat[N+q] + Im vhat[r-1-q]
   const int r = I.r;
-  float* wrow = I.W + (size_t)row * N;
+  float* wrow = I.W + (size_t)row * I.ld;
 #pragma unroll 2
   for (int q = 0; q < F::E; ++q) {
     const int k = t + F::TT * q;
@@ -578,7 +578,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
     constexpr int q = decltype(qc)::value;
     const int k = t + F::TT * q;
     const bool in = valid && k < N;
-    const size_t gi = (size_t)(in ? k : 0) * N + ii;
+    const size_t gi = (size_t)(in ? k : 0) * I.ld + ii;
     cp_async4(&s_hi[k * C::CT + c], I.u_hi + gi, in);
     cp_async4(&s_lo[k * C::CT + c], I.u_lo + gi, in);
     cp_async4(&s_d[k * C::CT + c], I.u_d + gi, in && !I.first);
@@ -588,8 +588,8 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int k = t + F::TT * q, k2 = Np - 1 - k;
-    const float a = (valid && k < N) ? I.W[(size_t)k * N + ii] : 0.f;
-    const float b = (valid && k2 < N) ? I.W[(size_t)k2 * N + ii] : 0.f;
+    const float a = (valid && k < N) ? I.W[(size_t)k * I.ld + ii] : 0.f;
+    const float b = (valid && k2 < N) ? I.W[(size_t)k2 * I.ld + ii] : 0.f;
     x[q] = make_float2(a, b);
   });
   // the twiddle group (committed first) has landed once at most the state
@@ -623,7 +623,7 @@ __global__ void __launch_bounds__(BLOCK, 3) kr_cols_solve(const __grid_constant_
       const float err = (hi - (s - bb)) + (d - bb);
       const float l2 = lo + err;
       const float h2 = s + l2;
-      const size_t idx = (size_t)j * N + i;
+      const size_t idx = (size_t)j * I.ld + i;
       I.u_hi[idx] = h2;
       I.u_lo[idx] = l2 - (h2 - s);
       I.u_d[idx] = d;
