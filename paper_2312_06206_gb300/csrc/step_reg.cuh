@@ -235,9 +235,12 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
     const int n = t + F::TT * q;
-    const float a = (valid && 2 * n < N) ? ur[2 * n] : 0.f;
-    const float b = (valid && 2 * n + 1 < N) ? ur[2 * n + 1] : 0.f;
-    x[q] = make_float2(a, b);
+    // one 8-byte load per pair (aligned: even offset, rows of 128 bytes; at
+    // 2n + 1 = N the second element is row padding, replaced by 0)
+    float2 v = make_float2(0.f, 0.f);
+    if (valid && 2 * n < N) v = *reinterpret_cast<const float2*>(ur + 2 * n);
+    if (2 * n + 1 >= N) v.y = 0.f;
+    x[q] = v;
   });
   cp_async_wait_all();
   __syncthreads();
@@ -447,46 +450,62 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
     constexpr bool DIFF = decltype(diff_c)::value;
 #pragma unroll 1
     for (int q0 = 0; q0 < F::E; q0 += 4) {
-      float ch[8], cl[8], uv[8], dv[8];
+      // the pairs x = 2n, 2n + 1 as 8-byte loads: rows start on 128-byte
+      // boundaries and the row pitch is even, so a pair is aligned, and at
+      // x = N - 1 (odd N) its second element is row padding, in bounds
+      float2 ch[4], cl[4], uv[4], dv[4];
 #pragma unroll
-      for (int j = 0; j < 8; ++j) {
-        const int x = 2 * (t + F::TT * (q0 + (j >> 1))) + (j & 1);
+      for (int j2 = 0; j2 < 4; ++j2) {
+        const int x = 2 * (t + F::TT * (q0 + j2));
         const bool ok = valid && x < N;
-        ch[j] = ok ? I.C_hi[rbase + x] : 0.f;
-        cl[j] = ok ? I.C_lo[rbase + x] : 0.f;
-        uv[j] = ok ? I.u_hi[rbase + x] : 0.f;
-        if constexpr (DIFF) dv[j] = (ok && !I.first) ? I.u_d[rbase + x] : 0.f;
+        const size_t at = ok ? rbase + x : 0;
+        const float2 z = make_float2(0.f, 0.f);
+        ch[j2] = ok ? *reinterpret_cast<const float2*>(I.C_hi + at) : z;
+        cl[j2] = ok ? *reinterpret_cast<const float2*>(I.C_lo + at) : z;
+        uv[j2] = ok ? *reinterpret_cast<const float2*>(I.u_hi + at) : z;
+        if constexpr (DIFF) dv[j2] = (ok && !I.first) ? *reinterpret_cast<const float2*>(I.u_d + at) : z;
       }
 #pragma unroll
       for (int j2 = 0; j2 < 4; ++j2) {
         const int n = t + F::TT * (q0 + j2);
         const float2 cv = sm[pad32(n)];
-        float b[2] = {0.f, 0.f};
+        float b[2] = {0.f, 0.f}, cn[2] = {0.f, 0.f}, cln[2] = {0.f, 0.f};
 #pragma unroll
         for (int e = 0; e < 2; ++e) {
           const int x = 2 * n + e;
           if (valid && x < N) {
             // C <- C + conv (two-sum into the double-float pair)
-            const float hi = ch[2 * j2 + e], lo = cl[2 * j2 + e], cx = e ? cv.y : cv.x;
+            const float hi = e ? ch[j2].y : ch[j2].x, lo = e ? cl[j2].y : cl[j2].x, cx = e ? cv.y : cv.x;
             const float s = hi + cx;
             const float bb = s - hi;
             const float err = (hi - (s - bb)) + (cx - bb);
             const float l2 = lo + err;
             const float c = s + l2;
-            I.C_hi[rbase + x] = c;
-            I.C_lo[rbase + x] = l2 - (c - s);
+            cn[e] = c;
+            cln[e] = l2 - (c - s);
+            const float u = e ? uv[j2].y : uv[j2].x;
             if constexpr (!DIFF) {
-              float gs = g_of_r(I, uv[2 * j2 + e]);
+              float gs = g_of_r(I, u);
               if (I.F) gs += I.fsc * I.F[rbase + x];
               const float gg = tau2 * gs;
               b[e] = I.first ? tau * I.phi2[rbase + x] + 0.5f * (c + gg) : c + gg;
             } else {
-              const float d = dv[2 * j2 + e];
-              float gs = g_of_r(I, uv[2 * j2 + e] + 0.5f * d);
+              const float d = e ? dv[j2].y : dv[j2].x;
+              float gs = g_of_r(I, u + 0.5f * d);
               if (I.F) gs += I.fsc * I.F[rbase + x];
               b[e] = (c + 0.5f * cx) + tau2 * gs - d;
             }
           }
+        }
+        // the updated remainder pair: one 8-byte store each, or the single
+        // element at x = N - 1 (the padding is never written)
+        const int x = 2 * n;
+        if (valid && x + 1 < N) {
+          *reinterpret_cast<float2*>(I.C_hi + rbase + x) = make_float2(cn[0], cn[1]);
+          *reinterpret_cast<float2*>(I.C_lo + rbase + x) = make_float2(cln[0], cln[1]);
+        } else if (valid && x < N) {
+          I.C_hi[rbase + x] = cn[0];
+          I.C_lo[rbase + x] = cln[0];
         }
         sm[pad32(n)] = make_float2(b[0], b[1]);
       }
@@ -509,8 +528,8 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
       if (k < N) {
         const float2 v = sm[pad32(m)];
         const bool two = k + 1 < N;
-        wrow[k] = v.x;
-        if (two) wrow[k + 1] = v.y;
+        if (two) *reinterpret_cast<float2*>(wrow + k) = v;   // aligned: even k, rows of 128 bytes
+        else wrow[k] = v.x;
         unsigned hi, lo;
         split_bf16x2(v.x, two ? v.y : 0.f, &hi, &lo);
         *reinterpret_cast<unsigned*>(bh + k) = hi;
