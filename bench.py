@@ -327,10 +327,9 @@ def aggregate(times, world_size, pts_per_step, steps_list, reduce_max=None):
 
 # DRAM bytes per launch (dram__bytes_read.sum + dram__bytes_write.sum) of a
 # kernel in a workload, from the ncu captures summarised under profiles/
-# (kr_cols_conv_n1023.md, k_tc_gemm_n1023.md, k_tc_gemm_n4095.md); absent =
-# no capture of the current kernel, reported as null.
-NCU_TRAFFIC = {("n1023", "kr_cols_conv"): 50.52e6, ("n1023", "k_tc_gemm(x+y)"): 86.1e6,
-               ("n4095", "k_tc_gemm(x+y)"): 1687.3e6}
+# (kr_cols_conv_n1023.md, k_tc_gemm_n1023.md); absent = no capture of the
+# current kernel, reported as null.
+NCU_TRAFFIC = {("n1023", "kr_cols_conv"): 50.46e6, ("n1023", "k_tc_gemm(x+y)"): 90.5e6}
 
 
 # Algorithmic work per grid point of one instance and step, per kernel
