@@ -344,17 +344,21 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   // with the rows fastest.  Item 0 also holds the x-frequency N' result (item
   // 1's pair) in the imaginary part of slot 0.
   const float2* base = reinterpret_cast<const float2*>(smem_raw);
-  for (int e = threadIdx.x; e < (C::CT / 2) * N; e += BLOCK) {
-    const int j = e % N, i = e / N, it = item_of(2 * i);
+#pragma unroll 1
+  for (int i = 0; i < C::CT / 2; ++i) {
+    const int it = item_of(2 * i);
     if (it > Np || it == 1) continue;
-    const float2 w = twh[j];
     const float2* se = base + (2 * i) * C::SMV;
-    const float2 y = cadd(se[pad32(j)], cmulc(se[C::SMV + pad32(j)], w));
-    if (it == 0) {
-      const float2 yn = cadd(se[2 * C::SMV + pad32(j)], cmulc(se[3 * C::SMV + pad32(j)], w));
-      I.S[j] = make_float2(y.x, yn.x);
-    } else {
-      I.S[(size_t)slot_of(it) * N + j] = y;
+    float2* col = I.S + (size_t)slot_of(it) * N;
+    for (int j = threadIdx.x; j < N; j += BLOCK) {
+      const float2 w = twh[j];
+      const float2 y = cadd(se[pad32(j)], cmulc(se[C::SMV + pad32(j)], w));
+      if (it == 0) {
+        const float2 yn = cadd(se[2 * C::SMV + pad32(j)], cmulc(se[3 * C::SMV + pad32(j)], w));
+        col[j] = make_float2(y.x, yn.x);
+      } else {
+        col[j] = y;
+      }
     }
   }
 }
