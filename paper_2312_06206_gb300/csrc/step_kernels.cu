@@ -34,11 +34,17 @@ namespace {
 constexpr int kThreads = 256;
 constexpr int kMaxPairs = 16;
 
+// the general nonlinearity out of line: the row kernels' epilogues inline
+// g many times over, and only launches with g kind 3 take this call
+template <typename T>
+__device__ __noinline__ T g_general(T u, T c1, T c3, T cs) {
+  return (c1 + c3 * u * u) * u + cs * sin(u);
+}
 template <typename T>
 __device__ __forceinline__ T g_of(const RhsParams& rp, T u) {
   if (rp.g == 1) return -u * u * u;
   if (rp.g == 2) return -sin(u);
-  if (rp.g == 3) return (T(rp.gc1) + T(rp.gc3) * u * u) * u + T(rp.gcs) * sin(u);
+  if (rp.g == 3) return g_general<T>(u, T(rp.gc1), T(rp.gc3), T(rp.gcs));
   return T(0);
 }
 
@@ -147,8 +153,9 @@ __device__ __forceinline__ T gs_out(const cx<T>* vh, int k, const Geom& g, const
 // Slot s >= 1 holds X[brev(s)]; slot 0 holds X[0] + i X[Np] (both real).
 // ---------------------------------------------------------------------------
 // With u2 (the diffusion step, FP64) the transformed rows are those of
-// u + beta (u - u2): the extrapolation u~ = u^n + (u^n - u^{n-1})/2.
-template <typename T>
+// u + beta (u - u2): the extrapolation u~ = u^n + (u^n - u^{n-1})/2; EXTRAP
+// selects that form at compile time (the other launches carry none of it).
+template <typename T, bool EXTRAP = false>
 __global__ void __launch_bounds__(kThreads)
 k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw,
            const cx<T>* __restrict__ tw, int NR, const T* __restrict__ u2 = nullptr, T beta = T(0)) {
@@ -165,7 +172,7 @@ k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* 
       const T* row = u + (size_t)(row0 + v) * N;
       if (2 * n < N) a = row[2 * n];
       if (2 * n + 1 < N) b = row[2 * n + 1];
-      if (u2) {
+      if constexpr (EXTRAP) {
         const T* row2 = u2 + (size_t)(row0 + v) * N;
         if (2 * n < N) a += beta * (a - row2[2 * n]);
         if (2 * n + 1 < N) b += beta * (b - row2[2 * n + 1]);
@@ -349,17 +356,24 @@ k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ 
 // increment d is what was transformed, and C accumulates -kappa tau L_h u^n)
 // C + conv/2 = -kappa tau L_h (u^n + d/2).  uaux is u^{n-1} in the plain form
 // and d in the compensated one.
-template <typename T>
+// DIFF: the equation of the launch (a template parameter of the row kernel,
+// so that the wave step's epilogue carries none of the diffusion step's code).
+template <typename T, bool DIFF>
 __device__ __forceinline__ T rhs_at(const RhsParams& rp, const cx<T>* e, int k, size_t idx, const T* u,
                                     const T* uaux, const T* phi2, float* Ch, float* Cl) {
+  if constexpr (!DIFF) {
+    T conv = real_view<T>(e, k);
+    if (Ch) conv = acc_remainder<T>(Ch, Cl, idx, conv);
+    const T uu = u[idx];
+    T gsrc = g_of<T>(rp, uu);
+    if (rp.F) gsrc += T(rp.fsc) * static_cast<const T*>(rp.F)[idx];
+    const T gg = T(rp.tau2) * gsrc;
+    return rp.first ? T(rp.tau) * phi2[idx] + T(0.5) * (conv + gg) : conv + gg;
+  }
   const T cd = real_view<T>(e, k);
   const T conv = Ch ? acc_remainder<T>(Ch, Cl, idx, cd) : cd;
   const T uu = u[idx];
   T fsrc = rp.F ? T(rp.fsc) * static_cast<const T*>(rp.F)[idx] : T(0);
-  if (rp.eq == 0) {
-    const T gg = T(rp.tau2) * (g_of<T>(rp, uu) + fsrc);
-    return rp.first ? T(rp.tau) * phi2[idx] + T(0.5) * (conv + gg) : conv + gg;
-  }
   const T d = rp.first ? T(0) : (Ch ? uaux[idx] : uu - uaux[idx]);
   const T ut = uu + T(0.5) * d;
   const T b = conv + T(rp.tau2) * (g_of<T>(rp, ut) + fsrc) - d;
@@ -373,7 +387,7 @@ __device__ __forceinline__ T rhs_at(const RhsParams& rp, const cx<T>* e, int k, 
 // ---------------------------------------------------------------------------
 // DENSE: the dense-inverse form stops after B^n, which it writes to W and,
 // split into BF16 pairs, to Bh / Bl (ld ldp).
-template <typename T, bool DENSE = false, int NT = kThreads>
+template <typename T, bool DENSE = false, int NT = kThreads, bool DIFF = false>
 __global__ void __launch_bounds__(NT)
 k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __restrict__ uaux,
              const T* __restrict__ phi2, T* __restrict__ W,
@@ -392,6 +406,32 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
   const int halfNp = Np >> 1;
   const int npairs = NR * halfNp;
   constexpr int MP = kMaxPairs * kThreads / NT;   // same pair capacity at any block size
+  if constexpr (DENSE) {
+    // B^n straight to W and its BF16 pair (no register staging: the rows are
+    // not transformed further)
+#pragma unroll 4
+    for (int it = 0; it < MP; ++it) {
+      const int t = threadIdx.x + it * blockDim.x;
+      if (t < npairs) {
+        const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
+        if (v < nrows) {
+          const size_t row = (size_t)(row0 + v);
+          const cx<T>* e = buf + v * vs;
+          if (k < N) {
+            const T b = rhs_at<T, DIFF>(rp, e, k, row * N + k, u, uaux, phi2, Ch, Cl);
+            W[row * N + k] = b;
+            split_bf16(b, Bh + row * ldp + k, Bl + row * ldp + k);
+          }
+          if (k2 < N) {
+            const T b = rhs_at<T, DIFF>(rp, e, k2, row * N + k2, u, uaux, phi2, Ch, Cl);
+            W[row * N + k2] = b;
+            split_bf16(b, Bh + row * ldp + k2, Bl + row * ldp + k2);
+          }
+        }
+      }
+    }
+    return;
+  }
   T ra[MP], rb[MP];
 #pragma unroll
   for (int it = 0; it < MP; ++it) {
@@ -403,31 +443,10 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
       if (v < nrows) {
         const int row = row0 + v;
         const cx<T>* e = buf + v * vs;
-        if (k < N) ra[it] = rhs_at<T>(rp, e, k, (size_t)row * N + k, u, uaux, phi2, Ch, Cl);
-        if (k2 < N) rb[it] = rhs_at<T>(rp, e, k2, (size_t)row * N + k2, u, uaux, phi2, Ch, Cl);
+        if (k < N) ra[it] = rhs_at<T, DIFF>(rp, e, k, (size_t)row * N + k, u, uaux, phi2, Ch, Cl);
+        if (k2 < N) rb[it] = rhs_at<T, DIFF>(rp, e, k2, (size_t)row * N + k2, u, uaux, phi2, Ch, Cl);
       }
     }
-  }
-  if constexpr (DENSE) {
-#pragma unroll
-    for (int it = 0; it < MP; ++it) {
-      const int t = threadIdx.x + it * blockDim.x;
-      if (t < npairs) {
-        const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
-        if (v < nrows) {
-          const size_t row = (size_t)(row0 + v);
-          if (k < N) {
-            W[row * N + k] = ra[it];
-            split_bf16(ra[it], Bh + row * ldp + k, Bl + row * ldp + k);
-          }
-          if (k2 < N) {
-            W[row * N + k2] = rb[it];
-            split_bf16(rb[it], Bh + row * ldp + k2, Bl + row * ldp + k2);
-          }
-        }
-      }
-    }
-    return;
   }
   __syncthreads();
 #pragma unroll
@@ -574,8 +593,12 @@ cudaError_t step_setup_attributes() {
   const int mx = 227 * 1024;
   cudaError_t e;
   if ((e = cudaFuncSetAttribute(k_rows_r2c<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_r2c<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_cols_conv<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_rows_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
+  if ((e = cudaFuncSetAttribute(k_rows_solve<T, false, kThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                mx)))
+    return e;
   if ((e = cudaFuncSetAttribute(k_cols_solve<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_rows_remainder<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
   if ((e = cudaFuncSetAttribute(k_rows_gs<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
@@ -583,6 +606,12 @@ cudaError_t step_setup_attributes() {
     if ((e = cudaFuncSetAttribute(k_rows_solve<T, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx))) return e;
     if ((e = cudaFuncSetAttribute(k_rows_solve<T, true, 2 * kThreads>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   mx)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k_rows_solve<T, true, kThreads, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  mx)))
+      return e;
+    if ((e = cudaFuncSetAttribute(k_rows_solve<T, true, 2 * kThreads, true>,
+                                  cudaFuncAttributeMaxDynamicSharedMemorySize, mx)))
       return e;
   }
   return cudaSuccess;
@@ -680,14 +709,20 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   // incremental remainder (Ch != nullptr): transform the increment d = u_prev
   // FP64 diffusion step (n >= 1): transform u~ = u^n + (u^n - u^{n-1})/2
   const bool extrap = !Ch && rp.eq == 1 && !rp.first;
-  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(Ch ? u_prev : u_cur, S, g, stw, tw, NR,
-                                                        extrap ? u_prev : nullptr, T(0.5));
+  if (extrap)
+    k_rows_r2c<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, stw, tw, NR, u_prev, T(0.5));
+  else
+    k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(Ch ? u_prev : u_cur, S, g, stw, tw, NR);
   if (ev) cudaEventRecord(ev[1], st);
   cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
   if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
-  k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, u_prev, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
-                                                          NR, Ch, Cl);
+  if (rp.eq == 1)
+    k_rows_solve<T, false, kThreads, true><<<rblocks, kThreads, NR * vbytes, st>>>(
+        S, u_cur, u_prev, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl);
+  else
+    k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, u_prev, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
+                                                            NR, Ch, Cl);
   if (ev) cudaEventRecord(ev[3], st);
   if (transposed_y_sweep<T>(u_lo)) {
     // FP32 compensated form: the y sweep on rows of W^T (S is free scratch)
@@ -762,8 +797,15 @@ cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const 
   cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
   if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
-  if (wide_rows<T>(g))
+  const bool diff = rp.eq == 1;
+  if (wide_rows<T>(g) && diff)
+    k_rows_solve<T, true, 2 * kThreads, true><<<rblocks, 2 * kThreads, NR * vbytes, st>>>(
+        S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
+  else if (wide_rows<T>(g))
     k_rows_solve<T, true, 2 * kThreads><<<rblocks, 2 * kThreads, NR * vbytes, st>>>(
+        S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
+  else if (diff)
+    k_rows_solve<T, true, kThreads, true><<<rblocks, kThreads, NR * vbytes, st>>>(
         S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
   else
     k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
