@@ -490,7 +490,7 @@ __device__ bool wait_panels(const TcInst& in, int n0, volatile int* abort_flag, 
 // numbered problem by problem; inside a problem in groups of kGroupM tile
 // rows, column-major within a group, so that the tiles in flight at one time
 // share A and B panels in L2.
-constexpr int kGroupM = 8;
+constexpr int kGroupM = 32;
 template <int BN>
 __device__ __forceinline__ void tile_coords(const TcBatch& bt, int t, int* z, int* m0, int* n0) {
   constexpr int per = BN / BOX;   // B boxes per tile width
