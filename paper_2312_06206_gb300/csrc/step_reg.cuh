@@ -252,15 +252,19 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   // its rows fastest (runs of VB rows), reading every vector's buffer
   const float2* base = reinterpret_cast<const float2*>(smem_raw);
   const int row0 = blockIdx.x * C::VB;
-  for (int e = threadIdx.x; e < C::VB * F::L; e += BLOCK) {
-    const int vv = e % C::VB, k = e / C::VB;
-    if (row0 + vv >= N) continue;
-    const float2* smv = base + vv * C::SMV;
+  // thread -> row vv of the block (fixed: BLOCK is a multiple of VB) and
+  // slots k, k + BLOCK / VB, ...
+  static_assert(BLOCK % C::VB == 0, "whole slot runs per block pass");
+  const int vv = threadIdx.x % C::VB;
+  if (row0 + vv >= N) return;
+  const float2* smv = base + vv * C::SMV;
+  float2* col = I.S + row0 + vv;
+  for (int k = threadIdx.x / C::VB; k < F::L; k += BLOCK / C::VB) {
     const float2 Z = smv[pad32(k)];
     const float2 Zc = cconj(smv[pad32((F::L - k) & (F::L - 1))]);
     const float2 Ev = cscale(cadd(Z, Zc), 0.5f);
     const float2 Ov = cscale(cmul_mi(csub(Z, Zc)), 0.5f);
-    I.S[(size_t)k * N + row0 + vv] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(s_tw[k], Ov));
+    col[(size_t)k * N] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(s_tw[k], Ov));
   }
 }
 
@@ -390,11 +394,13 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   {
     float2* base = reinterpret_cast<float2*>(smem_raw);
     const int row0 = blockIdx.x * C::VB;
-    for (int e = threadIdx.x; e < C::VB * F::L; e += BLOCK) {
-      const int vv = e % C::VB, k = e / C::VB;
-      const bool ok = row0 + vv < N;
-      cp_async8(&base[vv * C::SMV + pad32(k)], I.S + (size_t)k * N + (ok ? row0 + vv : 0), ok);
-    }
+    static_assert(BLOCK % C::VB == 0, "whole slot runs per block pass");
+    const int vv = threadIdx.x % C::VB;
+    const bool ok = row0 + vv < N;
+    const float2* col = I.S + (ok ? row0 + vv : 0);
+    float2* dst = base + vv * C::SMV;
+    for (int k = threadIdx.x / C::VB; k < F::L; k += BLOCK / C::VB)
+      cp_async8(&dst[pad32(k)], col + (ok ? (size_t)k * N : 0), ok);
   }
   cp_async_commit();
   // the rows the B^n epilogue reads (remainder pair, u^n) into L2 while the
@@ -452,8 +458,9 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   // wave step's loop carries nothing of the diffusion step's
   auto bn_loop = [&](auto diff_c) {
     constexpr bool DIFF = decltype(diff_c)::value;
+    // pairs n < N'/2 only: x = 2n < N <= N' (the x sweep reads no more)
 #pragma unroll 1
-    for (int q0 = 0; q0 < F::E; q0 += 4) {
+    for (int q0 = 0; q0 < F::E / 2; q0 += 4) {
       // the pairs x = 2n, 2n + 1 as 8-byte loads: rows start on 128-byte
       // boundaries and the row pitch is even, so a pair is aligned, and at
       // x = N - 1 (odd N) its second element is row padding, in bounds
@@ -511,37 +518,29 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
           I.C_hi[rbase + x] = cn[0];
           I.C_lo[rbase + x] = cln[0];
         }
-        sm[pad32(n)] = make_float2(b[0], b[1]);
+        if constexpr (DENSE) {
+          // B^n of the pair straight to W (8 bytes, or the last element)
+          // and its BF16 pairs (one 4-byte store each; the row pitch ldp is
+          // even, and at x = N, the zero padding, the split of 0 is stored)
+          if (valid && x < N) {
+            float* wr = I.W + rbase;
+            if (x + 1 < N) *reinterpret_cast<float2*>(wr + x) = make_float2(b[0], b[1]);
+            else wr[x] = b[0];
+            unsigned hi, lo;
+            split_bf16x2(b[0], b[1], &hi, &lo);
+            *reinterpret_cast<unsigned*>(I.Bh + (size_t)rrow * I.ldp + x) = hi;
+            *reinterpret_cast<unsigned*>(I.Bl + (size_t)rrow * I.ldp + x) = lo;
+          }
+        } else {
+          sm[pad32(n)] = make_float2(b[0], b[1]);
+        }
       }
     }
   };
   if (I.eq == 1) bn_loop(std::integral_constant<bool, true>{});
   else bn_loop(std::integral_constant<bool, false>{});
   __syncwarp();
-  if constexpr (DENSE) {
-    if (!valid) return;
-    float* wrow = I.W + (size_t)row * I.ld;
-    unsigned short* bh = I.Bh + (size_t)row * I.ldp;
-    unsigned short* bl = I.Bl + (size_t)row * I.ldp;
-    // B^n at x = 2m and 2m + 1 (one float2 of the buffer) per lane: the BF16
-    // pairs go out as one 4-byte store each (the row pitch ldp is even; at
-    // x = N, the zero padding, the split of 0 is stored)
-#pragma unroll 2
-    for (int q = 0; q < F::E / 2; ++q) {
-      const int m = t + F::TT * q, k = 2 * m;
-      if (k < N) {
-        const float2 v = sm[pad32(m)];
-        const bool two = k + 1 < N;
-        if (two) *reinterpret_cast<float2*>(wrow + k) = v;   // aligned: even k, rows of 128 bytes
-        else wrow[k] = v.x;
-        unsigned hi, lo;
-        split_bf16x2(v.x, two ? v.y : 0.f, &hi, &lo);
-        *reinterpret_cast<unsigned*>(bh + k) = hi;
-        *reinterpret_cast<unsigned*>(bl + k) = lo;
-      }
-    }
-    return;
-  }
+  if constexpr (DENSE) return;
   // v1 = Q (B' + i J B')
   static_for<0, F::E>([&](auto qc) {
     constexpr int q = decltype(qc)::value;
