@@ -387,6 +387,20 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   float2* s_tw1 = reinterpret_cast<float2*>(smem_raw) + C::VB * C::SMV;
   float2* s_tw = s_tw1 + F::L;
   stage_twiddles<LOGL, BLOCK>(I, s_tw1, s_tw);
+  // the rows the B^n epilogue reads (remainder pair, u^n) into L2, one
+  // request per 128-byte line, valid elements only, before waiting for the
+  // convolution: neither kernel of this step before this one writes them
+  // (they were written in the previous step), so the requests run under the
+  // convolution's tail; a prefetch only warms L2, which is coherent, so it
+  // cannot make a later load see older data
+  if (valid) {
+    const size_t rb = (size_t)row * I.ld;
+    for (int c0 = 32 * t; c0 < N; c0 += 32 * F::TT) {
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_hi + rb + c0));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_lo + rb + c0));
+      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.u_hi + rb + c0));
+    }
+  }
   pdl_wait_prerequisites();
   // stage the block's spectrum rows from the slot-major spectrum S[k * N + row]
   // (slot by slot, rows fastest: runs of VB rows); u^n, and phi2 on the
@@ -403,16 +417,6 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
       cp_async8(&dst[pad32(k)], col + (ok ? (size_t)k * N : 0), ok);
   }
   cp_async_commit();
-  // the rows the B^n epilogue reads (remainder pair, u^n) into L2 while the
-  // transform runs: one request per 128-byte line, valid elements only
-  if (valid) {
-    const size_t rb = (size_t)row * I.ld;
-    for (int c0 = 32 * t; c0 < N; c0 += 32 * F::TT) {
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_hi + rb + c0));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.C_lo + rb + c0));
-      asm volatile("prefetch.global.L2 [%0];" ::"l"(I.u_hi + rb + c0));
-    }
-  }
   cp_async_wait_all();
   __syncthreads();
   // a row vector belongs to TT threads of one warp: warp barriers from here
