@@ -259,12 +259,21 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
   if (row0 + vv >= N) return;
   const float2* smv = base + vv * C::SMV;
   float2* col = I.S + row0 + vv;
-  for (int k = threadIdx.x / C::VB; k < F::L; k += BLOCK / C::VB) {
-    const float2 Z = smv[pad32(k)];
-    const float2 Zc = cconj(smv[pad32((F::L - k) & (F::L - 1))]);
+  // slots k <= N'/2 with their partners N' - k, which read the same two
+  // buffer entries (slot 0 and slot N'/2 are their own partners)
+  for (int k = threadIdx.x / C::VB; k <= F::L / 2; k += BLOCK / C::VB) {
+    const int kp = (F::L - k) & (F::L - 1);
+    const float2 Z = smv[pad32(k)], Zp = smv[pad32(kp)];
+    const float2 Zc = cconj(Zp);
     const float2 Ev = cscale(cadd(Z, Zc), 0.5f);
     const float2 Ov = cscale(cmul_mi(csub(Z, Zc)), 0.5f);
     col[(size_t)k * N] = (k == 0) ? make_float2(Ev.x + Ov.x, Ev.x - Ov.x) : cadd(Ev, cmul(s_tw[k], Ov));
+    if (kp != k) {
+      const float2 Zc2 = cconj(Z);
+      const float2 Ev2 = cscale(cadd(Zp, Zc2), 0.5f);
+      const float2 Ov2 = cscale(cmul_mi(csub(Zp, Zc2)), 0.5f);
+      col[(size_t)kp * N] = cadd(Ev2, cmul(s_tw[kp], Ov2));
+    }
   }
 }
 
