@@ -594,6 +594,11 @@ __global__ void __launch_bounds__(GEMM_THREADS, 1) k_tc_gemm(const __grid_consta
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  // launched as a programmatic dependent, the set-up above ran under the
+  // kernel before this one; wait for it (its outputs are this launch's
+  // operands, and it zeroed the counters) before any global access.
+  // Launched without that attribute this is a no-op.
+  asm volatile("griddepcontrol.wait;" ::: "memory");
 
   if (warp == 0) {
     if (lane == 0) {
@@ -888,14 +893,23 @@ cudaError_t launch_tc_gemm(const TcBatch& b, int* err, cudaStream_t st) {
   // one CTA per SM by its shared memory)
   bool coop = false;
   for (int k = 0; k < b.count; ++k) coop = coop || b.in[k].dep_wait;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeCooperative;
-  attr[0].val.cooperative = 1;
+  cudaLaunchAttribute attr[2];
+  int nattr = 0;
+  if (coop) {
+    attr[nattr].id = cudaLaunchAttributeCooperative;
+    attr[nattr].val.cooperative = 1;
+    ++nattr;
+  }
+  if (b.pdl) {
+    attr[nattr].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[nattr].val.programmaticStreamSerializationAllowed = 1;
+    ++nattr;
+  }
   cudaLaunchConfig_t cfg = {};
   cfg.blockDim = dim3(GEMM_THREADS);
   cfg.stream = st;
   cfg.attrs = attr;
-  cfg.numAttrs = coop ? 1 : 0;
+  cfg.numAttrs = nattr;
   if (even && boxes / 2 >= 2 * sms) {
     const int total = boxes / 2;
     cfg.gridDim = dim3(sms);

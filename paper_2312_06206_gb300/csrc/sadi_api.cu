@@ -534,6 +534,8 @@ RegInst reg_inst(const sadi_ctx* c) {
   r.Bh = c->Bh;
   r.Bl = c->Bl;
   r.ldp = c->npad;
+  r.dep = c->prec == SADI_PREC_FP32_DENSE ? c->tcdep : nullptr;
+  r.ndep = c->npad / kTcBox + 1;
   return r;
 }
 
@@ -627,9 +629,14 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
     tb.count = 2 * m;
     tb.wait_ns = 0;
     tb.tile_next = cs[k0]->tcdep + cs[k0]->npad / kTcBox;
+    // register path: the B^n kernel zeroed the counters, and the first GEMM
+    // follows it directly in the stream (unless profiling events sit
+    // between), so it is launched as its programmatic dependent; otherwise
+    // the counters are zeroed here
+    tb.pdl = (c->reg_path && k0 == 0 && !ev) ? 1 : 0;
     for (int k = 0; k < m && e == cudaSuccess; ++k) {
       const sadi_ctx* ck = cs[k0 + k];
-      e = cudaMemsetAsync(ck->tcdep, 0, sizeof(int) * (ck->npad / kTcBox + 1), st_);
+      if (!c->reg_path) e = cudaMemsetAsync(ck->tcdep, 0, sizeof(int) * (ck->npad / kTcBox + 1), st_);
       for (int pass = 0; pass < 2; ++pass) {
         TcInst& in = tb.in[pass * m + k];
         in = pass == 0 ? *ck->tc_x : *ck->tc_y;

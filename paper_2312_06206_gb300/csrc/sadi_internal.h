@@ -164,6 +164,10 @@ struct RegInst {
   unsigned short* Bh;   // dense-inverse form: BF16 split of B^n (ld ldp, zero-padded)
   unsigned short* Bl;
   int ldp;
+  // dense form: the sweep GEMM's panel and tile counters (ndep ints), zeroed
+  // by the B^n kernel for the GEMM launched after it (nullptr: none)
+  int* dep;
+  int ndep;
   int N, r;
   int ld;               // row pitch (elements) of the N x N arrays: u_hi, u_lo, u_d, phi2, W, F, C_hi, C_lo
   float tau, tau2;
@@ -284,6 +288,10 @@ struct TcBatch {
   // in order from this counter as they become free (nullptr: the static
   // order, CTA c taking tiles c, c + grid, ...)
   int* tile_next;
+  // launched as a programmatic dependent of the kernel before it in the
+  // stream (host-side choice; the kernel waits for that kernel after its
+  // set-up in either case)
+  int pdl;
   TcInst in[kTcMaxBatch];
 };
 // tensor map of a rows x kdim BF16 matrix (row-major) with box box_rows x 64

@@ -411,6 +411,13 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
     }
   }
   pdl_wait_prerequisites();
+  // dense form: zero the sweep GEMM's counters for the GEMM that follows
+  // (every kernel of the previous step, the GEMM that used them included,
+  // has completed once the wait above returns)
+  if constexpr (DENSE) {
+    if (blockIdx.x == 0 && I.dep)
+      for (int i = threadIdx.x; i < I.ndep; i += BLOCK) I.dep[i] = 0;
+  }
   // stage the block's spectrum rows from the slot-major spectrum S[k * N + row]
   // (slot by slot, rows fastest: runs of VB rows); u^n, and phi2 on the
   // first step, are read in the B^n epilogue together with the remainder
