@@ -36,6 +36,10 @@
 // problems precede those of the later ones in every CTA's walk, and such a
 // launch is cooperative, so every counter is raised by a resident CTA that
 // never waits itself.
+// A launch may be a programmatic dependent of the kernel before it
+// (TcBatch::pdl): its CTAs set up barriers and tensor memory under that
+// kernel's tail and wait for it (griddepcontrol.wait) before any other
+// global access; the counters are then zeroed by that kernel.
 // Every mbarrier and counter wait is bounded (1 s of %globaltimer, or the
 // launch's TcBatch::wait_ns); on expiry the CTA sets *err, the other roles stop at their next wait, the
 // producer waits (bounded) for the copies it issued, all MMAs are waited for,
