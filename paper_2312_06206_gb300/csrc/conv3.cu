@@ -113,6 +113,7 @@ constexpr size_t smem_b() {
 // stores, the buffer may be refilled.
 __global__ void __launch_bounds__(kThreadsAC) k_conv3_a(const float2* __restrict__ S, const float2* __restrict__ tw,
                                                         Conv3 c, int N, int Np) {
+  pdl_entry();
   using F = rf::RegFFT<float, 6>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s_buf = reinterpret_cast<float2*>(smem_raw);   // [2 buffers][2 tiles][kR2 * kTP]
@@ -160,6 +161,7 @@ __global__ void __launch_bounds__(kThreadsAC) k_conv3_a(const float2* __restrict
 
 template <int LOGR1>
 __global__ void __launch_bounds__(32 * rf::RegFFT<float, LOGR1>::TT) k_conv3_b(Conv3 c) {
+  pdl_entry();
   using F = rf::RegFFT<float, LOGR1>;
   constexpr int R1 = 1 << LOGR1;
   constexpr int NT = 32 * F::TT;
@@ -226,6 +228,7 @@ __global__ void __launch_bounds__(32 * rf::RegFFT<float, LOGR1>::TT) k_conv3_b(C
 
 __global__ void __launch_bounds__(kThreadsAC) k_conv3_c(float2* __restrict__ S, const float2* __restrict__ tw,
                                                         Conv3 c, int N, int Np) {
+  pdl_entry();
   using F = rf::RegFFT<float, 6>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   float2* s_buf = reinterpret_cast<float2*>(smem_raw);   // [2 buffers][2 halves][kR2 * kTP]
@@ -348,8 +351,7 @@ cudaError_t launch_b(const Conv3& c, int groups, cudaStream_t st) {
     grids[dev].store(grid, std::memory_order_release);
   }
   const int items = groups * kR2;
-  k_conv3_b<LOGR1><<<grid < items ? grid : items, NT, smem_b<LOGR1>(), st>>>(c);
-  return cudaGetLastError();
+  return launch_dependent(k_conv3_b<LOGR1>, dim3(grid < items ? grid : items), dim3(NT), smem_b<LOGR1>(), st, c);
 }
 
 }  // namespace
@@ -419,16 +421,16 @@ cudaError_t launch_conv3(const Conv3& c, int N, int Np, void* Sv, const void* tw
     grids_ac[dev].store(grid_ac, std::memory_order_release);
   }
   const int gac = grid_ac < items ? grid_ac : items;
-  k_conv3_a<<<gac, kThreadsAC, kSmemAC, st>>>(S, tw, c, N, Np);
-  cudaError_t e = cudaGetLastError();
+  // the three passes are programmatic dependents, each of the one before it
+  cudaError_t e = launch_dependent(k_conv3_a, dim3(gac), dim3(kThreadsAC), kSmemAC, st, static_cast<const float2*>(S),
+                                   tw, c, N, Np);
   if (e != cudaSuccess) return e;
   if (c.logR1 == 5) e = launch_b<5>(c, groups, st);
   else if (c.logR1 == 6) e = launch_b<6>(c, groups, st);
   else if (c.logR1 == 7) e = launch_b<7>(c, groups, st);
   else e = cudaErrorInvalidValue;
   if (e != cudaSuccess) return e;
-  k_conv3_c<<<gac, kThreadsAC, kSmemAC, st>>>(S, tw, c, N, Np);
-  return cudaGetLastError();
+  return launch_dependent(k_conv3_c, dim3(gac), dim3(kThreadsAC), kSmemAC, st, S, tw, c, N, Np);
 }
 
 }  // namespace sadi

@@ -331,4 +331,35 @@ constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
 // current device; looked up on the first call per device, cached afterwards.
 cudaError_t noalloc_scratch_address(int device, void** out);
 
+// ---- programmatic dependent launch of the shared-memory engine's kernels ------
+// launch_dependent starts `kernel` on st as a programmatic dependent of the
+// kernel before it in the stream: its blocks may be scheduled before that
+// kernel has finished.  Every kernel launched this way opens with
+// pdl_entry(), which lets the kernel after it be scheduled likewise and then
+// waits until the kernel before it has completed and its writes are visible
+// (a no-op for a launch without the attribute).  Every argument is passed
+// explicitly (default arguments do not apply through the pointer).
+template <typename... KArgs, typename... Args>
+inline cudaError_t launch_dependent(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                                    Args... args) {
+  static_assert(sizeof...(KArgs) == sizeof...(Args), "every kernel argument passed explicitly");
+  cudaLaunchAttribute a[1];
+  a[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  a[0].val.programmaticStreamSerializationAllowed = 1;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = a;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, static_cast<KArgs>(args)...);
+}
+#ifdef __CUDACC__
+__device__ __forceinline__ void pdl_entry() {
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+}
+#endif
+
 }  // namespace sadi

@@ -159,6 +159,7 @@ template <typename T, bool EXTRAP = false>
 __global__ void __launch_bounds__(kThreads)
 k_rows_r2c(const T* __restrict__ u, cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw,
            const cx<T>* __restrict__ tw, int NR, const T* __restrict__ u2 = nullptr, T beta = T(0)) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
@@ -211,6 +212,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_cols_conv(cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
             const T* __restrict__ lpb, int CT) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np, logNp = g.logNp;
@@ -330,6 +332,7 @@ template <typename T>
 __global__ void __launch_bounds__(kThreads)
 k_rows_remainder(const cx<T>* __restrict__ S, Geom g, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
                  int NR, float* __restrict__ Ch, float* __restrict__ Cl) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N;
@@ -394,6 +397,7 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
              Geom g, RhsParams rp, const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw,
              const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int NR,
              float* Ch, float* Cl, unsigned short* Bh = nullptr, unsigned short* Bl = nullptr, int ldp = 0) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np;
@@ -481,6 +485,7 @@ __global__ void __launch_bounds__(kThreads)
 k_cols_solve(const T* __restrict__ W, const T* u_cur, T* u_prev, T* u_next, T* u_lo, Geom g, int first,
              const cx<T>* __restrict__ stw, const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s,
              const cx<T>* __restrict__ lam_c, const T* __restrict__ G, int CT) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np;
@@ -523,6 +528,7 @@ k_cols_solve(const T* __restrict__ W, const T* u_cur, T* u_prev, T* u_next, T* u
 constexpr int kTT = 32;   // transpose tile
 
 __global__ void __launch_bounds__(kTT * 8) k_transpose_f32(const float* __restrict__ A, float* __restrict__ AT, int N) {
+  pdl_entry();
   __shared__ float tile[kTT][kTT + 1];
   const int x0 = blockIdx.x * kTT, y0 = blockIdx.y * kTT;
   for (int r = threadIdx.y; r < kTT; r += 8) {
@@ -542,6 +548,7 @@ __global__ void __launch_bounds__(kThreads)
 k_rows_gs(const T* __restrict__ WT, T* __restrict__ UT, Geom g, const cx<T>* __restrict__ stw,
           const cx<T>* __restrict__ tw, const cx<T>* __restrict__ lam_s, const cx<T>* __restrict__ lam_c,
           const T* __restrict__ G, int NR) {
+  pdl_entry();
   extern __shared__ __align__(16) unsigned char smem_raw[];
   cx<T>* buf = reinterpret_cast<cx<T>*>(smem_raw);
   const int N = g.N, Np = g.Np;
@@ -570,6 +577,7 @@ k_rows_gs(const T* __restrict__ WT, T* __restrict__ UT, Geom g, const cx<T>* __r
 // k_cols_solve, element (j, i) with uhat = UT[i][j]
 __global__ void __launch_bounds__(kTT * 8) k_transpose_leapfrog(const float* __restrict__ UT, float* u_cur,
                                                                  float* d, float* u_lo, int N, int first) {
+  pdl_entry();
   __shared__ float tile[kTT][kTT + 1];
   const int i0 = blockIdx.x * kTT, j0 = blockIdx.y * kTT;
   for (int r = threadIdx.y; r < kTT; r += 8) {
@@ -687,9 +695,8 @@ cudaError_t launch_cols_conv(const Geom& g, const StepTables<T>& tb, int CTc, cx
     return cudaErrorInvalidValue;
   }
   const size_t vbytes = (size_t)vstride<T>(g.Np) * sizeof(cx<T>);
-  k_cols_conv<T><<<g.Np / CTc, kThreads, 2 * CTc * vbytes, st>>>(S, g, reinterpret_cast<const cx<T>*>(tb.stw),
-                                                                 reinterpret_cast<const cx<T>*>(tb.tw), tb.lpb, CTc);
-  return cudaGetLastError();
+  return launch_dependent(k_cols_conv<T>, dim3(g.Np / CTc), dim3(kThreads), 2 * CTc * vbytes, st, S, g,
+                          reinterpret_cast<const cx<T>*>(tb.stw), reinterpret_cast<const cx<T>*>(tb.tw), tb.lpb, CTc);
 }
 
 template <typename T>
@@ -709,38 +716,47 @@ cudaError_t launch_step(const Geom& g, const StepTables<T>& tb, const Tiles& tl,
   // incremental remainder (Ch != nullptr): transform the increment d = u_prev
   // FP64 diffusion step (n >= 1): transform u~ = u^n + (u^n - u^{n-1})/2
   const bool extrap = !Ch && rp.eq == 1 && !rp.first;
-  if (extrap)
-    k_rows_r2c<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(u_cur, S, g, stw, tw, NR, u_prev, T(0.5));
-  else
-    k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(Ch ? u_prev : u_cur, S, g, stw, tw, NR);
+  // every kernel of the step a programmatic dependent of the one before it
+  const dim3 rg(rblocks), kt(kThreads);
+  const size_t rsm = NR * vbytes;
+  unsigned short* const no_bf16 = nullptr;
+  cudaError_t ce = extrap ? launch_dependent(k_rows_r2c<T, true>, rg, kt, rsm, st, u_cur, S, g, stw, tw, NR,
+                                             static_cast<const T*>(u_prev), T(0.5))
+                          : launch_dependent(k_rows_r2c<T>, rg, kt, rsm, st, static_cast<const T*>(Ch ? u_prev : u_cur),
+                                             S, g, stw, tw, NR, static_cast<const T*>(nullptr), T(0));
+  if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[1], st);
-  cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
+  ce = launch_cols_conv<T>(g, tb, CTc, S, st);
   if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
-  if (rp.eq == 1)
-    k_rows_solve<T, false, kThreads, true><<<rblocks, kThreads, NR * vbytes, st>>>(
-        S, u_cur, u_prev, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl);
-  else
-    k_rows_solve<T><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, u_prev, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
-                                                            NR, Ch, Cl);
+  ce = rp.eq == 1 ? launch_dependent(k_rows_solve<T, false, kThreads, true>, rg, kt, rsm, st, S, u_cur,
+                                     static_cast<const T*>(u_prev), phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl,
+                                     no_bf16, no_bf16, 0)
+                  : launch_dependent(k_rows_solve<T>, rg, kt, rsm, st, S, u_cur, static_cast<const T*>(u_prev), phi2,
+                                     W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, no_bf16, no_bf16, 0);
+  if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[3], st);
   if (transposed_y_sweep<T>(u_lo)) {
     // FP32 compensated form: the y sweep on rows of W^T (S is free scratch)
     float* WT = reinterpret_cast<float*>(S);
     float* UT = WT + (size_t)g.N * g.N;
     const dim3 tg((g.N + kTT - 1) / kTT, (g.N + kTT - 1) / kTT), tb8(kTT, 8);
-    k_transpose_f32<<<tg, tb8, 0, st>>>(reinterpret_cast<const float*>(W), WT, g.N);
-    k_rows_gs<T><<<rblocks, kThreads, NR * vbytes, st>>>(reinterpret_cast<const T*>(WT), reinterpret_cast<T*>(UT), g,
-                                                        stw, tw, ls, lc, tb.G, NR);
-    k_transpose_leapfrog<<<tg, tb8, 0, st>>>(UT, reinterpret_cast<float*>(const_cast<T*>(u_cur)),
-                                             reinterpret_cast<float*>(u_prev), reinterpret_cast<float*>(u_lo), g.N,
-                                             rp.first);
+    ce = launch_dependent(k_transpose_f32, tg, tb8, 0, st, reinterpret_cast<const float*>(W), WT, g.N);
+    if (ce == cudaSuccess)
+      ce = launch_dependent(k_rows_gs<T>, rg, kt, rsm, st, reinterpret_cast<const T*>(WT), reinterpret_cast<T*>(UT), g,
+                            stw, tw, ls, lc, tb.G, NR);
+    if (ce == cudaSuccess)
+      ce = launch_dependent(k_transpose_leapfrog, tg, tb8, 0, st, static_cast<const float*>(UT),
+                            reinterpret_cast<float*>(const_cast<T*>(u_cur)), reinterpret_cast<float*>(u_prev),
+                            reinterpret_cast<float*>(u_lo), g.N, rp.first);
   } else {
-    k_cols_solve<T><<<(g.N + CTs - 1) / CTs, kThreads, CTs * vbytes, st>>>(W, u_cur, u_prev, u_next, u_lo, g,
-                                                                            rp.first, stw, tw, ls, lc, tb.G, CTs);
+    ce = launch_dependent(k_cols_solve<T>, dim3((g.N + CTs - 1) / CTs), kt, CTs * vbytes, st,
+                          static_cast<const T*>(W), u_cur, u_prev, u_next, u_lo, g, rp.first, stw, tw, ls, lc, tb.G,
+                          CTs);
   }
+  if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[4], st);
-  return cudaGetLastError();
+  return cudaSuccess;
 }
 
 template cudaError_t step_setup_attributes<float>();
@@ -792,25 +808,29 @@ cudaError_t launch_dense_rows(const Geom& g, const StepTables<float>& tb, const 
   const int NR = tl.rows, CTc = tl.conv_cols;
   const int rblocks = (g.N + NR - 1) / NR;
   if (ev) cudaEventRecord(ev[0], st);
-  k_rows_r2c<T><<<rblocks, kThreads, NR * vbytes, st>>>(d, S, g, stw, tw, NR);
+  // every kernel a programmatic dependent of the one before it
+  const dim3 rg(rblocks);
+  const size_t rsm = NR * vbytes;
+  cudaError_t ce = launch_dependent(k_rows_r2c<T>, rg, dim3(kThreads), rsm, st, d, S, g, stw, tw, NR,
+                                    static_cast<const T*>(nullptr), T(0));
+  if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[1], st);
-  cudaError_t ce = launch_cols_conv<T>(g, tb, CTc, S, st);
+  ce = launch_cols_conv<T>(g, tb, CTc, S, st);
   if (ce != cudaSuccess) return ce;
   if (ev) cudaEventRecord(ev[2], st);
   const bool diff = rp.eq == 1;
+  const dim3 kt(kThreads), kt2(2 * kThreads);
   if (wide_rows<T>(g) && diff)
-    k_rows_solve<T, true, 2 * kThreads, true><<<rblocks, 2 * kThreads, NR * vbytes, st>>>(
-        S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
-  else if (wide_rows<T>(g))
-    k_rows_solve<T, true, 2 * kThreads><<<rblocks, 2 * kThreads, NR * vbytes, st>>>(
-        S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
-  else if (diff)
-    k_rows_solve<T, true, kThreads, true><<<rblocks, kThreads, NR * vbytes, st>>>(
-        S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
-  else
-    k_rows_solve<T, true><<<rblocks, kThreads, NR * vbytes, st>>>(S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
-                                                                   NR, Ch, Cl, Bh, Bl, ldp);
-  return cudaGetLastError();
+    return launch_dependent(k_rows_solve<T, true, 2 * kThreads, true>, rg, kt2, rsm, st, S, u_cur, d, phi2, W, g, rp,
+                            stw, tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
+  if (wide_rows<T>(g))
+    return launch_dependent(k_rows_solve<T, true, 2 * kThreads>, rg, kt2, rsm, st, S, u_cur, d, phi2, W, g, rp, stw,
+                            tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
+  if (diff)
+    return launch_dependent(k_rows_solve<T, true, kThreads, true>, rg, kt, rsm, st, S, u_cur, d, phi2, W, g, rp, stw,
+                            tw, ls, lc, tb.G, NR, Ch, Cl, Bh, Bl, ldp);
+  return launch_dependent(k_rows_solve<T, true>, rg, kt, rsm, st, S, u_cur, d, phi2, W, g, rp, stw, tw, ls, lc, tb.G,
+                          NR, Ch, Cl, Bh, Bl, ldp);
 }
 
 }  // namespace sadi
