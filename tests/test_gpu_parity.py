@@ -176,6 +176,47 @@ def test_batch_step_matches_single_contexts(S):
         s.close()
 
 
+def test_dense_batch_over_two_gemm_launches_matches_single_contexts(S):
+    # ten dense-form contexts of one FFT length (N' = 64): the B^n kernel of
+    # the batch zeroes every member's GEMM counters, the first sweep GEMM
+    # (eight members) runs as its programmatic dependent, the second (two
+    # members) after it; stepped directly and by graph replay, the batch must
+    # reproduce single-context stepping bitwise
+    specs = [(40 + 2 * k, 1.2 + 0.06 * k, 1.0, 0.02, k % 3) for k in range(10)]
+
+    import torch
+    st = torch.cuda.Stream()
+
+    def make():
+        out = []
+        for k, (N, al, ka, ta, g) in enumerate(specs):
+            s = S.Sadi(N, al, ka, ta)
+            s.set_options(g, S.SADI_PREC_FP32_DENSE)
+            s.set_stream(st.cuda_stream)                  # a graph needs one stream
+            s.set_initial(WL.gaussian_bumps(N, 4, 500 + k), 0.3 * WL.random_field(N, 600 + k))
+            out.append(s)
+        return out
+    single = make()
+    for s in single:
+        s.step(5)
+    ref = [s.get()[0] for s in single]
+    batch = make()
+    S.sadi_batch_step(batch, 5)
+    for s, r in zip(batch, ref):
+        u, n = s.get()
+        assert n == 5 and np.array_equal(u, r)
+    replay = make()
+    S.sadi_batch_step(replay, 1)
+    g = S.SadiGraph(replay, 1)
+    g.launch(4)
+    g.close()
+    for s, r in zip(replay, ref):
+        u, n = s.get()
+        assert n == 5 and np.array_equal(u, r)
+    for s in single + batch + replay:
+        s.close()
+
+
 def test_batch_step_rejects_bad_batches(S):
     a = S.Sadi(31, 1.5, 1.0, 0.1)
     b = S.Sadi(31, 1.5, 1.0, 0.1)
