@@ -609,12 +609,19 @@ sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
     }
     e = launch_step_reg(b, c->g.logNp, max_n, st_, ev, true);
   } else {
-    if (count != 1) return fail(c, SADI_EINVAL, "internal: shared-memory dense group of more than one");
-    const RhsParams rp = rhs_of(c, c->n);
-    StepTables<float> tb{c->stw32, c->tw32, c->lpb32, c->lams32, c->lamc32, c->G32, c3_of(c)};
-    e = launch_dense_rows(c->g, tb, c->tiles32, rp, static_cast<const float*>(c->ubuf[0]),
-                          static_cast<const float*>(c->ubuf[1]), static_cast<const float*>(c->phi2), c->S,
-                          static_cast<float*>(c->W), c->Chi, c->Clo, c->Bh, c->Bl, c->npad, st_, ev);
+    // shared-memory engine: the FFT part one member after another (a
+    // profiled group has one member, so the events time its kernels), then
+    // the sweeps of all members batched below
+    if (ev && count != 1) return fail(c, SADI_EINVAL, "internal: profiled shared-memory dense group of more than one");
+    e = cudaSuccess;
+    for (int k = 0; k < count && e == cudaSuccess; ++k) {
+      sadi_ctx* ck = cs[k];
+      const RhsParams rp = rhs_of(ck, ck->n);
+      StepTables<float> tb{ck->stw32, ck->tw32, ck->lpb32, ck->lams32, ck->lamc32, ck->G32, c3_of(ck)};
+      e = launch_dense_rows(ck->g, tb, ck->tiles32, rp, static_cast<const float*>(ck->ubuf[0]),
+                            static_cast<const float*>(ck->ubuf[1]), static_cast<const float*>(ck->phi2), ck->S,
+                            static_cast<float*>(ck->W), ck->Chi, ck->Clo, ck->Bh, ck->Bl, ck->npad, st_, ev);
+    }
   }
   if (e == cudaSuccess && ev) e = cudaEventRecord(ev[3], st_);
   // Both sweeps of up to kTcMaxBatch / 2 members per launch: the x-sweep
@@ -740,19 +747,24 @@ namespace sadi_api {
 
 sadi_status batch_issue(sadi_ctx** ctxs, int count, int nsteps) {
   // group register-path contexts by FFT length (insertion order kept)
-  // (dense-form contexts on the register path form their own groups)
+  // (dense-form contexts on the register path form their own groups), and
+  // dense-form contexts on the shared-memory engine by FFT length too (their
+  // FFT kernels run one member after another, their sweep GEMMs batched; a
+  // profiled one steps alone, so that its events time its own kernels)
   std::vector<std::vector<sadi_ctx*>> groups;
   std::vector<sadi_ctx*> others;
   for (int k = 0; k < count; ++k) {
     sadi_ctx* c = ctxs[k];
     const bool dense_reg = is_dense(c) && c->reg_path;
-    if (!uses_reg_path(c) && !dense_reg) {
+    const bool dense_smem = is_dense(c) && !c->reg_path && !c->profiling;
+    if (!uses_reg_path(c) && !dense_reg && !dense_smem) {
       others.push_back(c);
       continue;
     }
     bool placed = false;
     for (auto& gr : groups)
-      if (gr[0]->g.logNp == c->g.logNp && is_dense(gr[0]) == is_dense(c) && (int)gr.size() < kMaxBatch) {
+      if (gr[0]->g.logNp == c->g.logNp && is_dense(gr[0]) == is_dense(c) && gr[0]->reg_path == c->reg_path &&
+          (int)gr.size() < kMaxBatch) {
         gr.push_back(c);
         placed = true;
         break;

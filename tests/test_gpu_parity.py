@@ -217,6 +217,33 @@ def test_dense_batch_over_two_gemm_launches_matches_single_contexts(S):
         s.close()
 
 
+def test_dense_batch_on_the_shared_memory_engine_matches_single_contexts(S):
+    # dense-form contexts of one FFT length on the shared-memory engine
+    # (N' = 2048): their FFT kernels run one after another, both sweeps of
+    # all of them in one GEMM launch; bitwise equal to single-context stepping
+    specs = [(1500, 1.4, 1.0, 1e-3, 1), (1100, 1.7, 0.8, 1e-3, 2), (2047, 1.2, 1.2, 5e-4, 0)]
+
+    def make():
+        out = []
+        for k, (N, al, ka, ta, g) in enumerate(specs):
+            s = S.Sadi(N, al, ka, ta)
+            s.set_options(g, S.SADI_PREC_FP32_DENSE)
+            s.set_initial(WL.gaussian_bumps(N, 4, 700 + k))
+            out.append(s)
+        return out
+    single = make()
+    for s in single:
+        s.step(3)
+    ref = [s.get()[0] for s in single]
+    batch = make()
+    S.sadi_batch_step(batch, 3)
+    for s, r in zip(batch, ref):
+        u, n = s.get()
+        assert n == 3 and np.array_equal(u, r)
+    for s in single + batch:
+        s.close()
+
+
 def test_batch_step_rejects_bad_batches(S):
     a = S.Sadi(31, 1.5, 1.0, 0.1)
     b = S.Sadi(31, 1.5, 1.0, 0.1)
