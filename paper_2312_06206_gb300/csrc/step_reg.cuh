@@ -336,14 +336,20 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   // has read it
   load_nat<LOGL>(x, reinterpret_cast<const float2*>(smem_raw) + (c & ~1) * C::SMV, t);
   __syncthreads();
-  static_for<0, F::E>([&](auto qc) {
-    constexpr int q = decltype(qc)::value;
-    float2 val = x[q];
-    if (item == 0) val.y = 0.f;
-    else if (item == 1) val = make_float2(val.y, 0.f);
+  // item and half are uniform over the vector's warp: branches, not selects
+  if (item <= 1) {
+    static_for<0, F::E>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      x[q] = item == 0 ? make_float2(x[q].x, 0.f) : make_float2(x[q].y, 0.f);
+    });
+  }
+  if (h) {
     // odd half: y-frequencies 2 k2 + 1 of the length-2L transform
-    x[q] = h ? cmul(val, twh[t + F::TT * q]) : val;
-  });
+    static_for<0, F::E>([&](auto qc) {
+      constexpr int q = decltype(qc)::value;
+      x[q] = cmul(x[q], twh[t + F::TT * q]);
+    });
+  }
   F::template fwd<true>(x, sm, t, s_tw1);
   static_for<0, F::E>([&](auto rc) {
     constexpr int r = decltype(rc)::value;
