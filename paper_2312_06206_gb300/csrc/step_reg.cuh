@@ -64,8 +64,9 @@ struct RowCfg {
   static constexpr int kMinBlocks = BLOCK >= 512 ? 1 : 4;
 };
 // The convolution kernel: vectors owned by warps (as in the row kernels), CT
-// per block; the FFT buffers, the vectors' symbol rows (natural order) and
-// the staged table tw1.
+// per block; the FFT buffers and the staged table tw1 (the symbol rows are
+// read from global memory: without them four blocks of 128 threads fit an
+// SM, against three).
 template <int LOGL, int BLOCK>
 struct ConvCfg {
   using F = rf::RegFFT<float, LOGL>;
@@ -77,9 +78,8 @@ struct ConvCfg {
   static constexpr int SMV = vec_smem<LOGL>(CT >= 16 ? 1 : 16 / CT);
   // the half-angle twiddles tw[0 .. L) are staged too when the shared memory
   // still admits the block count of the launch bounds
-  static constexpr size_t bytes_base =
-      (size_t)CT * SMV * sizeof(float2) + (size_t)CT * F::L * sizeof(float) + (size_t)F::L * sizeof(float2);
-  static constexpr int kBlocksPerSm = BLOCK >= 256 ? 2 : 3;
+  static constexpr size_t bytes_base = (size_t)CT * SMV * sizeof(float2) + (size_t)F::L * sizeof(float2);
+  static constexpr int kBlocksPerSm = BLOCK >= 256 ? 2 : 4;
   static constexpr bool STAGE_TW =
       kBlocksPerSm * (bytes_base + F::L * sizeof(float2) + 1024) <= (size_t)228 * 1024;
   static constexpr size_t bytes = bytes_base + (STAGE_TW ? F::L * sizeof(float2) : 0);
@@ -282,9 +282,9 @@ __global__ void __launch_bounds__(BLOCK, RowCfg<LOGL, BLOCK>::kMinBlocks) kr_row
 // of slot 0), i >= 2 = x-frequency i - 1 (slot i - 1).  Each item has two
 // vectors (even / odd y-frequency halves), vectors c = 2 i + h of the block.
 // A vector belongs to TT consecutive threads of one warp, so its transforms
-// synchronise the warp only.  The block's columns and symbol rows arrive in
-// shared memory by cp.async, so no registers are held while they are in
-// flight.
+// synchronise the warp only.  The block's columns arrive in shared memory by
+// cp.async, so no registers are held while they are in flight; each lane's
+// 32 symbol values are read from global memory (128-byte coalesced rows).
 template <int LOGL, int BLOCK>
 __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_cols_conv(
     const __grid_constant__ RegBatch B) {
@@ -295,8 +295,7 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   const RegInst& I = B.in[blockIdx.y];
   const int N = I.N, Np = F::L;
   const int c = threadIdx.x / F::TT, t = threadIdx.x % F::TT;
-  float* s_lam = reinterpret_cast<float*>(reinterpret_cast<float2*>(smem_raw) + C::CT * C::SMV);
-  float2* s_tw1 = reinterpret_cast<float2*>(s_lam + C::CT * F::L);
+  float2* s_tw1 = reinterpret_cast<float2*>(smem_raw) + C::CT * C::SMV;
   float2* s_tw = s_tw1 + F::L;
   const float2* twh = C::STAGE_TW ? s_tw : I.tw;   // tw[j] from shared or global memory
   if constexpr (C::STAGE_TW)
@@ -306,12 +305,6 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   auto slot_of = [&](int it) { return (it <= 1 || it > Np) ? 0 : it - 1; };
   auto kx_of = [&](int it) { return (it == 0 || it > Np) ? 0 : (it == 1 ? Np : it - 1); };
   for (int e = threadIdx.x; e < F::L; e += BLOCK) cp_async8(&s_tw1[e], I.tw1 + e, true);
-  // the symbol rows (16-byte pieces; a row is L floats)
-  for (int e = threadIdx.x; e < C::CT * (F::L / 4); e += BLOCK) {
-    const int cc = e / (F::L / 4), p = e % (F::L / 4);
-    const float* src = I.lreg + ((size_t)kx_of(item_of(cc)) * 2 + (cc & 1)) * Np + 4 * p;
-    cp_async16(s_lam + cc * F::L + 4 * p, src, true);
-  }
   // each item's column, rows 0 .. N-1 (zero-filled to L), once, into the
   // buffer of its even-half vector: the spectrum is slot-major (S[k * N + j]),
   // so a column is contiguous; thread -> (item, row) with the rows fastest
@@ -329,7 +322,7 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
 
   const int item = item_of(c), h = c & 1;
   float2* sm = reinterpret_cast<float2*>(smem_raw) + c * C::SMV;
-  const float* lam = s_lam + c * F::L;
+  const float* lam = I.lreg + ((size_t)kx_of(item) * 2 + h) * Np;
   float2 x[F::E];
   // both halves read the column from the even vector's buffer; the barrier
   // keeps the even half's transform from overwriting it before the odd half
@@ -353,7 +346,7 @@ __global__ void __launch_bounds__(BLOCK, ConvCfg<LOGL, BLOCK>::kBlocksPerSm) kr_
   F::template fwd<true>(x, sm, t, s_tw1);
   static_for<0, F::E>([&](auto rc) {
     constexpr int r = decltype(rc)::value;
-    x[r] = cscale(x[r], lam[F::template freq_index<r>(t)]);
+    x[r] = cscale(x[r], __ldg(&lam[F::template freq_index<r>(t)]));
   });
   F::template inv<true>(x, sm, t, s_tw1);
   store_nat<LOGL>(x, sm, t);
