@@ -330,7 +330,7 @@ def aggregate(times, world_size, pts_per_step, steps_list, reduce_max=None):
 # (kr_rows_r2c_n1023.md, kr_cols_conv_n1023.md, kr_rows_solve_dense_n1023.md,
 # k_tc_gemm_n1023.md, k_tc_gemm_n4095.md); absent = no capture of the
 # current kernel, reported as null.
-NCU_TRAFFIC = {("n1023", "kr_rows_r2c"): 12.66e6, ("n1023", "kr_cols_conv"): 50.46e6,
+NCU_TRAFFIC = {("n1023", "kr_rows_r2c"): 12.66e6, ("n1023", "kr_cols_conv"): 50.48e6,
                ("n1023", "kr_rows_solve<dense>"): 70.76e6, ("n1023", "k_tc_gemm(x+y)"): 89.4e6,
                ("n4095", "k_tc_gemm(x+y)"): 1733.6e6}
 
