@@ -65,8 +65,8 @@ def test_dense_setup_requires_the_dense_form(S):
 
 
 @pytest.mark.parametrize("N,alpha,g", [(1, 1.5, 1), (2, 1.3, 2), (5, 1.9, 0), (8, 1.6, 1), (9, 1.4, 2),
-                                       (31, 1.7, 2), (33, 1.2, 1), (63, 1.5, 1), (100, 1.3, 2), (255, 1.8, 2),
-                                       (257, 1.5, 1)])
+                                       (31, 1.7, 2), (33, 1.2, 1), (63, 1.5, 1), (64, 1.4, 2), (100, 1.3, 2),
+                                       (128, 1.6, 1), (255, 1.8, 2), (257, 1.5, 1)])
 def test_dense_step_parity(S, N, alpha, g):
     kappa, tau = 1.0, 0.02
     phi1 = WL.gaussian_bumps(N, 8, 5 + N)

@@ -94,7 +94,7 @@ def test_fp64_step_parity_ragged_sizes(S, N, alpha, g):
     assert np.abs(u - ref).max() <= 1e-10 * np.abs(ref).max()
 
 
-@pytest.mark.parametrize("N,alpha,g", [(63, 1.5, 1), (100, 1.3, 2), (255, 1.8, 2)])
+@pytest.mark.parametrize("N,alpha,g", [(63, 1.5, 1), (64, 1.4, 0), (100, 1.3, 2), (128, 1.6, 1), (255, 1.8, 2)])
 def test_fp32_step_parity(S, N, alpha, g):
     kappa, tau = 1.0, 0.02
     phi1 = WL.gaussian_bumps(N, 8, 5 + N)
