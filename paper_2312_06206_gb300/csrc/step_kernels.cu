@@ -405,7 +405,6 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
   const int row0 = blockIdx.x * NR;
   const int nrows = min(NR, N - row0);
   rows_inverse<T>(buf, S, g, NR, row0, nrows, vs, stw, tw);
-  const T half = T(0.5);
   // B^n and v1 = Q (v' + i J v'), staged through registers (in place).
   const int halfNp = Np >> 1;
   const int npairs = NR * halfNp;
@@ -434,40 +433,40 @@ k_rows_solve(const cx<T>* __restrict__ S, const T* __restrict__ u, const T* __re
         }
       }
     }
-    return;
-  }
-  T ra[MP], rb[MP];
+  } else {
+    T ra[MP], rb[MP];
 #pragma unroll
-  for (int it = 0; it < MP; ++it) {
-    const int t = threadIdx.x + it * blockDim.x;
-    ra[it] = T(0);
-    rb[it] = T(0);
-    if (t < npairs) {
-      const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
-      if (v < nrows) {
-        const int row = row0 + v;
-        const cx<T>* e = buf + v * vs;
-        if (k < N) ra[it] = rhs_at<T, DIFF>(rp, e, k, (size_t)row * N + k, u, uaux, phi2, Ch, Cl);
-        if (k2 < N) rb[it] = rhs_at<T, DIFF>(rp, e, k2, (size_t)row * N + k2, u, uaux, phi2, Ch, Cl);
+    for (int it = 0; it < MP; ++it) {
+      const int t = threadIdx.x + it * blockDim.x;
+      ra[it] = T(0);
+      rb[it] = T(0);
+      if (t < npairs) {
+        const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
+        if (v < nrows) {
+          const int row = row0 + v;
+          const cx<T>* e = buf + v * vs;
+          if (k < N) ra[it] = rhs_at<T, DIFF>(rp, e, k, (size_t)row * N + k, u, uaux, phi2, Ch, Cl);
+          if (k2 < N) rb[it] = rhs_at<T, DIFF>(rp, e, k2, (size_t)row * N + k2, u, uaux, phi2, Ch, Cl);
+        }
       }
     }
-  }
-  __syncthreads();
+    __syncthreads();
 #pragma unroll
-  for (int it = 0; it < MP; ++it) {
-    const int t = threadIdx.x + it * blockDim.x;
-    if (t < npairs) {
-      const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
-      cx<T>* e = buf + v * vs;
-      e[sidx<T>(k)] = cmul(mkc(ra[it], rb[it]), __ldg(&tw[k]));
-      e[sidx<T>(k2)] = cmul(mkc(rb[it], ra[it]), __ldg(&tw[k2]));
+    for (int it = 0; it < MP; ++it) {
+      const int t = threadIdx.x + it * blockDim.x;
+      if (t < npairs) {
+        const int v = t / halfNp, k = t % halfNp, k2 = Np - 1 - k;
+        cx<T>* e = buf + v * vs;
+        e[sidx<T>(k)] = cmul(mkc(ra[it], rb[it]), __ldg(&tw[k]));
+        e[sidx<T>(k2)] = cmul(mkc(rb[it], ra[it]), __ldg(&tw[k2]));
+      }
     }
-  }
-  __syncthreads();
-  gs_core<T>(buf, NR, vs, g, stw, tw, lam_s, lam_c);
-  for (int t = threadIdx.x; t < nrows * N; t += blockDim.x) {
-    const int v = t / N, k = t % N;
-    W[(size_t)(row0 + v) * N + k] = gs_out<T>(buf + v * vs, k, g, G);
+    __syncthreads();
+    gs_core<T>(buf, NR, vs, g, stw, tw, lam_s, lam_c);
+    for (int t = threadIdx.x; t < nrows * N; t += blockDim.x) {
+      const int v = t / N, k = t % N;
+      W[(size_t)(row0 + v) * N + k] = gs_out<T>(buf + v * vs, k, g, G);
+    }
   }
 }
 
