@@ -387,61 +387,43 @@ __global__ void k_reg_tables(Geom g, const double* __restrict__ lnat, double sca
 }
 
 // Element-wise conversions over a rows x cols array (source rows sld apart,
-// destination rows dld apart); one thread per element.
+// destination rows dld apart): thread -> column blockIdx.x * blockDim.x +
+// threadIdx.x of rows blockIdx.y, blockIdx.y + gridDim.y, ... (no index
+// division per element).
 struct Pitch2 {
-  int cols, sld, dld;
-  __device__ void at(size_t k, size_t* si, size_t* di) const {
-    const size_t r = k / (size_t)cols, c = k % (size_t)cols;
-    *si = r * sld + c;
-    *di = r * dld + c;
-  }
+  int rows, cols, sld, dld;
 };
-__global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, size_t n, Pitch2 p) {
-  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  size_t si, di;
-  if (k < n) {
-    p.at(k, &si, &di);
-    d[di] = (float)s[si];
-  }
+template <typename F>
+__device__ __forceinline__ void for_each_element(const Pitch2& p, F f) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= p.cols) return;
+  for (int r = blockIdx.y; r < p.rows; r += gridDim.y) f((size_t)r * p.sld + c, (size_t)r * p.dld + c);
 }
-__global__ void k_f2d(const float* __restrict__ s, double* __restrict__ d, size_t n, Pitch2 p) {
-  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  size_t si, di;
-  if (k < n) {
-    p.at(k, &si, &di);
-    d[di] = (double)s[si];
-  }
+__global__ void k_d2f(const double* __restrict__ s, float* __restrict__ d, Pitch2 p) {
+  for_each_element(p, [&](size_t si, size_t di) { d[di] = (float)s[si]; });
 }
-
-__global__ void k_split_d2ff(const double* __restrict__ s, float* __restrict__ hi, float* __restrict__ lo, size_t n,
-                             Pitch2 p) {
-  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  size_t si, di;
-  if (k < n) {
-    p.at(k, &si, &di);
+__global__ void k_f2d(const float* __restrict__ s, double* __restrict__ d, Pitch2 p) {
+  for_each_element(p, [&](size_t si, size_t di) { d[di] = (double)s[si]; });
+}
+__global__ void k_split_d2ff(const double* __restrict__ s, float* __restrict__ hi, float* __restrict__ lo, Pitch2 p) {
+  for_each_element(p, [&](size_t si, size_t di) {
     const double v = s[si];
     const float h = (float)v;
     hi[di] = h;
     lo[di] = (float)(v - (double)h);
-  }
+  });
 }
 __global__ void k_join_ff2d(const float* __restrict__ hi, const float* __restrict__ lo, double* __restrict__ d,
-                            size_t n, Pitch2 p) {
-  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  size_t si, di;
-  if (k < n) {
-    p.at(k, &si, &di);
-    d[di] = (double)hi[si] + (double)lo[si];
-  }
+                            Pitch2 p) {
+  for_each_element(p, [&](size_t si, size_t di) { d[di] = (double)hi[si] + (double)lo[si]; });
 }
 __global__ void k_join_ff2f(const float* __restrict__ hi, const float* __restrict__ lo, float* __restrict__ d,
-                            size_t n, Pitch2 p) {
-  const size_t k = blockIdx.x * (size_t)blockDim.x + threadIdx.x;
-  size_t si, di;
-  if (k < n) {
-    p.at(k, &si, &di);
-    d[di] = hi[si] + lo[si];
-  }
+                            Pitch2 p) {
+  for_each_element(p, [&](size_t si, size_t di) { d[di] = hi[si] + lo[si]; });
+}
+// grid of a conversion: 256 threads a block across a row, rows over y
+inline dim3 pitch_grid(int rows, int cols) {
+  return dim3((unsigned)((cols + 255) / 256), (unsigned)(rows < 65535 ? rows : 65535));
 }
 
 inline unsigned nblk(size_t n, int bs) { return (unsigned)((n + bs - 1) / bs); }
@@ -473,37 +455,32 @@ cudaError_t launch_riesz1d(double* a, int n, double alpha, cudaStream_t st) {
 }
 
 cudaError_t launch_convert_d2f(const double* s, float* d, int rows, int cols, int sld, int dld, cudaStream_t st) {
-  const size_t n = (size_t)rows * cols;
-  if (n == 0) return cudaSuccess;
-  k_d2f<<<nblk(n, 256), 256, 0, st>>>(s, d, n, Pitch2{cols, sld, dld});
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_d2f<<<pitch_grid(rows, cols), 256, 0, st>>>(s, d, Pitch2{rows, cols, sld, dld});
   return cudaGetLastError();
 }
 cudaError_t launch_split_d2ff(const double* s, float* hi, float* lo, int rows, int cols, int sld, int dld,
                               cudaStream_t st) {
-  const size_t n = (size_t)rows * cols;
-  if (n == 0) return cudaSuccess;
-  k_split_d2ff<<<nblk(n, 256), 256, 0, st>>>(s, hi, lo, n, Pitch2{cols, sld, dld});
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_split_d2ff<<<pitch_grid(rows, cols), 256, 0, st>>>(s, hi, lo, Pitch2{rows, cols, sld, dld});
   return cudaGetLastError();
 }
 cudaError_t launch_join_ff2d(const float* hi, const float* lo, double* d, int rows, int cols, int sld, int dld,
                              cudaStream_t st) {
-  const size_t n = (size_t)rows * cols;
-  if (n == 0) return cudaSuccess;
-  k_join_ff2d<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n, Pitch2{cols, sld, dld});
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_join_ff2d<<<pitch_grid(rows, cols), 256, 0, st>>>(hi, lo, d, Pitch2{rows, cols, sld, dld});
   return cudaGetLastError();
 }
 cudaError_t launch_join_ff2f(const float* hi, const float* lo, float* d, int rows, int cols, int sld, int dld,
                              cudaStream_t st) {
-  const size_t n = (size_t)rows * cols;
-  if (n == 0) return cudaSuccess;
-  k_join_ff2f<<<nblk(n, 256), 256, 0, st>>>(hi, lo, d, n, Pitch2{cols, sld, dld});
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_join_ff2f<<<pitch_grid(rows, cols), 256, 0, st>>>(hi, lo, d, Pitch2{rows, cols, sld, dld});
   return cudaGetLastError();
 }
 
 cudaError_t launch_convert_f2d(const float* s, double* d, int rows, int cols, int sld, int dld, cudaStream_t st) {
-  const size_t n = (size_t)rows * cols;
-  if (n == 0) return cudaSuccess;
-  k_f2d<<<nblk(n, 256), 256, 0, st>>>(s, d, n, Pitch2{cols, sld, dld});
+  if (rows <= 0 || cols <= 0) return cudaSuccess;
+  k_f2d<<<pitch_grid(rows, cols), 256, 0, st>>>(s, d, Pitch2{rows, cols, sld, dld});
   return cudaGetLastError();
 }
 
