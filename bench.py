@@ -29,6 +29,7 @@ instance (cycling through the three alpha), rank 0 only.
 from __future__ import annotations
 
 import argparse
+import contextlib
 import json
 import math
 import os
@@ -77,6 +78,17 @@ def _args():
     ap.add_argument("--acc-steps", type=int, default=1000,
                     help="steps of the accuracy check (FP32 form vs plain FP64 from the same data)")
     return ap.parse_args()
+
+
+def _nvtx(name):
+    """An NVTX range around the timed steps, so that a profiler can be told
+    to capture those launches alone (e.g. ncu --nvtx --nvtx-include
+    "timed_steps/"); a no-op where torch has no NVTX."""
+    try:
+        import torch
+        return torch.cuda.nvtx.range(name)
+    except Exception:
+        return contextlib.nullcontext()
 
 
 def _dist():
@@ -540,10 +552,11 @@ def run_batch(a):
     sampler.start()
     barrier()
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(a.steps)]
-    for k in range(a.steps):
-        evs[k][0].record(stream)
-        graph.launch(1)
-        evs[k][1].record(stream)
+    with _nvtx("timed_steps"):
+        for k in range(a.steps):
+            evs[k][0].record(stream)
+            graph.launch(1)
+            evs[k][1].record(stream)
     barrier()
     ms = sum(e0.elapsed_time(e1) for e0, e1 in evs)
     clocks = sampler.stop()
@@ -763,14 +776,15 @@ def main():
             graph = S.SadiGraph(ctxs, 1)
         barrier()
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
-        for k in range(K):
-            flush.zero_()
-            evs[k][0].record(stream)
-            if graph is not None:
-                graph.launch(1)
-            else:
-                step_all(ctxs)
-            evs[k][1].record(stream)
+        with _nvtx("timed_steps"):
+            for k in range(K):
+                flush.zero_()
+                evs[k][0].record(stream)
+                if graph is not None:
+                    graph.launch(1)
+                else:
+                    step_all(ctxs)
+                evs[k][1].record(stream)
         barrier()
         if graph is not None:
             graph.close()
