@@ -412,7 +412,9 @@ def roofline_of(phase_ms, N, Np, dense, ninst, workload):
     kernel's bound is the roof its algorithmic intensity (method flops per
     method byte) meets first: HBM below the ridge FP32 peak / HBM peak, the
     FP32 pipes above it; a kernel with no method flops is HBM-bound."""
-    reg = Np <= 1024
+    # the register path: both forms up to N' = 1024, the dense form's FFT part
+    # at N' = 2048 too
+    reg = Np <= 1024 or (dense and Np == 2048)
     pre = "kr_" if reg else "k_"
     conv = "kr_cols_conv" if reg else ("k_conv3_a+b+c" if Np == 8192 else "k_cols_conv")   # three passes at 8192
     if dense:

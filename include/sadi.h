@@ -177,8 +177,10 @@ sadi_status sadi_set_initial(sadi_ctx *ctx, const double *phi1, const double *ph
 sadi_status sadi_step(sadi_ctx *ctx, int nsteps);
 
 /* Advance each of count contexts by nsteps time steps (asynchronous), as
- * sadi_step would, but batched: FP32 and FP32_DENSE contexts with FFT length
- * N' <= 1024 are grouped by precision and N' (at most 32 per group) and each
+ * sadi_step would, but batched: FP32 contexts with FFT length N' <= 1024 and
+ * FP32_DENSE contexts with N' <= 2048 (unless explicit tiles keep them on
+ * the shared-memory engine, see sadi_set_tiles) are grouped by precision
+ * and N' (at most 32 per group) and each
  * group runs one launch per kernel for all its members (independent problems
  * of possibly different N, alpha, kappa, tau and g; both dense sweeps of up
  * to 8 members in one GEMM launch); the other contexts step one after
@@ -212,7 +214,7 @@ sadi_status sadi_batch_set_initial(sadi_batch *batch, int k, const double *phi1,
 
 /* Advance every member by nsteps >= 0 steps (asynchronous on the batch's
  * stream): batched launches as sadi_batch_step makes them (one launch per
- * kernel for each group of equal FFT length <= 1024), and once every member
+ * kernel for each group of equal FFT length on the register path), and once every member
  * is past its n = 0 step, replays of a CUDA graph of one batched step
  * (captured on first use; FP32 forms without source terms or profiling --
  * otherwise the steps are launched directly).  Results are identical to
@@ -282,9 +284,10 @@ void sadi_graph_destroy(sadi_graph *graph);
  * sadi_batch_step steps it (up to 32 contexts per group) -- SADI_PREC_FP32
  * (Gohberg-Semencul FFT sweeps) and, unless flags bit 0 is set or
  * s a_0 > 0.2 (the dense form's accuracy limit above),
- * SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, on the
- * shared-memory FFT engine (N' > 1024), the work decomposition of
- * sadi_set_tiles by coordinate descent.  flags bit 1 keeps the precision the
+ * SADI_PREC_FP32_DENSE (tensor-core dense-inverse sweeps) -- and, for a
+ * form on the shared-memory FFT engine (FP32 at N' > 1024, FP32_DENSE at
+ * N' > 2048), the work decomposition of sadi_set_tiles by coordinate
+ * descent.  flags bit 1 keeps the precision the
  * contexts already have (FP32 or FP32_DENSE, equal within each N) and tunes
  * only the tiles.  Each context is left with g, the fastest precision and
  * tiles of its group, uninitialised (call sadi_set_initial next).  Must precede sadi_set_initial and
@@ -354,7 +357,13 @@ sadi_status sadi_get_info(const sadi_ctx *ctx, int *fft_len, int *border_rank);
  * return SADI_EINVAL and leave the setting unchanged.  The tiles change the
  * order of some rounding steps (the column convolution multiplies the symbol
  * fused into its transforms or in a separate pass), so results of different
- * tiles agree to rounding, not bitwise.  Call after sadi_set_options. */
+ * tiles agree to rounding, not bitwise.  The tiles are those of the
+ * shared-memory FFT engine; the register path (FP32 at N' <= 1024,
+ * FP32_DENSE at N' <= 2048) has none.  At N' = 2048 the dense form's FFT
+ * part runs on the register path by default, and explicit (non-zero) tiles
+ * move it to the shared-memory engine (all zero moves it back); such a
+ * change re-lays the state and must precede sadi_set_initial and
+ * sadi_set_source (SADI_ESTATE otherwise).  Call after sadi_set_options. */
 sadi_status sadi_set_tiles(sadi_ctx *ctx, int rows, int conv_cols, int solve_cols);
 
 /* Current tiles of the selected precision: tiles[0..2] = rows, conv_cols,

@@ -196,10 +196,10 @@ sadi_status apply(std::vector<sadi_ctx*>& grp, int g, const Cand& cd) {
     c->n = 0;
     sadi_status st = sadi_set_options(c, g, cd.prec);
     if (st != SADI_OK) return st;
-    if (cd.t.rows > 0) {
-      st = sadi_set_tiles(c, cd.t.rows, cd.t.conv_cols, cd.t.solve_cols);
-      if (st != SADI_OK) return st;
-    }
+    // zero tiles restore the defaults (and, for the dense form at N' = 2048,
+    // the register path that an earlier candidate's tiles may have left)
+    st = sadi_set_tiles(c, cd.t.rows, cd.t.conv_cols, cd.t.solve_cols);
+    if (st != SADI_OK) return st;
   }
   return SADI_OK;
 }
@@ -228,28 +228,31 @@ sadi_status sadi_autotune(sadi_ctx** ctxs, int count, int g, int flags) {
   for (int k = 0; k < count; ++k) by_n[ctxs[k]->g.N].push_back(ctxs[k]);
   for (auto& kv : by_n) {
     std::vector<sadi_ctx*>& all = kv.second;
-    // register-path contexts step in batches of up to kMaxBatch; the
-    // shared-memory engine steps each context on its own
-    const bool reg = all[0]->reg_path;
-    const size_t cap = reg ? (size_t)kMaxBatch : 1;
-    std::vector<sadi_ctx*> grp(all.begin(), all.begin() + std::min(all.size(), cap));
-    const int N = kv.first, Np = grp[0]->g.Np;
+    const int N = kv.first, Np = all[0]->g.Np, logNp = all[0]->g.logNp;
     std::vector<int> precs{SADI_PREC_FP32};
     // the dense form's split-BF16 error scales with E = H^-1 - I, i.e. with
     // s a_0 (s = kappa tau^2 / (2 h^alpha)); it is offered only while E is small
     double a0 = 0.0;
-    if (cudaMemcpy(&a0, grp[0]->a1, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
-      return cuda_fail(grp[0], cudaErrorUnknown, "reading a_0");
-    const bool dense_ok = grp[0]->s * a0 <= kDenseMaxSA0;
+    if (cudaMemcpy(&a0, all[0]->a1, sizeof(double), cudaMemcpyDeviceToHost) != cudaSuccess)
+      return cuda_fail(all[0], cudaErrorUnknown, "reading a_0");
+    const bool dense_ok = all[0]->s * a0 <= kDenseMaxSA0;
     if (!(flags & 1) && dense_ok) precs.push_back(SADI_PREC_FP32_DENSE);
     if (flags & 2) {
       // keep the precision the group was created with; tune its tiles only
-      const int p0 = grp[0]->prec;
+      const int p0 = all[0]->prec;
       for (sadi_ctx* c : all)
         if (c->prec != p0) return fail(c, SADI_EINVAL, "flags bit 1: contexts of one N differ in precision");
-      if (p0 == SADI_PREC_FP64) return fail(grp[0], SADI_EUNSUPPORTED, "flags bit 1 tunes the FP32 forms only");
+      if (p0 == SADI_PREC_FP64) return fail(all[0], SADI_EUNSUPPORTED, "flags bit 1 tunes the FP32 forms only");
       precs.assign(1, p0);
     }
+    // register-path contexts step in batches of up to kMaxBatch, the
+    // shared-memory engine one context after another; every candidate is
+    // timed on the same group (the step time of the whole group), as large
+    // as a register-path candidate batches
+    bool any_reg = false;
+    for (int prec : precs) any_reg = any_reg || reg_path_supported(logNp, prec);
+    const size_t cap = any_reg ? (size_t)kMaxBatch : 1;
+    std::vector<sadi_ctx*> grp(all.begin(), all.begin() + std::min(all.size(), cap));
     std::string log = fmt("N=%.0f N'=%.0f batch=%.0f s*a0=%.3g:", N, Np, (double)grp.size(), grp[0]->s * a0);
     Cand best{SADI_PREC_FP32, Tiles{0, 0, 0}};
     double best_ms = 1e30;
@@ -259,7 +262,7 @@ sadi_status sadi_autotune(sadi_ctx** ctxs, int count, int g, int flags) {
       if (st != SADI_OK) return st;
       double ms = 0;
       if ((st = time_group(grp, 5, &ms)) != SADI_OK) return st;
-      if (!reg) {
+      if (!reg_path_supported(logNp, prec)) {
         // coordinate descent over the shared-memory engine's decomposition
         // (the dense form leaves the y-sweep tile unused); the column
         // convolution may also run as three passes (kConvThreePass)

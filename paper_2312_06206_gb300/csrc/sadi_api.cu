@@ -98,6 +98,16 @@ int log2i(int v) {
 
 size_t esize(int prec) { return prec == SADI_PREC_FP64 ? sizeof(double) : sizeof(float); }
 
+// The FFT engine of the context's precision: the register path where it
+// serves that precision (both FP32 forms up to N' = 1024, the dense form's FFT
+// part up to N' = 2048), except that explicit tiles keep the dense form on
+// the shared-memory engine at lengths where the GS form runs there too.  The
+// state's row pitch follows the engine (alloc_state).
+bool wants_reg_path(const sadi_ctx* c) {
+  if (!reg_path_supported(c->g.logNp, c->prec)) return false;
+  return !(c->tiles_explicit && !reg_path_supported(c->g.logNp, SADI_PREC_FP32));
+}
+
 sadi_status alloc_state(sadi_ctx* c) {
   // row pitch of the N x N arrays: the FP32 forms on the register path pad
   // their rows to 128 bytes (16-byte vector accesses in the sweep GEMM's
@@ -298,7 +308,7 @@ sadi_status create_impl(int eq, int N, double alpha, double kappa, double tau, c
     c->err = "sadi_create: Durbin recursion broke down (H not numerically SPD)";
     return bail(SADI_ENOTSPD);
   }
-  c->reg_path = reg_path_supported(g.logNp);
+  c->reg_path = wants_reg_path(c);
   if ((e = run_reg_tables(g, c->lnat, scale, c->lamc64, c->lams64, c->rtw1, c->rlreg, c->rlamc, c->rlams, st)))
     return bail(cuda_fail(c, e, "register-path tables"));
   if ((e = step_setup_attributes<float>())) return bail(cuda_fail(c, e, "kernel attributes"));
@@ -351,6 +361,7 @@ sadi_status sadi_set_options(sadi_ctx* c, int g, int prec) {
   if (prec != c->prec) {
     if (c->F) return fail(c, SADI_ESTATE, "set the precision before sadi_set_source");
     c->prec = prec;
+    c->reg_path = wants_reg_path(c);
     if (c->Fconv) cudaFree(c->Fconv);
     c->Fconv = nullptr;
     return alloc_state(c);
@@ -591,7 +602,8 @@ sadi_status step_reg_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
 }
 
 // One step of count dense-form contexts with equal FFT length on stream st:
-// the FFT part batched (register path, N' <= 1024; count == 1 otherwise), then
+// the FFT part batched (register path, N' <= 2048), or one member after
+// another (shared-memory engine), then
 // the x-sweep and y-sweep GEMMs batched (at most kTcMaxBatch per launch).
 sadi_status step_dense_group(sadi_ctx* const* cs, int count, cudaStream_t st_) {
   sadi_ctx* c = cs[0];
@@ -1006,12 +1018,34 @@ sadi_status sadi_get_info(const sadi_ctx* c, int* fft_len, int* border_rank) {
 
 sadi_status sadi_set_tiles(sadi_ctx* c, int rows, int conv_cols, int solve_cols) {
   if (!c) return SADI_EINVAL;
+  if (c->broken) return fail(c, SADI_ESTATE, "context unusable after a CUDA error");
   Tiles t{rows, conv_cols, solve_cols};
   const bool f64 = c->prec == SADI_PREC_FP64;
-  if (rows == 0 && conv_cols == 0 && solve_cols == 0)
-    t = f64 ? default_tiles<double>(c->g.Np, c->g.N) : default_tiles<float>(c->g.Np, c->g.N);
+  const bool dflt = rows == 0 && conv_cols == 0 && solve_cols == 0;
+  if (dflt) t = f64 ? default_tiles<double>(c->g.Np, c->g.N) : default_tiles<float>(c->g.Np, c->g.N);
   const bool ok = f64 ? tiles_valid<double>(c->g, t) : tiles_valid<float>(c->g, t);
   if (!ok) return fail(c, SADI_EINVAL, "tile sizes invalid for this N and precision");
+  // the engine these tiles select (the dense form at N' = 2048: explicit
+  // tiles the shared-memory engine, the defaults the register path); the
+  // FP64 path's tiles leave the FP32 forms' choice alone
+  const bool was_explicit = c->tiles_explicit;
+  const bool expl = f64 ? was_explicit : !dflt;
+  c->tiles_explicit = expl;
+  const bool reg = wants_reg_path(c);
+  c->tiles_explicit = was_explicit;
+  if (!f64 && t.conv_cols == kConvThreePass && (reg || !conv3_supported(c->g.logNp)))
+    return fail(c, SADI_EINVAL, "the three-pass convolution serves FFT lengths 2048 .. 8192");
+  if (reg != c->reg_path) {
+    if (c->initialized || c->F)
+      return fail(c, SADI_ESTATE,
+                  "tiles that change the FFT engine (dense form, N' = 2048) must precede sadi_set_initial and "
+                  "sadi_set_source");
+    c->tiles_explicit = expl;
+    c->reg_path = reg;
+    const sadi_status sa = alloc_state(c);
+    if (sa != SADI_OK) return sa;
+  }
+  c->tiles_explicit = expl;
   if (!f64 && t.conv_cols == kConvThreePass) {
     const sadi_status s3 = ensure_conv3(c);
     if (s3 != SADI_OK) return s3;

@@ -38,7 +38,10 @@ struct sadi_ctx {
   double2* stw64 = nullptr;  // per-stage FFT twiddles
   float2* stw32 = nullptr;
   Tiles tiles64{}, tiles32{};
-  // FP32 register-FFT path tables (N' <= 1024)
+  // tiles set explicitly (not the defaults): at N' = 2048 they keep the
+  // dense form on the shared-memory engine
+  bool tiles_explicit = false;
+  // FP32 register-FFT path tables (N' <= 2048)
   float2* rtw1 = nullptr;
   float* rlreg = nullptr;
   float2* rlamc = nullptr;

@@ -143,7 +143,8 @@ bool tiles_valid(const Geom& g, const Tiles& t);
 template <typename T>
 cudaError_t step_setup_attributes();
 
-// FP32 register-FFT path (FFT length N' <= 1024).  One instance of a batch:
+// FP32 register-FFT path (FFT length N' <= 1024; N' = 2048 for the dense
+// form's FFT part).  One instance of a batch:
 // natural-order tables and the in-place double-float state.
 struct RegInst {
   const float2* tw1;    // [N'] two-level FFT twiddles exp(-2 pi i t k1 / N') at [k1 * TT + t]
@@ -182,7 +183,9 @@ struct RegBatch {
   int count;
   RegInst in[kMaxBatch];
 };
-bool reg_path_supported(int logNp);
+// whether a context of FFT length 2^logNp and precision prec (SADI_PREC_*)
+// can step on the register path
+bool reg_path_supported(int logNp, int prec);
 // One step of every instance of the batch (all with FFT length 2^logNp);
 // max_n = the largest N in the batch.  dense: only the row FFT, the column
 // convolution and the B^n kernel run (events 0..2), the latter writing B^n to

@@ -1,6 +1,7 @@
 // step_reg.cuh -- the S-ADI step (Sec. 3, eq. "ADI scheme equivalent") for
-// FFT lengths N' <= 1024 with the register-resident two-level FFT of
-// regfft.cuh.  Same four kernels and the same mathematics as step_kernels.cu:
+// FFT lengths N' <= 1024 (both FP32 forms) and N' = 2048 (the dense-inverse
+// form's FFT part) with the register-resident two-level FFT of regfft.cuh.
+// Same four kernels and the same mathematics as step_kernels.cu:
 //   kr_rows_r2c    rows of the increment d^n = u^n - u^{n-1} -> half spectrum
 //                  along x (natural slots)
 //   kr_cols_conv   per x frequency: y FFT (even/odd halves) x symbol, inverse
@@ -60,8 +61,9 @@ struct RowCfg {
   static constexpr size_t bytes_r2c = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
   static constexpr size_t bytes_solve = (size_t)VB * SMV * sizeof(float2) + tw_bytes;
   // resident blocks per SM promised to the compiler (its register budget):
-  // four narrow blocks, or one wide block of up to 2048 threads
-  static constexpr int kMinBlocks = BLOCK >= 512 ? 1 : 4;
+  // four narrow blocks (two at N' = 2048, whose 64 elements per lane need
+  // the full 255 registers), or one wide block of up to 2048 threads
+  static constexpr int kMinBlocks = BLOCK >= 512 ? 1 : (LOGL >= 11 ? 2 : 4);
 };
 // The convolution kernel: vectors owned by warps (as in the row kernels), CT
 // per block; the FFT buffers and the staged table tw1 (the symbol rows are
@@ -79,7 +81,7 @@ struct ConvCfg {
   // the half-angle twiddles tw[0 .. L) are staged too when the shared memory
   // still admits the block count of the launch bounds
   static constexpr size_t bytes_base = (size_t)CT * SMV * sizeof(float2) + (size_t)F::L * sizeof(float2);
-  static constexpr int kBlocksPerSm = BLOCK >= 256 ? 2 : 4;
+  static constexpr int kBlocksPerSm = BLOCK >= 256 || LOGL >= 11 ? 2 : 4;
   static constexpr bool STAGE_TW =
       kBlocksPerSm * (bytes_base + F::L * sizeof(float2) + 1024) <= (size_t)228 * 1024;
   static constexpr size_t bytes = bytes_base + (STAGE_TW ? F::L * sizeof(float2) : 0);
@@ -699,8 +701,21 @@ inline bool fewer_waves(int shape, int count, int max_n, int narrow_rows, int wi
   return (wb + sms * ow - 1) / (sms * ow) < (nb + sms * on - 1) / (sms * on);
 }
 
+// FFT lengths of the register path: both FP32 forms up to 2^kRegMaxLogGS, the
+// dense-inverse form's FFT part (no GS sweeps) up to 2^kRegMaxLogDense.  At
+// N' = 2048 the GS sweep kernels would hold 64 elements per lane at the full
+// register budget, 2 blocks per SM, and measured slower than the
+// shared-memory engine's; the dense form's three kernels measured faster.
+constexpr int kRegMaxLogGS = 10;
+constexpr int kRegMaxLogDense = 11;
+
 template <int LOGL>
 cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaEvent_t* ev, bool dense) {
+  static_assert(LOGL <= kRegMaxLogDense, "register path FFT length");
+  // the GS form's kernels (and the wide row blocks, N' = 1024 only) exist at
+  // the lengths that use them
+  constexpr bool kGS = LOGL <= kRegMaxLogGS;
+  if (!kGS && !dense) return cudaErrorInvalidValue;
   using RC = RowCfg<LOGL, kRowBlock>;
   using CC = ColCfg<LOGL, kColBlock>;
   using VC = ConvCfg<LOGL, kConvBlock>;
@@ -739,15 +754,18 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
     }
     if ((e = cudaFuncSetAttribute(kr_rows_r2c<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                   (int)RC::bytes_r2c)) ||
-        (e = cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)RC::bytes_solve)) ||
         (e = cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock, true>,
                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)RC::bytes_solve)) ||
         (e = cudaFuncSetAttribute(kr_cols_conv<LOGL, kConvBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)VC::bytes)) ||
-        (e = cudaFuncSetAttribute(kr_cols_solve<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                  (int)CC::bytes_solve)))
+                                  (int)VC::bytes)))
       return e;
+    if constexpr (kGS) {
+      if ((e = cudaFuncSetAttribute(kr_rows_solve<LOGL, kRowBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)RC::bytes_solve)) ||
+          (e = cudaFuncSetAttribute(kr_cols_solve<LOGL, kColBlock>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                    (int)CC::bytes_solve)))
+        return e;
+    }
     attr_done[dev].store(1, std::memory_order_release);
   }
   const dim3 rgrid((max_n + RC::VB - 1) / RC::VB, b.count);
@@ -776,22 +794,34 @@ cudaError_t launch_reg_impl(const RegBatch& b, int max_n, cudaStream_t st, cudaE
   };
   cudaError_t e;
   if (ev) cudaEventRecord(ev[0], st);
-  if (wide[0]) e = launch(kr_rows_r2c<LOGL, kRowBlockWide>, wgrid, kRowBlockWide, RW::bytes_r2c);
-  else e = launch(kr_rows_r2c<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_r2c);
+  if constexpr (LOGL == 10) {
+    if (wide[0]) e = launch(kr_rows_r2c<LOGL, kRowBlockWide>, wgrid, kRowBlockWide, RW::bytes_r2c);
+    else e = launch(kr_rows_r2c<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_r2c);
+  } else {
+    e = launch(kr_rows_r2c<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_r2c);
+  }
   if (e != cudaSuccess) return e;
   if (ev) cudaEventRecord(ev[1], st);
   if ((e = launch(kr_cols_conv<LOGL, kConvBlock>, cgrid, kConvBlock, VC::bytes))) return e;
   if (ev) cudaEventRecord(ev[2], st);
   if (dense) {
-    if (wide[2]) return launch(kr_rows_solve<LOGL, kRowBlockWide, true>, wgrid, kRowBlockWide, RW::bytes_solve);
+    if constexpr (LOGL == 10) {
+      if (wide[2]) return launch(kr_rows_solve<LOGL, kRowBlockWide, true>, wgrid, kRowBlockWide, RW::bytes_solve);
+    }
     return launch(kr_rows_solve<LOGL, kRowBlock, true>, rgrid, kRowBlock, RC::bytes_solve);
   }
-  if (wide[1]) e = launch(kr_rows_solve<LOGL, kRowBlockWide>, wgrid, kRowBlockWide, RW::bytes_solve);
-  else e = launch(kr_rows_solve<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_solve);
-  if (e != cudaSuccess) return e;
-  if (ev) cudaEventRecord(ev[3], st);
-  if ((e = launch(kr_cols_solve<LOGL, kColBlock>, sgrid, kColBlock, CC::bytes_solve))) return e;
-  if (ev) cudaEventRecord(ev[4], st);
+  if constexpr (kGS) {
+    if constexpr (LOGL == 10) {
+      if (wide[1]) e = launch(kr_rows_solve<LOGL, kRowBlockWide>, wgrid, kRowBlockWide, RW::bytes_solve);
+      else e = launch(kr_rows_solve<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_solve);
+    } else {
+      e = launch(kr_rows_solve<LOGL, kRowBlock>, rgrid, kRowBlock, RC::bytes_solve);
+    }
+    if (e != cudaSuccess) return e;
+    if (ev) cudaEventRecord(ev[3], st);
+    if ((e = launch(kr_cols_solve<LOGL, kColBlock>, sgrid, kColBlock, CC::bytes_solve))) return e;
+    if (ev) cudaEventRecord(ev[4], st);
+  }
   return cudaSuccess;
 }
 

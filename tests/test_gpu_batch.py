@@ -20,8 +20,8 @@ def S():
     return sadi
 
 
-# (N, alpha, kappa, tau, g, prec): register path (N' = 64, 256), shared-memory
-# engine (N' = 2048), both FP32 forms
+# (N, alpha, kappa, tau, g, prec): register path (N' = 64, 256, and the
+# dense form at N' = 2048), shared-memory engine (the GS form at N' = 2048)
 SPECS = [(63, 1.5, 1.0, 0.02, 1, 1), (50, 1.2, 0.7, 0.03, 2, 1), (200, 1.8, 1.3, 0.01, 1, 2),
          (255, 1.6, 1.0, 0.005, 1, 2), (1500, 1.4, 0.5, 1e-3, 1, 1), (1100, 1.7, 0.8, 1e-3, 2, 2)]
 
@@ -47,9 +47,9 @@ def test_graph_replay_matches_batch_stepping_bitwise(S):
     S.sadi_batch_step(run, 1)                 # the n = 0 step is not replayed
     g = S.SadiGraph(run, nsteps=2)
     assert all(s.get()[1] == 1 for s in run)  # capture runs nothing
-    # two steps: register groups (N' = 64 FP32: 4 kernels; N' = 256 dense: 3
-    # kernels + one launch of both sweep GEMMs), two shared-memory contexts
-    # (FP32: 3 + the y sweep on the transpose, 3; dense: 3 + 1)
+    # two steps: register groups (N' = 64 FP32: 4 kernels; N' = 256 and
+    # N' = 2048 dense: 3 kernels + one launch of both sweep GEMMs each), one
+    # shared-memory context (FP32: 3 + the y sweep on the transpose, 3)
     assert g.sadi_graph_kernels() == 2 * (4 + 4 + 6 + 4)
     g.launch(3)
     for s, w in zip(run, want):
@@ -117,12 +117,21 @@ def test_autotune_picks_a_form_per_n_and_keeps_parity(S):
 
 def test_autotune_can_keep_the_precision(S):
     # flags bit 1: tiles only, the precision each context was given stays
+    # (the GS form at N' = 2048 on the shared-memory engine has tiles; the
+    # dense form there runs on the register path, which has none)
     ctxs = [S.Sadi(1100, 1.5, 1.0, 0.01) for _ in range(2)]
-    ctxs[0].set_options(1, S.SADI_PREC_FP32_DENSE)
-    ctxs[1].set_options(1, S.SADI_PREC_FP32_DENSE)
+    ctxs[0].set_options(1, S.SADI_PREC_FP32)
+    ctxs[1].set_options(1, S.SADI_PREC_FP32)
     S.sadi_autotune(ctxs, 1, 2)
-    assert all(s.sadi_get_options() == (1, S.SADI_PREC_FP32_DENSE) for s in ctxs)
-    assert "fp32-gsfft" not in ctxs[0].sadi_tuning_log() and "tiles" in ctxs[0].sadi_tuning_log()
+    assert all(s.sadi_get_options() == (1, S.SADI_PREC_FP32) for s in ctxs)
+    assert "fp32-dense" not in ctxs[0].sadi_tuning_log() and "tiles" in ctxs[0].sadi_tuning_log()
+    dense = [S.Sadi(1100, 1.5, 1.0, 0.01) for _ in range(2)]
+    for s in dense:
+        s.set_options(1, S.SADI_PREC_FP32_DENSE)
+    S.sadi_autotune(dense, 1, 2)
+    assert all(s.sadi_get_options() == (1, S.SADI_PREC_FP32_DENSE) for s in dense)
+    assert "fp32-gsfft" not in dense[0].sadi_tuning_log() and "tiles" not in dense[0].sadi_tuning_log()
+    ctxs += dense
     f64 = S.Sadi(63, 1.5, 1.0, 0.01)
     with pytest.raises(S.SadiError) as ei:
         S.sadi_autotune([f64], 1, 2)

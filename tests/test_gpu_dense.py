@@ -90,13 +90,82 @@ def test_dense_full_size_1023(S):
 
 @pytest.mark.parametrize("N,alpha,g,steps", [(2047, 1.4, 1, 5), (4095, 1.7, 1, 3)])
 def test_dense_large_n_against_fp64(S, N, alpha, g, steps):
-    # N' = 2048, 4096: the FFT part on the shared-memory engine, the sweeps as
-    # 8 x 16 and 16 x 32 tiles of 128 x 256
+    # N' = 2048: the FFT part on the register path; N' = 4096: on the
+    # shared-memory engine; the sweeps as 8 x 16 and 16 x 32 tiles of 128 x 256
     tau, kappa = 5e-4, 0.5
     phi1 = WL.gaussian_bumps(N, 8, 2000 + N)
     u64 = _run(S, N, alpha, kappa, tau, g, phi1, None, steps, S.SADI_PREC_FP64)
     ud = _run(S, N, alpha, kappa, tau, g, phi1, None, steps, S.SADI_PREC_FP32_DENSE)
     assert O.rel_l2(ud, u64) <= 1e-5, O.rel_l2(ud, u64)
+
+
+@pytest.mark.parametrize("N,alpha,g", [(1025, 1.3, 2), (1100, 1.7, 1)])
+def test_dense_fft_engines_at_2048_against_oracle(S, N, alpha, g):
+    # N' = 2048 (ragged: N = 1025 is the smallest N of that length): the
+    # dense form's FFT part on the register path (64 elements per lane) by
+    # default, on the shared-memory engine with explicit tiles; both against
+    # the oracle element by element, and against each other
+    kappa, tau, steps = 0.8, 1e-3, 3
+    phi1 = WL.gaussian_bumps(N, 6, 900 + N)
+    phi2 = 0.2 * WL.random_field(N, 901 + N)
+    P = O.Problem(N, alpha, kappa, tau, -1.0, 1.0, g)
+    ref = O.run(P, phi1, phi2, steps, tier="fft")
+    us = {}
+    for engine in ("register", "shared"):
+        with S.Sadi(N, alpha, kappa, tau) as s:
+            s.set_options(g, S.SADI_PREC_FP32_DENSE)
+            if engine == "shared":
+                s.sadi_set_tiles(*s.sadi_get_tiles())
+            s.set_initial(phi1, phi2)
+            s.step(steps)
+            us[engine], n = s.get()
+        assert n == steps
+        u = us[engine]
+        assert O.rel_l2(u, ref) <= 1e-5, (engine, O.rel_l2(u, ref))
+        assert np.abs(u - ref).max() <= 1e-5 * np.abs(ref).max(), engine
+    # different kernels (rounding order), the same scheme
+    assert not np.array_equal(us["register"], us["shared"])
+    assert O.rel_l2(us["register"], us["shared"]) <= 1e-6
+
+
+def test_dense_engine_choice_at_2048(S):
+    # explicit tiles move a dense N' = 2048 context to the shared-memory
+    # engine and zeros move it back, before sadi_set_initial only; the FP64
+    # path's tiles and the GS form are unaffected
+    N, alpha, kappa, tau = 1100, 1.5, 1.0, 1e-3
+    phi1 = WL.gaussian_bumps(N, 4, 950)
+
+    def run(tiles_seq):
+        with S.Sadi(N, alpha, kappa, tau) as s:
+            s.set_options(1, S.SADI_PREC_FP32_DENSE)
+            for t in tiles_seq:
+                s.sadi_set_tiles(*t)
+            s.set_initial(phi1)
+            s.step(2)
+            return s.get()[0]
+    with S.Sadi(N, alpha, kappa, tau) as s:
+        s.set_options(1, S.SADI_PREC_FP32_DENSE)
+        t = s.sadi_get_tiles()
+    u_reg = run([])
+    u_shared = run([t])
+    assert not np.array_equal(u_reg, u_shared)
+    assert np.array_equal(run([t, (0, 0, 0)]), u_reg)
+    # three passes need the shared-memory engine: explicit tiles give it
+    assert O.rel_l2(run([(t[0], -1, t[2])]), u_shared) <= 1e-6
+    with S.Sadi(N, alpha, kappa, tau) as s:
+        s.set_options(1, S.SADI_PREC_FP32_DENSE)
+        s.set_initial(phi1)
+        with pytest.raises(S.SadiError) as ei:     # would re-lay the state
+            s.sadi_set_tiles(*t)
+        assert ei.value.status == S.SADI_ESTATE
+        s.step(1)                                  # still steps on the register path
+    # tiles set for the FP64 path do not move the dense form later
+    with S.Sadi(N, alpha, kappa, tau) as s:
+        s.sadi_set_tiles(*s.sadi_get_tiles())
+        s.set_options(1, S.SADI_PREC_FP32_DENSE)
+        s.set_initial(phi1)
+        s.step(2)
+        assert np.array_equal(s.get()[0], u_reg)
 
 
 def test_dense_source_term_and_second_order(S):
@@ -155,8 +224,9 @@ def test_dense_batch_matches_single_contexts(S):
 def test_long_run_fp32_forms_track_fp64(S, N):
     # 250 steps of the N=4095 precision workload's parameters (alpha 1.7,
     # kappa 0.5, tau 5e-4, g = -u^3): both FP32 forms stay within 1e-6 of the
-    # FP64 path.  N = 1023 runs the register FFT path, N = 2047 the
-    # shared-memory engine, whose packed k1 = 0 / k1 = N' column must keep
+    # FP64 path.  N = 1023 runs the register FFT path; at N = 2047 the GS
+    # form runs on the shared-memory engine (the dense form's FFT part on the
+    # register path), whose packed k1 = 0 / k1 = N' column must keep
     # the small low-frequency symbol free of cancellation (before that was
     # fixed the drift here was about 4e-6).
     alpha, kappa, tau, g, steps = 1.7, 0.5, 5e-4, 1, 250

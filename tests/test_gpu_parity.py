@@ -217,10 +217,13 @@ def test_dense_batch_over_two_gemm_launches_matches_single_contexts(S):
         s.close()
 
 
-def test_dense_batch_on_the_shared_memory_engine_matches_single_contexts(S):
-    # dense-form contexts of one FFT length on the shared-memory engine
-    # (N' = 2048): their FFT kernels run one after another, both sweeps of
-    # all of them in one GEMM launch; bitwise equal to single-context stepping
+@pytest.mark.parametrize("engine", ["register", "shared"])
+def test_dense_batch_at_2048_matches_single_contexts(S, engine):
+    # dense-form contexts of FFT length 2048: on the register path (the
+    # default) one launch per FFT kernel covers all of them; with explicit
+    # tiles they stay on the shared-memory engine, whose FFT kernels run one
+    # context after another.  Both sweeps of all of them in one GEMM launch;
+    # bitwise equal to single-context stepping either way.
     specs = [(1500, 1.4, 1.0, 1e-3, 1), (1100, 1.7, 0.8, 1e-3, 2), (2047, 1.2, 1.2, 5e-4, 0)]
 
     def make():
@@ -228,6 +231,8 @@ def test_dense_batch_on_the_shared_memory_engine_matches_single_contexts(S):
         for k, (N, al, ka, ta, g) in enumerate(specs):
             s = S.Sadi(N, al, ka, ta)
             s.set_options(g, S.SADI_PREC_FP32_DENSE)
+            if engine == "shared":
+                s.sadi_set_tiles(*s.sadi_get_tiles())
             s.set_initial(WL.gaussian_bumps(N, 4, 700 + k))
             out.append(s)
         return out
@@ -314,7 +319,7 @@ def test_manufactured_solution_second_order_on_gpu(S, prec):
 
 @pytest.mark.parametrize("N,alpha,g,steps", [(2047, 1.4, 1, 5), (4095, 1.7, 1, 3)])
 def test_large_n_fp32_against_fp64(S, N, alpha, g, steps):
-    # N' = 2048 and 4096 run on the shared-memory FFT engine in both precisions;
+    # N' = 2048 (the GS form) and 4096 run on the shared-memory FFT engine;
     # the FP64 path is itself checked against the oracle at N = 2047 (2 steps).
     tau, kappa = 5e-4, 0.5
     phi1 = WL.gaussian_bumps(N, 8, 2000 + N)
