@@ -1,4 +1,4 @@
-// regfft.cuh -- register-resident two-level FFT of length L = TT * E (L <= 1024).
+// regfft.cuh -- register-resident two-level FFT of length L = TT * E (L <= 2048).
 //
 // A vector of length L is owned by TT threads; thread t holds E elements in
 // registers.  Forward transform (natural input x[q] = v[t + TT q]):
