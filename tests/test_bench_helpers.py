@@ -48,3 +48,15 @@ def test_roofline_names_bounds_and_traffic():
     assert r8["traffic"] is None
     r4 = bench.roofline_of([0.15, 0.41, 0.30, 0.58], 4095, 4096, True, 1, "n4095")
     assert "k_cols_conv" in r4["kernels"] and r4["kernel"] == "k_tc_gemm(x+y)"
+
+
+def test_roofline_names_at_fft_length_2048():
+    # N' = 2048: the dense form's FFT part runs on the register path, the GS
+    # form on the shared-memory engine (y sweep on the transpose)
+    phase_ms = [0.027, 0.068, 0.080, 0.100]
+    rd = bench.roofline_of(phase_ms, 2047, 2048, True, 1, None)
+    assert list(rd["kernels"]) == ["kr_rows_r2c", "kr_cols_conv", "kr_rows_solve<dense>", "k_tc_gemm(x+y)"]
+    rg = bench.roofline_of(phase_ms, 2047, 2048, False, 1, None)
+    assert list(rg["kernels"]) == ["k_rows_r2c", "k_cols_conv", "k_rows_solve",
+                                  "k_transpose+k_rows_gs+k_transpose_leapfrog"]
+    assert rd["traffic"] is None and rg["traffic"] is None
